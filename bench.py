@@ -1,0 +1,402 @@
+"""Benchmark of the direct-summation hot path on one (or N replica) GB300 GPUs.
+
+Workload: an N = 2^20 Plummer sphere with log-normal masses (sigma 0.5,
+total mass 1), eps = 4/N, seed 1003; one step = one full evaluation of
+acceleration, jerk and potential of all N i-particles against all N
+j-particles in mixed precision (the j images are rebuilt from the FP64 state
+by the device predictor, then the force kernel and, if the launch splits j,
+the reduction).  Metric: pair interactions per second (N^2 per step, Eq. 3's
+convention), with the k = 60 GFLOP/s figure and the fraction of FP32 peak.
+
+Alongside: the FP64 GPU path on an i-subset, the eps = 0 / r_min = 1e-6
+guarded variant, the end-to-end rate through the host-pointer C ABI (uploads
+and result downloads inside the timed region), the FP64 CPU oracle on a
+bounded i-subset (which also gives the per-particle error of the mixed
+results), SM clocks sampled during the timed region, and the roofline entry.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) are replicas: every rank
+evaluates its own copy of the workload; value = all ranks' pairs / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair interactions/s (acc+jerk+pot) mixed vs FP64 GPU at <=1e-6 rel force err"
+UNIT = "pair interactions/s"
+N_DEFAULT = 1 << 20
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("force_mixed.cu", "pair_mixed.cuh", "tma.cuh", "kirin_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_0707_0438_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        with open(self.tmp.name) as f:
+            rows = [r.split(",") for r in f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _fp32_peak_tflops(nsm: int, mhz: float) -> float:
+    """CUDA-core FP32 peak: SMs x 128 lanes x 2 flops (FMA) x clock."""
+    return nsm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def _time_oracle_sample(p, k_i, seed):
+    import oracle
+    il = _subset(p.n, k_i, seed)
+    t0 = time.perf_counter()
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    dt = time.perf_counter() - t0
+    return il, ref, dt, oracle.num_threads()
+
+
+def _subset(n, k, seed):
+    from paper_0707_0438_gb300 import workloads
+    return workloads.i_subset(n, k, seed)
+
+
+def _calibrated_oracle_size(p, target_s):
+    """i-subset size for about target_s seconds of oracle time on this host."""
+    _, _, dt, _ = _time_oracle_sample(p, 32, 99)
+    per_i = max(dt / 32, 1e-6)
+    return int(max(64, min(p.n, target_s / per_i)))
+
+
+def run_reference(args):
+    """The CPU oracle on the host cores (the reference arm), bounded sample per step."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from paper_0707_0438_gb300 import workloads
+    n = args.n
+    p = workloads.config_large(n)
+    per_step_s = max(1.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    k_i = _calibrated_oracle_size(p, per_step_s)
+    for w in range(args.warmup):
+        _time_oracle_sample(p, max(16, k_i // 8), 1000 + w)
+    times = []
+    threads = 1
+    for s in range(args.steps):
+        _, _, dt, threads = _time_oracle_sample(p, k_i, 2000 + s)
+        times.append(dt)
+    total = sum(times)
+    value = k_i * n * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(n, "oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{k_i} i x {n} j per step (FP64 CPU oracle, OpenMP over i)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(n, precision):
+    return {"workload": f"plummer N={n} lognormal masses (sigma 0.5), eps=4/N, seed 1003: one full "
+                        f"acc+jerk+pot evaluation of all i vs all j",
+            "n": n, "eps": 4.0 / n, "precision": precision, "global_batch": n, "parallelism": "replicas",
+            "l2": "256 MiB buffer written between timed steps (flushes L2)"}
+
+
+def run_native(args):
+    import torch
+
+    from paper_0707_0438_gb300 import abi, metrics, workloads
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    n = args.n
+    p = workloads.config_large(n)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    m_d = torch.tensor(p.m, device=dev)
+    x_d = torch.tensor(p.x, device=dev)
+    v_d = torch.tensor(p.v, device=dev)
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    jerk = torch.empty_like(acc)
+    pot = torch.empty(n, dtype=torch.float64, device=dev)
+
+    k = abi.Kirin(n, p.eps, precision="mixed", device=local, stream=sp)
+    k.set_j_particles_dev(m_d, x_d, v_d)
+    k.sync()
+    groups, n_split = k.get_launch(n)
+    launches_per_step = 2 + (1 if n_split > 1 else 0)  # predictor/pack, force, split reduction
+
+    def step(kk):
+        kk.predict(0.0)  # rebuild the j images from the FP64 state on the device
+        kk.compute_forces_dev(None, acc, jerk, pot)
+
+    def timed(kk, steps, warmup, dn=None):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step(kk)
+            kk.sync()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            for s in range(steps):
+                flush.zero_()  # on `stream`, outside the events
+                evs[s][0].record(stream)
+                step(kk)
+                evs[s][1].record(stream)
+            kk.sync()
+            torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3
+
+    # ---- headline: mixed precision, full evaluation ----
+    with ClockSampler(local) as clk:
+        t_mixed = timed(k, args.steps, args.warmup)
+    clocks = clk.summary()
+    t_max = t_mixed
+    if dist is not None:
+        tt = torch.tensor([t_mixed], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    pairs_per_step = float(n) * float(n)
+    value = world * pairs_per_step * args.steps / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+    res_mixed = (acc.cpu().numpy(), jerk.cpu().numpy(), pot.cpu().numpy()) if rank == 0 else None
+
+    if rank != 0:
+        k.close()
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    extra = {}
+    # ---- eps = 0 with the r_min = 1e-6 guard (Sect. 3.3.1) ----
+    k.set_params(0.0, 1.0, 1e-6, "mixed")
+    t_g = timed(k, max(1, args.steps // 2), 1)
+    extra["eps0_rmin_guard"] = {"value": pairs_per_step * max(1, args.steps // 2) / t_g, "unit": UNIT,
+                                "ms_per_step": 1e3 * t_g / max(1, args.steps // 2)}
+    k.set_params(p.eps, 1.0, 0.0, "mixed")
+
+    # ---- FP64 GPU path on an i-subset (all j) ----
+    n_sub = min(n, 16384)
+    il_sub = torch.tensor(workloads.i_subset(n, n_sub, 17), device=dev)
+    acc_s = torch.empty((n_sub, 3), dtype=torch.float64, device=dev)
+    jerk_s, pot_s = torch.empty_like(acc_s), torch.empty(n_sub, dtype=torch.float64, device=dev)
+    k.set_params(p.eps, 1.0, 0.0, "fp64")
+    with torch.cuda.stream(stream):
+        k.compute_forces_dev(il_sub, acc_s, jerk_s, pot_s)  # warm-up
+        k.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 2
+        for _ in range(reps):
+            k.compute_forces_dev(il_sub, acc_s, jerk_s, pot_s)
+        e1.record(stream)
+        k.sync()
+    t64 = e0.elapsed_time(e1) / 1e3 / reps
+    fp64_rate = n_sub * float(n) / t64
+    fp64_res = (acc_s.cpu().numpy(), jerk_s.cpu().numpy(), pot_s.cpu().numpy())
+    sub_idx = il_sub.cpu().numpy()
+    mixed_vs_fp64 = {q: metrics.summary(f(a[sub_idx], b)) for q, f, a, b in (
+        ("acc", metrics.rel_err_vec, res_mixed[0], fp64_res[0]),
+        ("jerk", metrics.rel_err_vec, res_mixed[1], fp64_res[1]),
+        ("pot", metrics.rel_err_scalar, res_mixed[2], fp64_res[2]))}
+    extra["fp64"] = {"value": fp64_rate, "unit": UNIT, "sample": f"{n_sub} i x {n} j",
+                     "mixed_speedup": value / world / fp64_rate, "mixed_vs_fp64_rel_err": mixed_vs_fp64}
+    k.set_params(p.eps, 1.0, 0.0, "mixed")
+
+    # ---- end to end through the host-pointer C ABI ----
+    pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    hm, hx, hv = pin((n,)), pin((n, 3)), pin((n, 3))
+    hm[:], hx[:], hv[:] = p.m, p.x, p.v
+    ha, hj, hp = pin((n, 3)), pin((n, 3)), pin((n,))
+    import ctypes
+    L = k.lib
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def e2e_step():
+        rc = L.kirin_set_j_particles(k.ctx, 0, n, dp(hm), dp(hx), dp(hv), None, None, None)
+        rc = rc or L.kirin_compute_forces(k.ctx, 0, None)
+        rc = rc or L.kirin_get_acc_jerk_pot(k.ctx, dp(ha), dp(hj), dp(hp))
+        if rc:
+            raise abi.KirinError(rc, "e2e step")
+
+    e2e_step()
+    e_steps = max(1, args.steps // 2)
+    t_e2e = 0.0
+    for _ in range(e_steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_step()
+        t_e2e += time.perf_counter() - t0
+    e2e = {"value": pairs_per_step * e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(hm.nbytes + hx.nbytes + hv.nbytes),
+           "d2h_bytes_per_step": int(ha.nbytes + hj.nbytes + hp.nbytes),
+           "ms_per_step": 1e3 * t_e2e / e_steps}
+    k.close()
+
+    # ---- CPU oracle on a bounded sample; also the error of the mixed results ----
+    cpu = None
+    if not args.no_cpu:
+        k_i = _calibrated_oracle_size(p, args.cpu_seconds)
+        il, ref, dt, threads = _time_oracle_sample(p, k_i, 3)
+        errs = {q: metrics.summary(f(a[il], b)) for q, f, a, b in (
+            ("acc", metrics.rel_err_vec, res_mixed[0], ref[0]),
+            ("jerk", metrics.rel_err_vec, res_mixed[1], ref[1]),
+            ("pot", metrics.rel_err_scalar, res_mixed[2], ref[2]))}
+        cpu = {"value": k_i * float(n) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{k_i} random i x all {n} j, FP64 CPU oracle (OpenMP over i), {dt:.1f} s"}
+        extra["mixed_vs_oracle_rel_err"] = errs
+
+    # ---- roofline of the force kernel (FP32 CUDA-core pipe) ----
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_src = _peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = _fp32_peak_tflops(props.multi_processor_count, f_max)
+    achieved = 60.0 * pairs_per_step / (t_mixed / args.steps) / 1e12  # Eq. 3, k = 60
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            tr = json.load(f).get("k_force_mixed", {})
+        if tr.get("source_sha") == _kernel_source_sha():
+            traffic = tr.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_note": f"FP32 CUDA-core peak {props.multi_processor_count} SMs x 128 x 2 x {f_max:.0f} MHz "
+                         f"(max SM clock, {peak_src}); achieved counts k=60 flops per pair (Eq. 3)"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / _fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 pair math, double-single positions, f64 results", "data": "synthetic",
+        "config": dict(_config(n, "mixed"), launch={"groups": groups, "n_split": n_split}),
+        "gflops_k60": 60.0 * value / 1e9, "gflops_k38_equiv": 38.0 * value / 1e9,
+        "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        "roofline": roof, "cpu_baseline": cpu,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,244 @@
+/*
+ * kirin.h -- C ABI of libkirin: direct O(N^2) softened gravitational
+ * acceleration, jerk and potential on one GB300 (sm_103a) GPU.
+ *
+ * The call sequence mirrors the GRAPE-6 style library of Appendix A
+ * (GPU_open / GPU_set_j_particle / GPU_set_ti / GPUcalc_firsthalf /
+ * GPUcalc_lasthalf / GPU_close), with the host-side predictor of Sect. 3.1 moved
+ * onto the device and j-particles kept resident in HBM between calls.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (KIRIN_OK) on success, a negative KIRIN_E* code otherwise.
+ *    Nothing aborts or exits; kirin_strerror() names a code and
+ *    kirin_last_error() gives the context's last detailed message.
+ *  - Host arrays are owned by the caller and only read/written during the call
+ *    (kirin_get_* calls synchronise first).  Device memory is owned by the
+ *    library and released by kirin_finalize / kirin_batch_destroy.
+ *  - Vectors are row-major: x[3*k + c] is component c of particle k.
+ *  - *_dev entry points take CUDA device pointers, enqueue work on the
+ *    context's stream and return without synchronising; errors detected on
+ *    the device (bad index, timed-out wait) are reported by the next
+ *    kirin_sync / kirin_get_* call on that context.
+ *  - Units: any consistent set; G is a parameter (1 in the Henon units of
+ *    Sect. 4).
+ */
+#ifndef KIRIN_H
+#define KIRIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KIRIN_OK 0
+#define KIRIN_EINVAL (-1)     /* bad argument: NULL, size, index, eps < 0, ... */
+#define KIRIN_ENOMEM (-2)     /* device or pinned host allocation failed */
+#define KIRIN_ECUDA (-3)      /* a CUDA runtime call failed (see kirin_last_error) */
+#define KIRIN_ENONFINITE (-4) /* NaN or Inf in uploaded particle data */
+#define KIRIN_ETIMEOUT (-5)   /* a bounded wait inside a kernel gave up */
+#define KIRIN_ESTATE (-6)     /* call out of order (e.g. forces before particles) */
+
+typedef struct kirin_ctx kirin_ctx;
+
+/* Arithmetic of the pair interaction.
+ * KIRIN_MIXED: positions held as double-single (hi + lo float pairs), the
+ *   separation formed in that precision and cast to FP32, FP32 pair arithmetic
+ *   with the hardware reciprocal square root, per-tile FP32 partial sums
+ *   folded into compensated (double-single) accumulators; results in FP64.
+ * KIRIN_FP64: every operation in FP64. */
+typedef enum { KIRIN_FP64 = 0, KIRIN_MIXED = 1 } kirin_precision;
+
+typedef struct {
+    double eps;      /* Plummer softening length, >= 0 (Sect. 3.3.1); s^2 = r^2 + eps^2 */
+    double G;        /* gravitational constant */
+    double r_min;    /* separation floor: s^2 = max(s^2, r_min^2), 0 = off; with eps = 0
+                        a pair at exactly zero separation contributes nothing (Sect. 3.3.1) */
+    int32_t prec;    /* kirin_precision */
+    int32_t device;  /* CUDA device ordinal */
+    void *stream;    /* cudaStream_t to enqueue on; NULL: the context creates its own */
+} kirin_config;
+
+/* GPU_open (Appendix A).  Creates a context for up to n_max particles on
+ * cfg->device and allocates its device buffers (about 160 bytes per particle
+ * plus result and split-partial buffers).  *out receives the context.
+ * Errors: EINVAL (NULL out/cfg, n_max < 1 or > 2^31 - 256, eps < 0, r_min < 0,
+ * unknown precision), ECUDA (no such device), ENOMEM. */
+int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg);
+
+/* GPU_close (Appendix A).  Synchronises, frees all device and host buffers
+ * and the stream the context created.  NULL is accepted. */
+int kirin_finalize(kirin_ctx *ctx);
+
+/* GPU_npipes (Appendix A): the capacity and the current launch shape.
+ * tile_i = i-particles per CTA, tile_j = j-particles per shared-memory tile
+ * for the context's precision.  Any output pointer may be NULL. */
+int kirin_query(const kirin_ctx *ctx, int64_t *n_max, int32_t *tile_i, int32_t *tile_j);
+
+/* Change the softening, G, separation floor or precision of an open context. */
+int kirin_set_params(kirin_ctx *ctx, double eps, double G, double r_min, int32_t prec);
+
+/* Make the context enqueue on `stream` (a cudaStream_t, NULL = its own stream). */
+int kirin_set_stream(kirin_ctx *ctx, void *stream);
+
+/* Launch shape of the force kernel (the configurable "npipes" of GPU_npipes,
+ * Appendix A, and the j-split of Sect. 3.2): `groups` j-groups per CTA
+ * (1, 2, 4 or 8; a CTA holds 512 / groups i-particles in mixed precision,
+ * 256 / groups in FP64) and `n_split` CTAs sharing the j range (1..1024,
+ * reduced on the device).  groups = n_split = 0 restores the automatic choice
+ * (a cost model over waves of CTAs).  Errors: EINVAL. */
+int kirin_set_launch(kirin_ctx *ctx, int32_t groups, int32_t n_split);
+
+/* The shape that a force call for n_i i-particles would use now. */
+int kirin_get_launch(kirin_ctx *ctx, int64_t n_i, int32_t *groups, int32_t *n_split);
+
+/* GPU_set_j_particle (Appendix A), in bulk: particles [first, first + n) get
+ * mass m[k], position x[3k..3k+2], velocity v[3k..], and for the predictor
+ * acceleration a, jerk and their time t0 (each of a, jerk, t0 may be NULL:
+ * zeros).  The number of j-particles becomes max(previous, first + n).
+ * The positions used by the force are the given ones until kirin_predict.
+ * Host arrays, copied before return.
+ * Errors: EINVAL (range outside [0, n_max), NULL m/x/v), ENONFINITE. */
+int kirin_set_j_particles(kirin_ctx *ctx, int64_t first, int64_t n, const double *m,
+                          const double *x, const double *v, const double *a,
+                          const double *jerk, const double *t0);
+
+/* Same as kirin_set_j_particles with device arrays (FP64, same layouts);
+ * enqueued on the context's stream.  Non-finite values are reported as
+ * ENONFINITE by the next kirin_sync / kirin_get_*. */
+int kirin_set_j_particles_dev(kirin_ctx *ctx, int64_t first, int64_t n, const double *m,
+                              const double *x, const double *v, const double *a,
+                              const double *jerk, const double *t0);
+
+/* Shrink or grow the number of j-particles (<= the highest index ever set + 1). */
+int kirin_set_nj(kirin_ctx *ctx, int64_t n_j);
+
+/* GPU_set_ti (Appendix A; Sect. 3.1 does it on the host, here it runs on the
+ * device in FP64): predict every j-particle to time t,
+ *   x_p = x + v dt + a dt^2/2 + jerk dt^3/6,  v_p = v + a dt + jerk dt^2/2,
+ * dt = t - t0_j, and use (x_p, v_p) for subsequent force calls.
+ * Errors: ESTATE (no particles). */
+int kirin_predict(kirin_ctx *ctx, double t);
+
+/* GPUcalc_firsthalf (Appendix A): start the evaluation, for the n_i
+ * i-particles listed in i_list (indices into the j set; NULL = all j in
+ * order, n_i ignored), of
+ *   a_i    =  G sum_{j != i} m_j d_ij / s^3
+ *   jerk_i =  G sum_{j != i} m_j [ w_ij / s^3 - 3 (d_ij . w_ij) d_ij / s^5 ]
+ *   phi_i  = -G sum_{j != i} m_j / s
+ * with d_ij = x_j - x_i, w_ij = v_j - v_i, s^2 = |d_ij|^2 + eps^2 (Sect. 2
+ * Eq. 1 with the attractive sign, Sect. 3 and Sect. 3.1).  Asynchronous;
+ * the host i_list is copied before return.  Small active blocks are split
+ * over j across thread groups and CTAs and reduced on the device (Sect. 3.2).
+ * Errors: EINVAL (n_i < 0 or > n_max, index outside [0, n_j)), ESTATE. */
+int kirin_compute_forces(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list);
+
+/* GPUcalc_lasthalf (Appendix A): wait for the last kirin_compute_forces and
+ * copy its results, in i_list order, to host arrays acc (n_i x 3),
+ * jerk (n_i x 3), pot (n_i).  Any of them may be NULL.
+ * Errors: ESTATE (no pending results), ETIMEOUT, ENONFINITE, ECUDA. */
+int kirin_get_acc_jerk_pot(kirin_ctx *ctx, double *acc, double *jerk, double *pot);
+
+/* Device twin of compute + get: i_list, acc, jerk, pot are device arrays
+ * (int32 n_i; FP64 n_i x 3, n_i x 3, n_i; any output may be NULL).  i_list
+ * NULL = all j.  Enqueued on the context's stream, no synchronisation. */
+int kirin_compute_forces_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list,
+                             double *acc, double *jerk, double *pot);
+
+/* Wait for all work of the context and report device-side errors. */
+int kirin_sync(kirin_ctx *ctx);
+
+/* Energies of Eq. 2: kin = sum 1/2 m |v|^2 (v: host n_j x 3, or NULL for the
+ * current, possibly predicted, velocities) and pot = 1/2 sum_i m_i phi_i with
+ * phi from a full evaluation at the current positions.  Synchronous. */
+int kirin_energy(kirin_ctx *ctx, const double *v, double *kin, double *pot);
+
+/* ---- 4th-order Hermite integration on the device (Sect. 3, Sect. 3.1) ----
+ * The predictor-corrector scheme the paper runs on the host, executed by
+ * device kernels on the context's particles:
+ *   corrector  a2 = [-6 (a0 - a1) - dt (4 j0 + 2 j1)] / dt^2,
+ *              a3 = [12 (a0 - a1) + 6 dt (j0 + j1)] / dt^3,
+ *              x1 = x_p + a2 dt^4/24 + a3 dt^5/120, v1 = v_p + a2 dt^3/6 + a3 dt^4/24
+ *   block steps: power-of-two dt in [dt_min, dt_max] from Aarseth's criterion
+ *   with accuracy eta; a step shrinks freely and doubles only when the new
+ *   time is a multiple of the doubled step. */
+
+/* Evaluate a, jerk for all particles at their current state, set t_i = t and
+ * dt_i = 0.01 |a| / |jerk| quantised down to a power of two in [dt_min, dt_max]. */
+int kirin_hermite_init(kirin_ctx *ctx, double t, double eta, double dt_min, double dt_max);
+
+/* One block step: t_next = min_i (t_i + dt_i); if t_next > t_end nothing is
+ * done and *n_active = 0.  Otherwise predict all j to t_next, evaluate the
+ * block {i : t_i + dt_i = t_next}, correct it and choose its new steps.
+ * *t_now receives t_next; *n_active the block size.  Either may be NULL. */
+int kirin_hermite_block_step(kirin_ctx *ctx, double t_end, double *t_now, int64_t *n_active);
+
+/* Block steps until every particle reached t_end (a multiple of dt_max) or
+ * max_steps steps were taken; *n_steps and *n_pairs receive the number of
+ * block steps and the sum of n_active * n_j over them (either may be NULL). */
+int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *n_steps,
+                      double *n_pairs);
+
+/* One shared step of size dt for all particles (no step-size update). */
+int kirin_hermite_shared_step(kirin_ctx *ctx, double dt);
+
+/* Copy the integrator state (host arrays, each may be NULL): x, v, a, jerk
+ * (n_j x 3), t and dt (n_j). */
+int kirin_get_state(kirin_ctx *ctx, double *x, double *v, double *a, double *jerk, double *t,
+                    double *dt);
+
+/* ---- accelerations of device particle sets (leapfrog clients, Sect. 4.3) ----
+ * Acceleration (and optionally potential) of all n particles of (m, x), every
+ * particle against every other, without jerk: the force-only evaluation the
+ * paper's treecode client needs.  m: n, x: n x 3, acc: n x 3, pot: n or NULL,
+ * all FP64 device arrays.  Uses the context's eps, G and precision and its
+ * j buffers (n <= n_max). */
+int kirin_accel_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x, double *acc,
+                    double *pot);
+
+/* Reverse-mode derivative of kirin_accel_dev (no counterpart in the paper):
+ * given g = dL/da (n x 3), write dL/dx (n x 3) and dL/dm (n), where
+ *   dL/dx_k = G sum_{j != k} K(d_kj) (m_k g_j - m_j g_k),
+ *   K(d) = I / s^3 - 3 d d^T / s^5,  d_kj = x_j - x_k,
+ *   dL/dm_k = G sum_{i != k} g_i . (x_k - x_i) / s_ik^3.
+ * gx or gm may be NULL.  FP64 device arrays; context precision. */
+int kirin_accel_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x,
+                            const double *g, double *gx, double *gm);
+
+/* ---- batched ensembles: many independent clusters in one launch ----
+ * Cluster c owns particles [offsets[c], offsets[c+1]) with softening eps[c];
+ * clusters do not interact.  State is FP64 on the device; the pair arithmetic
+ * is the mixed one. */
+typedef struct kirin_batch kirin_batch;
+
+/* offsets: host, n_clusters + 1 entries, offsets[0] = 0, non-decreasing;
+ * eps: host, n_clusters entries, >= 0.  Errors: EINVAL, ECUDA, ENOMEM. */
+int kirin_batch_create(kirin_batch **out, int32_t n_clusters, const int64_t *offsets,
+                       const double *eps, double G, int32_t device, void *stream);
+int kirin_batch_destroy(kirin_batch *b);
+
+/* Host FP64 state: m (n_total), x, v (n_total x 3). */
+int kirin_batch_set_state(kirin_batch *b, const double *m, const double *x, const double *v);
+int kirin_batch_get_state(kirin_batch *b, double *x, double *v);
+
+/* n_steps kick-drift-kick leapfrog steps of size dt for every cluster
+ * (Sect. 4.3 integrator); use_graph != 0 captures the steps in a CUDA graph
+ * (built on first use for a given (dt, n_steps), then replayed).
+ * Asynchronous; kirin_batch_sync waits and reports device errors. */
+int kirin_batch_leapfrog(kirin_batch *b, double dt, int32_t n_steps, int32_t use_graph);
+int kirin_batch_sync(kirin_batch *b);
+
+/* Accelerations of every particle of every cluster into a host array (n_total x 3). */
+int kirin_batch_accel(kirin_batch *b, double *acc);
+
+/* Human-readable name of a return code (static string). */
+const char *kirin_strerror(int code);
+
+/* The context's last detailed error message (static storage owned by ctx). */
+const char *kirin_last_error(const kirin_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KIRIN_H */

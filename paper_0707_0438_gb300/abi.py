@@ -1,0 +1,364 @@
+"""Thin Python binding of libkirin's C ABI (include/kirin.h), via ctypes.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep their C names (``kirin_init``, ``kirin_compute_forces``
+...) on the object returned by :func:`lib`; :class:`Kirin` and
+:class:`KirinBatch` wrap a context with numpy (host) and torch (device)
+arrays.  There is no fallback: if libkirin.so has not been built (see
+``paper_0707_0438_gb300.build``), :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+KIRIN_OK = 0
+KIRIN_EINVAL = -1
+KIRIN_ENOMEM = -2
+KIRIN_ECUDA = -3
+KIRIN_ENONFINITE = -4
+KIRIN_ETIMEOUT = -5
+KIRIN_ESTATE = -6
+KIRIN_FP64 = 0
+KIRIN_MIXED = 1
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kirin.h")
+
+
+class KirinError(RuntimeError):
+    def __init__(self, code, what, detail=""):
+        self.code = code
+        super().__init__(f"{what}: {code} ({_strerror(code)}){' - ' + detail if detail else ''}")
+
+
+class kirin_config(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("G", ctypes.c_double), ("r_min", ctypes.c_double),
+                ("prec", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes); pointers to device memory are passed as void*.
+_SIGS = {
+    "kirin_init": (ctypes.c_int, [ctypes.POINTER(_P), _I64, ctypes.POINTER(kirin_config)]),
+    "kirin_finalize": (ctypes.c_int, [_P]),
+    "kirin_query": (ctypes.c_int, [_P, _PI64, _PI32, _PI32]),
+    "kirin_set_params": (ctypes.c_int, [_P, _D, _D, _D, _I32]),
+    "kirin_set_stream": (ctypes.c_int, [_P, _P]),
+    "kirin_set_launch": (ctypes.c_int, [_P, _I32, _I32]),
+    "kirin_get_launch": (ctypes.c_int, [_P, _I64, _PI32, _PI32]),
+    "kirin_set_j_particles": (ctypes.c_int, [_P, _I64, _I64, _PD, _PD, _PD, _PD, _PD, _PD]),
+    "kirin_set_j_particles_dev": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _P, _P, _P, _P]),
+    "kirin_set_nj": (ctypes.c_int, [_P, _I64]),
+    "kirin_predict": (ctypes.c_int, [_P, _D]),
+    "kirin_compute_forces": (ctypes.c_int, [_P, _I64, _PI32]),
+    "kirin_get_acc_jerk_pot": (ctypes.c_int, [_P, _PD, _PD, _PD]),
+    "kirin_compute_forces_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P]),
+    "kirin_sync": (ctypes.c_int, [_P]),
+    "kirin_energy": (ctypes.c_int, [_P, _PD, _PD, _PD]),
+    "kirin_hermite_init": (ctypes.c_int, [_P, _D, _D, _D, _D]),
+    "kirin_hermite_block_step": (ctypes.c_int, [_P, _D, _PD, _PI64]),
+    "kirin_hermite_run": (ctypes.c_int, [_P, _D, _I64, _PI64, _PD]),
+    "kirin_hermite_shared_step": (ctypes.c_int, [_P, _D]),
+    "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
+    "kirin_accel_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P]),
+    "kirin_accel_adjoint_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
+    "kirin_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _PI64, _PD, _D, _I32, _P]),
+    "kirin_batch_destroy": (ctypes.c_int, [_P]),
+    "kirin_batch_set_state": (ctypes.c_int, [_P, _PD, _PD, _PD]),
+    "kirin_batch_get_state": (ctypes.c_int, [_P, _PD, _PD]),
+    "kirin_batch_leapfrog": (ctypes.c_int, [_P, _D, _I32, _I32]),
+    "kirin_batch_sync": (ctypes.c_int, [_P]),
+    "kirin_batch_accel": (ctypes.c_int, [_P, _PD]),
+    "kirin_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "kirin_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/kirin.h."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kirin_\w+)\s*\(", text)))
+
+
+def lib():
+    """The loaded libkirin with argument types set (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libkirin.so is not built ({path}); run __graft_entry__.build()")
+        cdll = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(cdll, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = cdll
+    return _lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return lib().kirin_strerror(code).decode()
+    except Exception:  # the library itself may be what is missing
+        return "?"
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_PD)
+
+
+def _host(a, shape=None, dtype=np.float64):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if shape is not None and a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+def _dev(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Kirin:
+    """One libkirin context (GPU_open ... GPU_close of Appendix A)."""
+
+    def __init__(self, n_max, eps, G=1.0, r_min=0.0, precision="mixed", device=0, stream=None):
+        self.lib = lib()
+        cfg = kirin_config(float(eps), float(G), float(r_min), _prec(precision), int(device),
+                           None if stream is None else ctypes.c_void_p(int(stream)))
+        h = ctypes.c_void_p()
+        self._check(self.lib.kirin_init(ctypes.byref(h), int(n_max), ctypes.byref(cfg)), "kirin_init", ctx=False)
+        self.ctx = h
+        self.n_max = int(n_max)
+        self.n_j = 0
+        self._pending = 0
+
+    def _check(self, rc, what, ctx=True):
+        if rc != KIRIN_OK:
+            detail = ""
+            if ctx and getattr(self, "ctx", None):
+                detail = self.lib.kirin_last_error(self.ctx).decode()
+            raise KirinError(rc, what, detail)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.kirin_finalize(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration
+    def set_params(self, eps, G=1.0, r_min=0.0, precision="mixed"):
+        self._check(self.lib.kirin_set_params(self.ctx, float(eps), float(G), float(r_min), _prec(precision)),
+                    "kirin_set_params")
+
+    def set_stream(self, stream):
+        self._check(self.lib.kirin_set_stream(self.ctx, None if stream is None else ctypes.c_void_p(int(stream))),
+                    "kirin_set_stream")
+
+    def set_launch(self, groups=0, n_split=0):
+        self._check(self.lib.kirin_set_launch(self.ctx, int(groups), int(n_split)), "kirin_set_launch")
+
+    def get_launch(self, n_i):
+        g, s = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.kirin_get_launch(self.ctx, int(n_i), ctypes.byref(g), ctypes.byref(s)),
+                    "kirin_get_launch")
+        return g.value, s.value
+
+    def query(self):
+        n, ti, tj = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.kirin_query(self.ctx, ctypes.byref(n), ctypes.byref(ti), ctypes.byref(tj)),
+                    "kirin_query")
+        return n.value, ti.value, tj.value
+
+    # -- GPU_set_j_particle / GPU_set_ti
+    def set_j_particles(self, m, x, v, a=None, jerk=None, t0=None, first=0):
+        m = _host(m)
+        n = m.shape[0]
+        x, v = _host(x, (n, 3)), _host(v, (n, 3))
+        a, jerk, t0 = _host(a, (n, 3)), _host(jerk, (n, 3)), _host(t0, (n,))
+        self._check(self.lib.kirin_set_j_particles(self.ctx, int(first), n, _dp(m), _dp(x), _dp(v), _dp(a),
+                                                   _dp(jerk), _dp(t0)), "kirin_set_j_particles")
+        self.n_j = max(self.n_j, first + n)
+
+    def set_j_particles_dev(self, m, x, v, a=None, jerk=None, t0=None, first=0):
+        n = m.shape[0]
+        self._check(self.lib.kirin_set_j_particles_dev(self.ctx, int(first), int(n), _dev(m), _dev(x), _dev(v),
+                                                       _dev(a), _dev(jerk), _dev(t0)), "kirin_set_j_particles_dev")
+        self.n_j = max(self.n_j, first + n)
+
+    def set_nj(self, n_j):
+        self._check(self.lib.kirin_set_nj(self.ctx, int(n_j)), "kirin_set_nj")
+        self.n_j = int(n_j)
+
+    def predict(self, t):
+        self._check(self.lib.kirin_predict(self.ctx, float(t)), "kirin_predict")
+
+    # -- GPUcalc_firsthalf / GPUcalc_lasthalf
+    def compute_forces(self, i_list=None):
+        if i_list is None:
+            self._check(self.lib.kirin_compute_forces(self.ctx, 0, None), "kirin_compute_forces")
+            self._pending = self.n_j
+        else:
+            il = np.ascontiguousarray(i_list, dtype=np.int32)
+            self._check(self.lib.kirin_compute_forces(self.ctx, il.shape[0], il.ctypes.data_as(_PI32)),
+                        "kirin_compute_forces")
+            self._pending = il.shape[0]
+
+    def get_acc_jerk_pot(self):
+        n = self._pending
+        acc, jerk, pot = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+        self._check(self.lib.kirin_get_acc_jerk_pot(self.ctx, _dp(acc), _dp(jerk), _dp(pot)), "kirin_get_acc_jerk_pot")
+        return acc, jerk, pot
+
+    def forces(self, i_list=None):
+        self.compute_forces(i_list)
+        return self.get_acc_jerk_pot()
+
+    def compute_forces_dev(self, i_list, acc, jerk, pot):
+        """Device arrays (torch): i_list int32 (n_i) or None, acc/jerk (n_i, 3) and pot (n_i) float64."""
+        n_i = self.n_j if i_list is None else i_list.shape[0]
+        self._check(self.lib.kirin_compute_forces_dev(self.ctx, int(n_i), _dev(i_list), _dev(acc), _dev(jerk),
+                                                      _dev(pot)), "kirin_compute_forces_dev")
+
+    def sync(self):
+        self._check(self.lib.kirin_sync(self.ctx), "kirin_sync")
+
+    def energy(self, v=None):
+        k, w = ctypes.c_double(), ctypes.c_double()
+        vv = _host(v, (self.n_j, 3))
+        self._check(self.lib.kirin_energy(self.ctx, _dp(vv), ctypes.byref(k), ctypes.byref(w)), "kirin_energy")
+        return k.value, w.value
+
+    # -- Hermite integrator
+    def hermite_init(self, t=0.0, eta=0.01, dt_min=2.0 ** -20, dt_max=2.0 ** -3):
+        self._check(self.lib.kirin_hermite_init(self.ctx, float(t), float(eta), float(dt_min), float(dt_max)),
+                    "kirin_hermite_init")
+
+    def hermite_block_step(self, t_end):
+        t, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(self.lib.kirin_hermite_block_step(self.ctx, float(t_end), ctypes.byref(t), ctypes.byref(n)),
+                    "kirin_hermite_block_step")
+        return t.value, n.value
+
+    def hermite_run(self, t_end, max_steps=0):
+        s, p = ctypes.c_int64(), ctypes.c_double()
+        self._check(self.lib.kirin_hermite_run(self.ctx, float(t_end), int(max_steps), ctypes.byref(s),
+                                               ctypes.byref(p)), "kirin_hermite_run")
+        return s.value, p.value
+
+    def hermite_shared_step(self, dt):
+        self._check(self.lib.kirin_hermite_shared_step(self.ctx, float(dt)), "kirin_hermite_shared_step")
+
+    def get_state(self):
+        n = self.n_j
+        x, v, a, j = (np.empty((n, 3)) for _ in range(4))
+        t, dt = np.empty(n), np.empty(n)
+        self._check(self.lib.kirin_get_state(self.ctx, _dp(x), _dp(v), _dp(a), _dp(j), _dp(t), _dp(dt)),
+                    "kirin_get_state")
+        return {"x": x, "v": v, "a": a, "j": j, "t": t, "dt": dt}
+
+    # -- device particle sets
+    def accel_dev(self, m, x, acc, pot=None):
+        self._check(self.lib.kirin_accel_dev(self.ctx, int(m.shape[0]), _dev(m), _dev(x), _dev(acc), _dev(pot)),
+                    "kirin_accel_dev")
+
+    def accel_adjoint_dev(self, m, x, g, gx, gm):
+        self._check(self.lib.kirin_accel_adjoint_dev(self.ctx, int(m.shape[0]), _dev(m), _dev(x), _dev(g), _dev(gx),
+                                                     _dev(gm)), "kirin_accel_adjoint_dev")
+
+
+class KirinBatch:
+    """Many independent clusters advanced together (kirin_batch_*)."""
+
+    def __init__(self, offsets, eps, G=1.0, device=0, stream=None):
+        self.lib = lib()
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        ep = np.ascontiguousarray(eps, dtype=np.float64)
+        h = ctypes.c_void_p()
+        rc = self.lib.kirin_batch_create(ctypes.byref(h), off.shape[0] - 1, off.ctypes.data_as(_PI64), _dp(ep),
+                                         float(G), int(device), None if stream is None else ctypes.c_void_p(int(stream)))
+        if rc != KIRIN_OK:
+            raise KirinError(rc, "kirin_batch_create")
+        self.b = h
+        self.n_total = int(off[-1])
+
+    def _check(self, rc, what):
+        if rc != KIRIN_OK:
+            raise KirinError(rc, what)
+
+    def set_state(self, m, x, v):
+        n = self.n_total
+        m, x, v = _host(m, (n,)), _host(x, (n, 3)), _host(v, (n, 3))
+        self._check(self.lib.kirin_batch_set_state(self.b, _dp(m), _dp(x), _dp(v)), "kirin_batch_set_state")
+
+    def get_state(self):
+        x, v = np.empty((self.n_total, 3)), np.empty((self.n_total, 3))
+        self._check(self.lib.kirin_batch_get_state(self.b, _dp(x), _dp(v)), "kirin_batch_get_state")
+        return x, v
+
+    def leapfrog(self, dt, n_steps, use_graph=True):
+        self._check(self.lib.kirin_batch_leapfrog(self.b, float(dt), int(n_steps), 1 if use_graph else 0),
+                    "kirin_batch_leapfrog")
+
+    def sync(self):
+        self._check(self.lib.kirin_batch_sync(self.b), "kirin_batch_sync")
+
+    def accel(self):
+        acc = np.empty((self.n_total, 3))
+        self._check(self.lib.kirin_batch_accel(self.b, _dp(acc)), "kirin_batch_accel")
+        return acc
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.kirin_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _prec(p) -> int:
+    if p in ("mixed", KIRIN_MIXED):
+        return KIRIN_MIXED
+    if p in ("fp64", KIRIN_FP64):
+        return KIRIN_FP64
+    raise ValueError(f"unknown precision {p!r}")

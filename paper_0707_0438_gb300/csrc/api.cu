@@ -1,0 +1,845 @@
+// libkirin host runtime: the C ABI of include/kirin.h.
+//
+// A context owns, for up to n_max particles, the FP64 base state (m, x, v, a,
+// jerk, t_i, dt_i), the predicted positions and velocities, the two j images
+// (mixed and FP64) that the force kernels stream, the i-list, result and
+// split-partial buffers, and one CUDA stream.  Host <-> device traffic per
+// call is only what the caller passes in or asks for; the j-particles stay
+// resident between calls (the paper re-sends every particle each block step,
+// Sect. 3.1).
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "kirin_internal.cuh"
+
+using namespace kirin;
+
+struct kirin_ctx {
+    int device = 0;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t n_max = 0;
+    int64_t n_img = 0;   // image capacity (multiple of TILE_J)
+    int64_t n_hi = 0;    // highest particle index ever set + 1
+    int64_t n_j = 0;     // j-particles in use
+    double eps = 0, G = 1, r_min = 0;
+    int prec = KIRIN_MIXED;
+
+    // FP64 base state
+    double *bm = nullptr, *bx = nullptr, *bv = nullptr, *ba = nullptr, *bj = nullptr;
+    double *bt = nullptr, *bdt = nullptr;
+    // current (possibly predicted) positions / velocities and the images
+    double *xp = nullptr, *vp = nullptr;
+    JMixed *jm = nullptr;
+    JF64 *jd = nullptr;
+    bool images_dirty = true;
+    int pred_mode = 0;  // 0: base x, v; 1: predicted to pred_t
+    double pred_t = 0;
+
+    int32_t *d_ilist = nullptr;
+    int32_t *h_ilist = nullptr;  // pinned staging
+    double *d_acc = nullptr, *d_jerk = nullptr, *d_pot = nullptr;
+    double *d_partial = nullptr;
+    size_t partial_cap = 0;  // doubles
+    unsigned *d_err = nullptr;
+    double *d_scal = nullptr;  // [0] t_next, [1..2] energies
+    int32_t *d_count = nullptr;
+    double *h_scal = nullptr;  // pinned mirrors
+    int32_t *h_count = nullptr;
+    unsigned *h_err = nullptr;
+
+    bool pending = false;
+    int64_t pending_n = 0;
+
+    // Hermite integrator
+    bool hermite_ready = false;
+    double eta = 0.01, dt_min = 1.0 / (1 << 20), dt_max = 0.125, t_shared = 0;
+
+    // launch-shape override (0 = automatic) and occupancy cache
+    int fix_groups = 0, fix_split = 0;
+    int occ[2][3][2][4] = {};  // [prec][mode][guard][log2 groups]
+
+    char msg[256] = {0};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        if (prev != dev)
+            ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+int set_msg(kirin_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(ctx, call)                                                                           \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return set_msg(ctx, KIRIN_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));          \
+    } while (0)
+
+int64_t round_up(int64_t n, int64_t m) { return (n + m - 1) / m * m; }
+
+int ilog2(int g) { return g == 1 ? 0 : g == 2 ? 1 : g == 4 ? 2 : 3; }
+
+bool guard_on(const kirin_ctx *c) { return c->eps == 0.0 || c->r_min > 0.0; }
+
+int ctas_per_sm(kirin_ctx *c, int prec, int mode, bool guard, int groups)
+{
+    int &slot = c->occ[prec == KIRIN_MIXED][mode][guard][ilog2(groups)];
+    if (slot == 0) {
+        slot = prec == KIRIN_MIXED ? force_mixed_ctas_per_sm(groups, guard, mode)
+                                   : force_fp64_ctas_per_sm(groups, mode);
+        if (slot <= 0)
+            slot = 1;
+    }
+    return slot;
+}
+
+// Launch shape for n_i i-particles against ntiles j tiles: minimise a simple
+// cost model, (waves of CTAs) x (pair slots per CTA) + per-CTA overhead +
+// split-partial traffic, over j-groups {1,2,4,8} and n_split.
+Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bool guard)
+{
+    if (c->fix_groups > 0 && c->fix_split > 0) {
+        Shape s{c->fix_groups, std::min(c->fix_split, std::max(1, ntiles))};
+        return s;
+    }
+    const int per_thread = prec == KIRIN_MIXED ? 2 : 1;
+    Shape best{1, 1};
+    double best_cost = 1e300;
+    const size_t cap_entries = (size_t)1 << 27;  // bound on n_split * 7 * n_i_pad doubles (1 GiB)
+    for (int groups = 1; groups <= 8; groups *= 2) {
+        const int i_cta = per_thread * FORCE_THREADS / groups;
+        const int64_t iblocks = (n_i + i_cta - 1) / i_cta;
+        const double slots = (double)c->nsm * ctas_per_sm(c, prec, mode, guard, groups);
+        const int max_split = std::min(ntiles, MAX_SPLIT);
+        for (int ns = 1; ns <= max_split; ns = ns < 64 ? ns + 1 : ns * 5 / 4) {
+            if (ns > 1 && (size_t)ns * 7 * iblocks * i_cta > cap_entries)
+                break;
+            const double ctas = (double)iblocks * ns;
+            const double waves = ceil(ctas / slots);
+            const double tiles_per = ceil((double)ntiles / ns);
+            // one CTA: tiles_per tiles of TILE_J x i_cta pair slots, plus ~2 tiles of set-up
+            const double cta_cost = (tiles_per + 2.0) * TILE_J * (double)i_cta;
+            double cost = waves * cta_cost;
+            if (ns > 1)  // partial write + reduction, in pair-slot units
+                cost += (double)ns * 7 * iblocks * i_cta * 4.0 / slots + 5.0e3 * TILE_J;
+            if (cost < best_cost * 0.999) {
+                best_cost = cost;
+                best = Shape{groups, ns};
+            }
+        }
+    }
+    return best;
+}
+
+int ensure_partial(kirin_ctx *c, size_t doubles)
+{
+    if (doubles <= c->partial_cap)
+        return KIRIN_OK;
+    if (c->d_partial) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->d_partial);
+        c->d_partial = nullptr;
+        c->partial_cap = 0;
+    }
+    if (cudaMalloc(&c->d_partial, doubles * sizeof(double)) != cudaSuccess)
+        return set_msg(c, KIRIN_ENOMEM, "split-partial buffer of %zu doubles", doubles);
+    c->partial_cap = doubles;
+    return KIRIN_OK;
+}
+
+int ensure_images(kirin_ctx *c)
+{
+    if (!c->images_dirty)
+        return KIRIN_OK;
+    const int64_t n_pad = round_up(std::max<int64_t>(c->n_j, 1), TILE_J);
+    CK(c, launch_predict_pack((int)c->n_j, (int)n_pad, c->pred_t, c->pred_mode, c->bm, c->bx, c->bv,
+                              c->ba, c->bj, c->bt, c->xp, c->vp, c->jm, c->jd, c->d_err, c->stream));
+    c->images_dirty = false;
+    return KIRIN_OK;
+}
+
+// Enqueue one force launch (plus split reduction) over the current images.
+int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mode, double *acc,
+              double *jerk, double *pot)
+{
+    if (n_i == 0)
+        return KIRIN_OK;
+    const int ntiles = (int)((std::max(n_j, 1) + TILE_J - 1) / TILE_J);
+    const bool guard = guard_on(c);
+    const Shape s = choose_shape(c, n_i, ntiles, c->prec, mode, guard);
+    ForceArgs a{};
+    a.jimg = c->prec == KIRIN_MIXED ? (const void *)c->jm : (const void *)c->jd;
+    a.ilist = d_ilist;
+    a.n_i = (int)n_i;
+    a.n_j = n_j;
+    a.ntiles = ntiles;
+    a.n_split = s.n_split;
+    a.eps2 = c->eps * c->eps;
+    a.rmin2 = c->r_min * c->r_min;
+    a.G = c->G;
+    a.acc = acc;
+    a.jerk = jerk;
+    a.pot = pot;
+    a.err = c->d_err;
+    const int i_cta = (c->prec == KIRIN_MIXED ? 2 : 1) * FORCE_THREADS / s.groups;
+    a.n_i_pad = (int)round_up(n_i, i_cta);
+    if (s.n_split > 1) {
+        int rc = ensure_partial(c, (size_t)s.n_split * 7 * a.n_i_pad);
+        if (rc)
+            return rc;
+        a.partial = c->d_partial;
+    }
+    if (c->prec == KIRIN_MIXED)
+        CK(c, launch_force_mixed(a, s, guard, mode, c->stream));
+    else
+        CK(c, launch_force_fp64(a, s, mode, c->stream));
+    if (s.n_split > 1)
+        CK(c, launch_reduce_splits(a, c->stream));
+    return KIRIN_OK;
+}
+
+int read_device_errors(kirin_ctx *c)
+{
+    CK(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const unsigned e = *c->h_err;
+    if (e == 0)
+        return KIRIN_OK;
+    CK(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+    if (e & (ERR_TIMEOUT | ERR_DRAIN))
+        return set_msg(c, KIRIN_ETIMEOUT, "a bounded device wait gave up (flags 0x%x)", e);
+    if (e & ERR_NONFINITE)
+        return set_msg(c, KIRIN_ENONFINITE, "non-finite particle data on the device");
+    if (e & ERR_INDEX)
+        return set_msg(c, KIRIN_EINVAL, "i index outside [0, n_j) on the device");
+    return set_msg(c, KIRIN_ECUDA, "device error flags 0x%x", e);
+}
+
+bool all_finite(const double *p, int64_t n)
+{
+    for (int64_t k = 0; k < n; ++k)
+        if (!isfinite(p[k]))
+            return false;
+    return true;
+}
+
+void free_all(kirin_ctx *c)
+{
+    void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
+                    c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
+                    c->d_count};
+    for (void *p : ptrs)
+        if (p)
+            cudaFree(p);
+    if (c->h_ilist)
+        cudaFreeHost(c->h_ilist);
+    if (c->h_scal)
+        cudaFreeHost(c->h_scal);
+    if (c->h_count)
+        cudaFreeHost(c->h_count);
+    if (c->h_err)
+        cudaFreeHost(c->h_err);
+    if (c->own_stream && c->stream)
+        cudaStreamDestroy(c->stream);
+}
+
+int check_params(double eps, double G, double r_min, int prec)
+{
+    if (!(eps >= 0.0) || !isfinite(eps) || !isfinite(G) || !(r_min >= 0.0) || !isfinite(r_min))
+        return KIRIN_EINVAL;
+    if (prec != KIRIN_FP64 && prec != KIRIN_MIXED)
+        return KIRIN_EINVAL;
+    return KIRIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kirin_strerror(int code)
+{
+    switch (code) {
+    case KIRIN_OK: return "success";
+    case KIRIN_EINVAL: return "invalid argument";
+    case KIRIN_ENOMEM: return "out of memory";
+    case KIRIN_ECUDA: return "CUDA runtime error";
+    case KIRIN_ENONFINITE: return "non-finite particle data";
+    case KIRIN_ETIMEOUT: return "device wait timed out";
+    case KIRIN_ESTATE: return "call out of order";
+    default: return "unknown error";
+    }
+}
+
+const char *kirin_last_error(const kirin_ctx *ctx) { return ctx ? ctx->msg : "no context"; }
+
+int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
+{
+    if (!out || !cfg)
+        return KIRIN_EINVAL;
+    *out = nullptr;
+    if (n_max < 1 || n_max > (int64_t)INT32_MAX - 256)
+        return KIRIN_EINVAL;
+    if (check_params(cfg->eps, cfg->G, cfg->r_min, cfg->prec))
+        return KIRIN_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return KIRIN_ECUDA;
+    }
+    DeviceGuard dg(cfg->device);
+    if (!dg.ok)
+        return KIRIN_ECUDA;
+    kirin_ctx *c = new (std::nothrow) kirin_ctx();
+    if (!c)
+        return KIRIN_ENOMEM;
+    c->device = cfg->device;
+    c->n_max = n_max;
+    c->n_img = round_up(n_max, TILE_J);
+    c->eps = cfg->eps;
+    c->G = cfg->G;
+    c->r_min = cfg->r_min;
+    c->prec = cfg->prec;
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (cfg->stream) {
+        c->stream = (cudaStream_t)cfg->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return KIRIN_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    const size_t n = (size_t)n_max;
+    bool ok = true;
+    auto dalloc = [&](void **p, size_t bytes) {
+        if (ok && cudaMalloc(p, bytes) != cudaSuccess)
+            ok = false;
+    };
+    dalloc((void **)&c->bm, n * sizeof(double));
+    dalloc((void **)&c->bx, 3 * n * sizeof(double));
+    dalloc((void **)&c->bv, 3 * n * sizeof(double));
+    dalloc((void **)&c->ba, 3 * n * sizeof(double));
+    dalloc((void **)&c->bj, 3 * n * sizeof(double));
+    dalloc((void **)&c->bt, n * sizeof(double));
+    dalloc((void **)&c->bdt, n * sizeof(double));
+    dalloc((void **)&c->xp, 3 * n * sizeof(double));
+    dalloc((void **)&c->vp, 3 * n * sizeof(double));
+    dalloc((void **)&c->jm, (size_t)c->n_img * sizeof(JMixed));
+    dalloc((void **)&c->jd, (size_t)c->n_img * sizeof(JF64));
+    dalloc((void **)&c->d_ilist, n * sizeof(int32_t));
+    dalloc((void **)&c->d_acc, 3 * n * sizeof(double));
+    dalloc((void **)&c->d_jerk, 3 * n * sizeof(double));
+    dalloc((void **)&c->d_pot, n * sizeof(double));
+    dalloc((void **)&c->d_err, sizeof(unsigned));
+    dalloc((void **)&c->d_scal, 4 * sizeof(double));
+    dalloc((void **)&c->d_count, sizeof(int32_t));
+    if (ok && cudaMallocHost((void **)&c->h_ilist, n * sizeof(int32_t)) != cudaSuccess)
+        ok = false;
+    if (ok && cudaMallocHost((void **)&c->h_scal, 4 * sizeof(double)) != cudaSuccess)
+        ok = false;
+    if (ok && cudaMallocHost((void **)&c->h_count, sizeof(int32_t)) != cudaSuccess)
+        ok = false;
+    if (ok && cudaMallocHost((void **)&c->h_err, sizeof(unsigned)) != cudaSuccess)
+        ok = false;
+    if (ok && cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream) != cudaSuccess)
+        ok = false;
+    if (ok && cudaMemsetAsync(c->bt, 0, n * sizeof(double), c->stream) != cudaSuccess)
+        ok = false;
+    if (ok && cudaStreamSynchronize(c->stream) != cudaSuccess)
+        ok = false;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return KIRIN_ENOMEM;
+    }
+    *out = c;
+    return KIRIN_OK;
+}
+
+int kirin_finalize(kirin_ctx *ctx)
+{
+    if (!ctx)
+        return KIRIN_OK;
+    DeviceGuard dg(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+    return KIRIN_OK;
+}
+
+int kirin_query(const kirin_ctx *ctx, int64_t *n_max, int32_t *tile_i, int32_t *tile_j)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (n_max)
+        *n_max = ctx->n_max;
+    if (tile_i)
+        *tile_i = (ctx->prec == KIRIN_MIXED ? 2 : 1) * FORCE_THREADS;
+    if (tile_j)
+        *tile_j = TILE_J;
+    return KIRIN_OK;
+}
+
+int kirin_set_params(kirin_ctx *ctx, double eps, double G, double r_min, int32_t prec)
+{
+    if (!ctx || check_params(eps, G, r_min, prec))
+        return KIRIN_EINVAL;
+    ctx->eps = eps;
+    ctx->G = G;
+    ctx->r_min = r_min;
+    ctx->prec = prec;
+    return KIRIN_OK;
+}
+
+int kirin_set_stream(kirin_ctx *ctx, void *stream)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->own_stream) {
+        cudaStreamDestroy(ctx->stream);
+        ctx->own_stream = false;
+    }
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        CK(ctx, cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    return KIRIN_OK;
+}
+
+int kirin_set_launch(kirin_ctx *ctx, int32_t groups, int32_t n_split)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (groups == 0 && n_split == 0) {
+        ctx->fix_groups = ctx->fix_split = 0;
+        return KIRIN_OK;
+    }
+    if ((groups != 1 && groups != 2 && groups != 4 && groups != 8) || n_split < 1 || n_split > MAX_SPLIT)
+        return KIRIN_EINVAL;
+    ctx->fix_groups = groups;
+    ctx->fix_split = n_split;
+    return KIRIN_OK;
+}
+
+int kirin_get_launch(kirin_ctx *ctx, int64_t n_i, int32_t *groups, int32_t *n_split)
+{
+    if (!ctx || n_i < 0)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    const int ntiles = (int)((std::max<int64_t>(ctx->n_j, 1) + TILE_J - 1) / TILE_J);
+    const Shape s = choose_shape(ctx, n_i, ntiles, ctx->prec, MODE_ACC_JERK_POT, guard_on(ctx));
+    if (groups)
+        *groups = s.groups;
+    if (n_split)
+        *n_split = s.n_split;
+    return KIRIN_OK;
+}
+
+int kirin_set_j_particles(kirin_ctx *ctx, int64_t first, int64_t n, const double *m, const double *x,
+                          const double *v, const double *a, const double *jerk, const double *t0)
+{
+    if (!ctx || !m || !x || !v || first < 0 || n < 0 || first + n > ctx->n_max)
+        return set_msg(ctx, KIRIN_EINVAL, "set_j_particles: bad range or NULL array");
+    if (n == 0)
+        return KIRIN_OK;
+    if (!all_finite(m, n) || !all_finite(x, 3 * n) || !all_finite(v, 3 * n) ||
+        (a && !all_finite(a, 3 * n)) || (jerk && !all_finite(jerk, 3 * n)) || (t0 && !all_finite(t0, n)))
+        return set_msg(ctx, KIRIN_ENONFINITE, "set_j_particles: NaN or Inf in input");
+    DeviceGuard dg(ctx->device);
+    const size_t f = (size_t)first, nn = (size_t)n;
+    cudaStream_t s = ctx->stream;
+    CK(ctx, cudaMemcpyAsync(ctx->bm + f, m, nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaMemcpyAsync(ctx->bx + 3 * f, x, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaMemcpyAsync(ctx->bv + 3 * f, v, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (a)
+        CK(ctx, cudaMemcpyAsync(ctx->ba + 3 * f, a, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    else
+        CK(ctx, cudaMemsetAsync(ctx->ba + 3 * f, 0, 3 * nn * sizeof(double), s));
+    if (jerk)
+        CK(ctx, cudaMemcpyAsync(ctx->bj + 3 * f, jerk, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    else
+        CK(ctx, cudaMemsetAsync(ctx->bj + 3 * f, 0, 3 * nn * sizeof(double), s));
+    if (t0)
+        CK(ctx, cudaMemcpyAsync(ctx->bt + f, t0, nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    else
+        CK(ctx, cudaMemsetAsync(ctx->bt + f, 0, nn * sizeof(double), s));
+    // host sources may be reused as soon as we return
+    CK(ctx, cudaStreamSynchronize(s));
+    ctx->n_hi = std::max(ctx->n_hi, first + n);
+    ctx->n_j = std::max(ctx->n_j, first + n);
+    ctx->pred_mode = 0;
+    ctx->images_dirty = true;
+    ctx->hermite_ready = false;
+    return KIRIN_OK;
+}
+
+int kirin_set_j_particles_dev(kirin_ctx *ctx, int64_t first, int64_t n, const double *m,
+                              const double *x, const double *v, const double *a, const double *jerk,
+                              const double *t0)
+{
+    if (!ctx || !m || !x || !v || first < 0 || n < 0 || first + n > ctx->n_max)
+        return set_msg(ctx, KIRIN_EINVAL, "set_j_particles_dev: bad range or NULL array");
+    if (n == 0)
+        return KIRIN_OK;
+    DeviceGuard dg(ctx->device);
+    CK(ctx, launch_scatter_state((int)first, (int)n, m, x, v, a, jerk, t0, ctx->bm, ctx->bx, ctx->bv,
+                                 ctx->ba, ctx->bj, ctx->bt, ctx->d_err, ctx->stream));
+    ctx->n_hi = std::max(ctx->n_hi, first + n);
+    ctx->n_j = std::max(ctx->n_j, first + n);
+    ctx->pred_mode = 0;
+    ctx->images_dirty = true;
+    ctx->hermite_ready = false;
+    return KIRIN_OK;
+}
+
+int kirin_set_nj(kirin_ctx *ctx, int64_t n_j)
+{
+    if (!ctx || n_j < 0 || n_j > ctx->n_hi)
+        return set_msg(ctx, KIRIN_EINVAL, "set_nj: n_j outside [0, highest index set]");
+    ctx->n_j = n_j;
+    ctx->images_dirty = true;
+    return KIRIN_OK;
+}
+
+int kirin_predict(kirin_ctx *ctx, double t)
+{
+    if (!ctx || !isfinite(t))
+        return KIRIN_EINVAL;
+    if (ctx->n_j == 0)
+        return set_msg(ctx, KIRIN_ESTATE, "predict: no particles");
+    ctx->pred_mode = 1;
+    ctx->pred_t = t;
+    ctx->images_dirty = true;
+    return KIRIN_OK;
+}
+
+int kirin_compute_forces(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (ctx->n_j == 0)
+        return set_msg(ctx, KIRIN_ESTATE, "compute_forces: no particles");
+    if (!i_list)
+        n_i = ctx->n_j;
+    if (n_i < 0 || n_i > ctx->n_max)
+        return set_msg(ctx, KIRIN_EINVAL, "compute_forces: n_i out of range");
+    DeviceGuard dg(ctx->device);
+    const int32_t *d_list = nullptr;
+    if (i_list) {
+        for (int64_t k = 0; k < n_i; ++k)
+            if (i_list[k] < 0 || i_list[k] >= ctx->n_j)
+                return set_msg(ctx, KIRIN_EINVAL, "compute_forces: i_list[%lld] = %d outside [0, %lld)",
+                               (long long)k, i_list[k], (long long)ctx->n_j);
+        // the previous upload may still be in flight from the pinned buffer
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        memcpy(ctx->h_ilist, i_list, (size_t)n_i * sizeof(int32_t));
+        CK(ctx, cudaMemcpyAsync(ctx->d_ilist, ctx->h_ilist, (size_t)n_i * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, ctx->stream));
+        d_list = ctx->d_ilist;
+    }
+    int rc = ensure_images(ctx);
+    if (rc)
+        return rc;
+    rc = run_force(ctx, n_i, d_list, (int)ctx->n_j, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
+    if (rc)
+        return rc;
+    ctx->pending = true;
+    ctx->pending_n = n_i;
+    return KIRIN_OK;
+}
+
+int kirin_get_acc_jerk_pot(kirin_ctx *ctx, double *acc, double *jerk, double *pot)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (!ctx->pending)
+        return set_msg(ctx, KIRIN_ESTATE, "get_acc_jerk_pot: no pending compute_forces");
+    DeviceGuard dg(ctx->device);
+    const size_t n = (size_t)ctx->pending_n;
+    if (acc)
+        CK(ctx, cudaMemcpyAsync(acc, ctx->d_acc, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (jerk)
+        CK(ctx, cudaMemcpyAsync(jerk, ctx->d_jerk, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (pot)
+        CK(ctx, cudaMemcpyAsync(pot, ctx->d_pot, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    const int rc = read_device_errors(ctx);
+    ctx->pending = false;
+    return rc;
+}
+
+int kirin_compute_forces_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list, double *acc,
+                             double *jerk, double *pot)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (ctx->n_j == 0)
+        return set_msg(ctx, KIRIN_ESTATE, "compute_forces_dev: no particles");
+    if (!i_list)
+        n_i = ctx->n_j;
+    if (n_i < 0 || n_i > ctx->n_max)
+        return set_msg(ctx, KIRIN_EINVAL, "compute_forces_dev: n_i out of range");
+    DeviceGuard dg(ctx->device);
+    int rc = ensure_images(ctx);
+    if (rc)
+        return rc;
+    return run_force(ctx, n_i, i_list, (int)ctx->n_j, MODE_ACC_JERK_POT, acc, jerk, pot);
+}
+
+int kirin_sync(kirin_ctx *ctx)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    return read_device_errors(ctx);
+}
+
+int kirin_energy(kirin_ctx *ctx, const double *v, double *kin, double *pot)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (ctx->n_j == 0)
+        return set_msg(ctx, KIRIN_ESTATE, "energy: no particles");
+    DeviceGuard dg(ctx->device);
+    int rc = ensure_images(ctx);
+    if (rc)
+        return rc;
+    const int n = (int)ctx->n_j;
+    rc = run_force(ctx, n, nullptr, n, MODE_ACC_POT, ctx->d_acc, nullptr, ctx->d_pot);
+    if (rc)
+        return rc;
+    const double *dv = ctx->vp;
+    if (v) {
+        if (!all_finite(v, 3 * (int64_t)n))
+            return set_msg(ctx, KIRIN_ENONFINITE, "energy: NaN or Inf in v");
+        CK(ctx, cudaMemcpyAsync(ctx->d_jerk, v, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        dv = ctx->d_jerk;
+    }
+    CK(ctx, launch_energy(n, ctx->bm, dv, ctx->d_pot, ctx->d_scal + 1, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    rc = read_device_errors(ctx);
+    if (rc)
+        return rc;
+    if (kin)
+        *kin = ctx->h_scal[1];
+    if (pot)
+        *pot = ctx->h_scal[2];
+    ctx->pending = false;
+    return KIRIN_OK;
+}
+
+// ---- Hermite integrator -----------------------------------------------------
+
+int kirin_hermite_init(kirin_ctx *ctx, double t, double eta, double dt_min, double dt_max)
+{
+    if (!ctx || !isfinite(t) || !(eta > 0) || !(dt_min > 0) || !(dt_max >= dt_min))
+        return KIRIN_EINVAL;
+    if (ctx->n_j == 0)
+        return set_msg(ctx, KIRIN_ESTATE, "hermite_init: no particles");
+    DeviceGuard dg(ctx->device);
+    ctx->pred_mode = 0;
+    ctx->images_dirty = true;
+    int rc = ensure_images(ctx);
+    if (rc)
+        return rc;
+    const int n = (int)ctx->n_j;
+    rc = run_force(ctx, n, nullptr, n, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
+    if (rc)
+        return rc;
+    CK(ctx, launch_hermite_init(n, t, ctx->d_acc, ctx->d_jerk, dt_min, dt_max, ctx->ba, ctx->bj, ctx->bt,
+                                ctx->bdt, ctx->stream));
+    rc = read_device_errors(ctx);
+    if (rc)
+        return rc;
+    ctx->eta = eta;
+    ctx->dt_min = dt_min;
+    ctx->dt_max = dt_max;
+    ctx->t_shared = t;
+    ctx->hermite_ready = true;
+    ctx->pending = false;
+    return KIRIN_OK;
+}
+
+int kirin_hermite_block_step(kirin_ctx *ctx, double t_end, double *t_now, int64_t *n_active)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (!ctx->hermite_ready)
+        return set_msg(ctx, KIRIN_ESTATE, "hermite_block_step: call kirin_hermite_init first");
+    DeviceGuard dg(ctx->device);
+    const int n = (int)ctx->n_j;
+    CK(ctx, launch_block_select(n, ctx->bt, ctx->bdt, t_end, ctx->d_ilist, ctx->d_scal, ctx->d_count,
+                                ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->h_count, ctx->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const double t_next = ctx->h_scal[0];
+    const int n_act = *ctx->h_count;
+    if (t_now)
+        *t_now = t_next;
+    if (n_active)
+        *n_active = n_act;
+    if (n_act == 0)
+        return KIRIN_OK;
+    ctx->pred_mode = 1;
+    ctx->pred_t = t_next;
+    ctx->images_dirty = true;
+    int rc = ensure_images(ctx);
+    if (rc)
+        return rc;
+    rc = run_force(ctx, n_act, ctx->d_ilist, n, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
+    if (rc)
+        return rc;
+    CK(ctx, launch_hermite_correct(n_act, ctx->d_ilist, t_next, ctx->eta, ctx->dt_min, ctx->dt_max, 1,
+                                   ctx->xp, ctx->vp, ctx->d_acc, ctx->d_jerk, ctx->bx, ctx->bv, ctx->ba,
+                                   ctx->bj, ctx->bt, ctx->bdt, ctx->stream));
+    ctx->images_dirty = true;  // base state moved
+    ctx->pending = false;
+    return KIRIN_OK;
+}
+
+int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *n_steps, double *n_pairs)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    int64_t steps = 0;
+    double pairs = 0.0;
+    while (max_steps <= 0 || steps < max_steps) {
+        double t_now = 0;
+        int64_t n_act = 0;
+        const int rc = kirin_hermite_block_step(ctx, t_end, &t_now, &n_act);
+        if (rc)
+            return rc;
+        if (n_act == 0)
+            break;
+        ++steps;
+        pairs += (double)n_act * (double)ctx->n_j;
+    }
+    if (n_steps)
+        *n_steps = steps;
+    if (n_pairs)
+        *n_pairs = pairs;
+    DeviceGuard dg(ctx->device);
+    return read_device_errors(ctx);
+}
+
+int kirin_hermite_shared_step(kirin_ctx *ctx, double dt)
+{
+    if (!ctx || !(dt > 0))
+        return KIRIN_EINVAL;
+    if (!ctx->hermite_ready)
+        return set_msg(ctx, KIRIN_ESTATE, "hermite_shared_step: call kirin_hermite_init first");
+    DeviceGuard dg(ctx->device);
+    const int n = (int)ctx->n_j;
+    const double t_next = ctx->t_shared + dt;
+    ctx->pred_mode = 1;
+    ctx->pred_t = t_next;
+    ctx->images_dirty = true;
+    int rc = ensure_images(ctx);
+    if (rc)
+        return rc;
+    rc = run_force(ctx, n, nullptr, n, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
+    if (rc)
+        return rc;
+    CK(ctx, launch_hermite_correct(n, nullptr, t_next, ctx->eta, ctx->dt_min, ctx->dt_max, 0, ctx->xp,
+                                   ctx->vp, ctx->d_acc, ctx->d_jerk, ctx->bx, ctx->bv, ctx->ba, ctx->bj,
+                                   ctx->bt, ctx->bdt, ctx->stream));
+    ctx->t_shared = t_next;
+    ctx->images_dirty = true;
+    ctx->pending = false;
+    return read_device_errors(ctx);
+}
+
+int kirin_get_state(kirin_ctx *ctx, double *x, double *v, double *a, double *jerk, double *t, double *dt)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    const size_t n = (size_t)ctx->n_j;
+    cudaStream_t s = ctx->stream;
+    if (x)
+        CK(ctx, cudaMemcpyAsync(x, ctx->bx, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (v)
+        CK(ctx, cudaMemcpyAsync(v, ctx->bv, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (a)
+        CK(ctx, cudaMemcpyAsync(a, ctx->ba, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (jerk)
+        CK(ctx, cudaMemcpyAsync(jerk, ctx->bj, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (t)
+        CK(ctx, cudaMemcpyAsync(t, ctx->bt, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (dt)
+        CK(ctx, cudaMemcpyAsync(dt, ctx->bdt, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return read_device_errors(ctx);
+}
+
+// ---- device particle sets -------------------------------------------------------
+
+int kirin_accel_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x, double *acc, double *pot)
+{
+    if (!ctx || !m || !x || n < 0 || n > ctx->n_max)
+        return set_msg(ctx, KIRIN_EINVAL, "accel_dev: bad size or NULL array");
+    if (n == 0)
+        return KIRIN_OK;
+    DeviceGuard dg(ctx->device);
+    const int64_t n_pad = round_up(n, TILE_J);
+    CK(ctx, launch_pack_xm((int)n, (int)n_pad, m, x, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
+    ctx->images_dirty = true;  // the images no longer show the context's particles
+    return run_force(ctx, n, nullptr, (int)n, MODE_ACC_POT, acc, nullptr, pot);
+}
+
+int kirin_accel_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x, const double *g,
+                            double *gx, double *gm)
+{
+    if (!ctx || !m || !x || !g || n < 0 || n > ctx->n_max)
+        return set_msg(ctx, KIRIN_EINVAL, "accel_adjoint_dev: bad size or NULL array");
+    if (n == 0)
+        return KIRIN_OK;
+    DeviceGuard dg(ctx->device);
+    const int64_t n_pad = round_up(n, TILE_J);
+    // images of (x, m) with g in the velocity slots
+    CK(ctx, launch_predict_pack((int)n, (int)n_pad, 0.0, 0, m, x, g, nullptr, nullptr, nullptr, nullptr,
+                                nullptr, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
+    ctx->images_dirty = true;
+    return run_force(ctx, n, nullptr, (int)n, MODE_ADJOINT, nullptr, gx, gm);
+}
+
+}  // extern "C"

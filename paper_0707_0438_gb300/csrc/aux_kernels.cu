@@ -1,0 +1,409 @@
+// O(N) kernels around the direct sum: the j-split reduction (Sect. 3.2), the
+// predictor that builds the j-particle images (Sect. 3.1, done on the device
+// instead of the host), energy sums (Eq. 2), and the Hermite corrector and
+// block-step scheduler (Sect. 3, Sect. 3.1).  All FP64.
+#include <cuda_runtime.h>
+
+#include "kirin_internal.cuh"
+
+namespace kirin {
+namespace {
+
+constexpr int AUX_THREADS = 256;
+
+inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// Sum the n_split partial results of every (i, quantity) in split order and
+// write the scaled outputs (acc, jerk: G * sum; pot: -G * sum).
+__global__ void k_reduce_splits(const ForceArgs A)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.n_i)
+        return;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        double sum = 0.0;
+        for (int y = 0; y < A.n_split; ++y)
+            sum += A.partial[((size_t)y * 7 + q) * A.n_i_pad + k];
+        if (q < 3) {
+            if (A.acc)
+                A.acc[3 * (size_t)k + q] = A.G * sum;
+        } else if (q < 6) {
+            if (A.jerk)
+                A.jerk[3 * (size_t)k + (q - 3)] = A.G * sum;
+        } else if (A.pot) {
+            A.pot[k] = -A.G * sum;
+        }
+    }
+}
+
+__device__ __forceinline__ void split_ds(double v, float &hi, float &lo)
+{
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+}
+
+__device__ __forceinline__ void write_images(int k, double X, double Y, double Z, double M, double VX,
+                                             double VY, double VZ, JMixed *jm, JF64 *jd)
+{
+    if (jm) {
+        float xh, xl, yh, yl, zh, zl;
+        split_ds(X, xh, xl);
+        split_ds(Y, yh, yl);
+        split_ds(Z, zh, zl);
+        const float m = __double2float_rn(M);
+        const float vx = __double2float_rn(VX), vy = __double2float_rn(VY), vz = __double2float_rn(VZ);
+        JMixed r;
+        r.q[0] = make_float4(xh, xh, yh, yh);
+        r.q[1] = make_float4(zh, zh, m, m);
+        r.q[2] = make_float4(xl, xl, yl, yl);
+        r.q[3] = make_float4(zl, zl, vx, vx);
+        r.q[4] = make_float4(vy, vy, vz, vz);
+        jm[k] = r;
+    }
+    if (jd) {
+        JF64 r;
+        r.q[0] = make_double2(X, Y);
+        r.q[1] = make_double2(Z, M);
+        r.q[2] = make_double2(VX, VY);
+        r.q[3] = make_double2(VZ, 0.0);
+        jd[k] = r;
+    }
+}
+
+// Predictor x_p = x + v dt + a dt^2/2 + jerk dt^3/6, v_p = v + a dt + jerk dt^2/2
+// (dt = t - t0), then the j images; records [n, n_pad) are zero-mass padding.
+__global__ void k_predict_pack(int n, int n_pad, double t, int predict, const double *__restrict__ m,
+                               const double *__restrict__ x, const double *__restrict__ v,
+                               const double *__restrict__ a, const double *__restrict__ jk,
+                               const double *__restrict__ t0, double *xp, double *vp, JMixed *jm,
+                               JF64 *jd, unsigned *err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_pad)
+        return;
+    if (k >= n) {
+        write_images(k, PAD_POS, PAD_POS, PAD_POS, 0.0, 0.0, 0.0, 0.0, jm, jd);
+        return;
+    }
+    double X[3], V[3];
+    if (predict) {
+        const double dt = t - t0[k];
+        const double dt2 = dt * dt / 2.0, dt3 = dt * dt * dt / 6.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t o = 3 * (size_t)k + c;
+            X[c] = x[o] + v[o] * dt + a[o] * dt2 + jk[o] * dt3;
+            V[c] = v[o] + a[o] * dt + jk[o] * dt2;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            X[c] = x[3 * (size_t)k + c];
+            V[c] = v[3 * (size_t)k + c];
+        }
+    }
+    if (xp) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xp[3 * (size_t)k + c] = X[c];
+            vp[3 * (size_t)k + c] = V[c];
+        }
+    }
+    if (!(isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2]) && isfinite(V[0]) && isfinite(V[1]) &&
+          isfinite(V[2]) && isfinite(m[k])))
+        atomicOr(err, ERR_NONFINITE);
+    write_images(k, X[0], X[1], X[2], m[k], V[0], V[1], V[2], jm, jd);
+}
+
+// Images from (m, x) only (velocities zero), for acceleration-only clients.
+__global__ void k_pack_xm(int n, int n_pad, const double *__restrict__ m, const double *__restrict__ x,
+                          JMixed *jm, JF64 *jd, unsigned *err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_pad)
+        return;
+    if (k >= n) {
+        write_images(k, PAD_POS, PAD_POS, PAD_POS, 0.0, 0.0, 0.0, 0.0, jm, jd);
+        return;
+    }
+    const double X = x[3 * (size_t)k], Y = x[3 * (size_t)k + 1], Z = x[3 * (size_t)k + 2];
+    if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(m[k])))
+        atomicOr(err, ERR_NONFINITE);
+    write_images(k, X, Y, Z, m[k], 0.0, 0.0, 0.0, jm, jd);
+}
+
+// Device-to-device upload of particles [first, first + n) into the base state.
+__global__ void k_scatter_state(int first, int n, const double *m, const double *x, const double *v,
+                                const double *a, const double *jk, const double *t0, double *bm,
+                                double *bx, double *bv, double *ba, double *bj, double *bt0,
+                                unsigned *err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n)
+        return;
+    const size_t d = (size_t)first + k;
+    bool fin = isfinite(m[k]);
+    bm[d] = m[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double xc = x[3 * (size_t)k + c], vc = v[3 * (size_t)k + c];
+        const double ac = a ? a[3 * (size_t)k + c] : 0.0;
+        const double jc = jk ? jk[3 * (size_t)k + c] : 0.0;
+        fin = fin && isfinite(xc) && isfinite(vc) && isfinite(ac) && isfinite(jc);
+        bx[3 * d + c] = xc;
+        bv[3 * d + c] = vc;
+        ba[3 * d + c] = ac;
+        bj[3 * d + c] = jc;
+    }
+    const double tt = t0 ? t0[k] : 0.0;
+    bt0[d] = tt;
+    if (!(fin && isfinite(tt)))
+        atomicOr(err, ERR_NONFINITE);
+}
+
+// One CTA: K = sum 1/2 m |v|^2 and W = 1/2 sum m phi, fixed order (deterministic).
+__global__ void __launch_bounds__(1024) k_energy(int n, const double *__restrict__ m,
+                                                 const double *__restrict__ v,
+                                                 const double *__restrict__ pot, double *out)
+{
+    __shared__ double sk[1024], sw[1024];
+    double kk = 0.0, ww = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double vx = v[3 * (size_t)i], vy = v[3 * (size_t)i + 1], vz = v[3 * (size_t)i + 2];
+        kk += 0.5 * m[i] * (vx * vx + vy * vy + vz * vz);
+        ww += 0.5 * m[i] * pot[i];
+    }
+    sk[threadIdx.x] = kk;
+    sw[threadIdx.x] = ww;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sk[threadIdx.x] += sk[threadIdx.x + w];
+            sw[threadIdx.x] += sw[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sk[0];
+        out[1] = sw[0];
+    }
+}
+
+__device__ __forceinline__ double norm3(const double *p)
+{
+    return sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+}
+
+// Largest power of two <= d within [dt_min, dt_max].
+__device__ __forceinline__ double quantise_down(double d, double dt_min, double dt_max)
+{
+    double q = dt_max;
+    while (q > d && q > dt_min)
+        q *= 0.5;
+    return q;
+}
+
+__global__ void k_hermite_init(int n, double t, const double *acc, const double *jerk, double dt_min,
+                               double dt_max, double *ba, double *bj, double *bt, double *bdt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n)
+        return;
+    double a[3], j[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[c] = acc[3 * (size_t)k + c];
+        j[c] = jerk[3 * (size_t)k + c];
+        ba[3 * (size_t)k + c] = a[c];
+        bj[3 * (size_t)k + c] = j[c];
+    }
+    bt[k] = t;
+    bdt[k] = quantise_down(0.01 * norm3(a) / norm3(j), dt_min, dt_max);
+}
+
+// One CTA of 1024 threads: t_next = min(t_i + dt_i) and the ordered list of
+// i with t_i + dt_i == t_next (empty if t_next > t_end).
+__global__ void __launch_bounds__(1024) k_block_select(int n, const double *__restrict__ bt,
+                                                       const double *__restrict__ bdt, double t_end,
+                                                       int32_t *ilist, double *t_next_out,
+                                                       int32_t *count_out)
+{
+    __shared__ double smin[1024];
+    __shared__ int scan[1024];
+    __shared__ int base;
+    double mn = INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        mn = fmin(mn, bt[i] + bdt[i]);
+    smin[threadIdx.x] = mn;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
+        __syncthreads();
+    }
+    const double tn = smin[0];
+    if (threadIdx.x == 0) {
+        base = 0;
+        *t_next_out = tn;
+    }
+    __syncthreads();
+    if (!(tn <= t_end)) {
+        if (threadIdx.x == 0)
+            *count_out = 0;
+        return;
+    }
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const int flag = (i < n && bt[i] + bdt[i] == tn) ? 1 : 0;
+        scan[threadIdx.x] = flag;
+        __syncthreads();
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            const int add = threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
+            __syncthreads();
+            scan[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (flag)
+            ilist[base + scan[threadIdx.x] - 1] = i;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1)
+            base += scan[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *count_out = base;
+}
+
+// Hermite corrector for the block (Sect. 3): a2, a3 from the two (a, jerk)
+// pairs, corrected x and v, and (update_dt) Aarseth's step on the
+// power-of-two ladder.
+__global__ void k_hermite_correct(int n_act, const int32_t *__restrict__ ilist, double t_next,
+                                  double eta, double dt_min, double dt_max, int update_dt,
+                                  const double *__restrict__ xp, const double *__restrict__ vp,
+                                  const double *__restrict__ acc, const double *__restrict__ jerk,
+                                  double *bx, double *bv, double *ba, double *bj, double *bt, double *bdt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_act)
+        return;
+    const size_t i = ilist ? (size_t)ilist[k] : (size_t)k;
+    const double dt = t_next - bt[i];
+    double a2[3], a3[3], a1[3], j1[3], a2e[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
+        a1[c] = acc[3 * (size_t)k + c];
+        j1[c] = jerk[3 * (size_t)k + c];
+        a2[c] = (-6.0 * (a0 - a1[c]) - dt * (4.0 * j0 + 2.0 * j1[c])) / (dt * dt);
+        a3[c] = (12.0 * (a0 - a1[c]) + 6.0 * dt * (j0 + j1[c])) / (dt * dt * dt);
+        const double dt4 = dt * dt * dt * dt;
+        bx[3 * i + c] = xp[3 * i + c] + a2[c] * dt4 / 24.0 + a3[c] * dt4 * dt / 120.0;
+        bv[3 * i + c] = vp[3 * i + c] + a2[c] * dt * dt * dt / 6.0 + a3[c] * dt4 / 24.0;
+        ba[3 * i + c] = a1[c];
+        bj[3 * i + c] = j1[c];
+        a2e[c] = a2[c] + dt * a3[c];
+    }
+    bt[i] = t_next;
+    if (update_dt) {
+        const double na = norm3(a1), nj = norm3(j1), n2 = norm3(a2e), n3 = norm3(a3);
+        const double raw = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
+        double q;
+        if (raw < dt) {
+            q = dt;
+            while (q > raw && q > dt_min)
+                q *= 0.5;
+        } else if (raw >= 2.0 * dt && 2.0 * dt <= dt_max && fmod(t_next, 2.0 * dt) == 0.0) {
+            q = 2.0 * dt;
+        } else {
+            q = dt;
+        }
+        bdt[i] = fmin(fmax(q, dt_min), dt_max);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_reduce_splits(const ForceArgs &a, cudaStream_t st)
+{
+    if (a.n_i == 0)
+        return cudaSuccess;
+    k_reduce_splits<<<blocks_for(a.n_i, AUX_THREADS), AUX_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_pack(int n, int n_pad, double t, int predict, const double *m,
+                                const double *x, const double *v, const double *a,
+                                const double *jk, const double *t0, double *xp, double *vp,
+                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st)
+{
+    if (n_pad == 0)
+        return cudaSuccess;
+    k_predict_pack<<<blocks_for(n_pad, AUX_THREADS), AUX_THREADS, 0, st>>>(
+        n, n_pad, t, predict, m, x, v, a, jk, t0, xp, vp, jm, jd, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_xm(int n, int n_pad, const double *m, const double *x, JMixed *jm,
+                           JF64 *jd, unsigned *err, cudaStream_t st)
+{
+    if (n_pad == 0)
+        return cudaSuccess;
+    k_pack_xm<<<blocks_for(n_pad, AUX_THREADS), AUX_THREADS, 0, st>>>(n, n_pad, m, x, jm, jd, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_state(int first, int n, const double *m, const double *x,
+                                 const double *v, const double *a, const double *jk,
+                                 const double *t0, double *bm, double *bx, double *bv,
+                                 double *ba, double *bj, double *bt0, unsigned *err,
+                                 cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_scatter_state<<<blocks_for(n, AUX_THREADS), AUX_THREADS, 0, st>>>(first, n, m, x, v, a, jk, t0,
+                                                                       bm, bx, bv, ba, bj, bt0, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(int n, const double *m, const double *v, const double *pot,
+                          double *out2, cudaStream_t st)
+{
+    k_energy<<<1, 1024, 0, st>>>(n, m, v, pot, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hermite_init(int n, double t, const double *acc, const double *jerk,
+                                double dt_min, double dt_max, double *ba, double *bj,
+                                double *bt, double *bdt, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_hermite_init<<<blocks_for(n, AUX_THREADS), AUX_THREADS, 0, st>>>(n, t, acc, jerk, dt_min,
+                                                                      dt_max, ba, bj, bt, bdt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end,
+                                int32_t *ilist, double *t_next_out, int32_t *count_out,
+                                cudaStream_t st)
+{
+    k_block_select<<<1, 1024, 0, st>>>(n, bt, bdt, t_end, ilist, t_next_out, count_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_next, double eta,
+                                   double dt_min, double dt_max, int update_dt,
+                                   const double *xp, const double *vp, const double *acc,
+                                   const double *jerk, double *bx, double *bv, double *ba,
+                                   double *bj, double *bt, double *bdt, cudaStream_t st)
+{
+    if (n_act == 0)
+        return cudaSuccess;
+    k_hermite_correct<<<blocks_for(n_act, AUX_THREADS), AUX_THREADS, 0, st>>>(
+        n_act, ilist, t_next, eta, dt_min, dt_max, update_dt, xp, vp, acc, jerk, bx, bv, ba, bj, bt,
+        bdt);
+    return cudaGetLastError();
+}
+
+}  // namespace kirin

@@ -1,0 +1,308 @@
+// Mixed-precision direct-summation kernel: acceleration, jerk and potential
+// of the active i-particles against every j-particle (Sect. 3, Sect. 3.1,
+// Sect. 3.2), for sm_103a.
+//
+// Design (GB300 rather than the G80 of the paper):
+//  * j-particles stream through shared memory in tiles of TILE_J, fetched by
+//    one thread with 1-D bulk (TMA) copies into a STAGES-deep ring guarded by
+//    mbarriers; the paper's "each thread caches one particle" loop (Sect. 3.1
+//    steps 1-3) becomes an asynchronous copy overlapped with compute.
+//  * Every thread owns two i-particles held in the two lanes of packed FP32x2
+//    registers, so each pair-interaction instruction is one FADD2/FMUL2/FFMA2
+//    for two pairs; j data are stored twice per record so that the broadcast
+//    shared-memory loads deliver {v, v} operands directly.
+//  * Positions are double-single; the separation is formed from the hi and lo
+//    parts before it is rounded to FP32.  The reciprocal square root is the
+//    MUFU instruction.
+//  * Per-thread FP32 partial sums cover at most FLUSH_J j-particles, then are
+//    folded into double-single (hi, lo) accumulators with an error-free
+//    two-sum; jerk is carried as two sums (w/s^3 and (d.w) d/s^5) combined at
+//    each fold.
+//  * The self pair (j = i) is not skipped in the loop: its acceleration and
+//    jerk terms are exact zeros, and its potential term, recomputed with the
+//    same FP32 operations, is subtracted from the compensated accumulator
+//    afterwards (never m/eps in FP32 after the fact).  With eps = 0 the
+//    guarded variant zeroes every pair at zero separation instead (Sect. 3.3.1).
+//  * Small active blocks: GROUPS > 1 splits each tile over thread groups with
+//    a shared-memory reduction, and grid.y > 1 splits the j range over CTAs
+//    whose partial sums are reduced on the device (Sect. 3.2 does this last
+//    sum on the host).
+//  * MODE_ACC_POT drops the jerk (the force-only evaluation of Sect. 4.3).
+//    MODE_ADJOINT is the reverse-mode derivative (no counterpart in the
+//    paper): the velocity slots of each record carry g = dL/da and the same
+//    seven sums become dL/dx_k = G sum_j [w/s^3 - 3 (d.w) d/s^5] with
+//    w = m_k g_j - m_j g_k (jerk slots) and dL/dm_k = -G sum_j g_j.d/s^3
+//    (potential slot); every self-pair term of the adjoint is an exact zero.
+#include <cuda_runtime.h>
+
+#include "kirin_internal.cuh"
+#include "pair_mixed.cuh"
+#include "tma.cuh"
+
+namespace kirin {
+namespace {
+
+constexpr int FLUSH_J = 256;  // j-particles per FP32 partial sum and thread
+
+__device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, double val)
+{
+    if (k >= A.n_i)
+        return;
+    if (A.n_split > 1) {
+        A.partial[((size_t)blockIdx.y * 7 + q) * A.n_i_pad + k] = val;
+        return;
+    }
+    if (q < 3) {
+        if (A.acc)
+            A.acc[3 * (size_t)k + q] = A.G * val;
+    } else if (q < 6) {
+        if (A.jerk)
+            A.jerk[3 * (size_t)k + (q - 3)] = A.G * val;
+    } else {
+        if (A.pot)
+            A.pot[k] = -A.G * val;
+    }
+}
+
+template <int GROUPS, bool GUARD, int MODE>
+__global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArgs A)
+{
+    constexpr bool ADJ = MODE == MODE_ADJOINT;
+    constexpr int GT = FORCE_THREADS / GROUPS;  // threads per j-group
+    constexpr int I_CTA = 2 * GT;               // i-particles per CTA
+    constexpr int JG = TILE_J / GROUPS;         // j per group and tile
+    constexpr uint32_t TILE_BYTES = TILE_J * sizeof(JMixed);
+    static_assert(GT >= 32, "a warp must read one j at a time (broadcast loads)");
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    JMixed *tiles = reinterpret_cast<JMixed *>(smem_raw);
+    __shared__ __align__(8) uint64_t bars[STAGES];
+
+    const int tid = threadIdx.x;
+    const int g = tid / GT;
+    const int s = tid - g * GT;
+    const JMixed *__restrict__ J = static_cast<const JMixed *>(A.jimg);
+
+    // ---- the two i-particles of this thread (lanes x and y) ----
+    int idx[2];
+#pragma unroll
+    for (int L = 0; L < 2; ++L) {
+        const int k = blockIdx.x * I_CTA + s + L * GT;
+        int i = -1;
+        if (k < A.n_i) {
+            i = A.ilist ? A.ilist[k] : k;
+            if (i < 0 || i >= A.n_j) {
+                atomicOr(A.err, ERR_INDEX);
+                i = -1;
+            }
+        }
+        idx[L] = i;
+    }
+    const float eps2f = (float)A.eps2;
+    const float rmin2f = (float)A.rmin2;
+    const IPair I = load_ipair(J + (idx[0] >= 0 ? idx[0] : 0), J + (idx[1] >= 0 ? idx[1] : 0), eps2f, rmin2f);
+
+    // ---- j range of this CTA (grid.y splits the tiles) ----
+    const int y = blockIdx.y;
+    const int tb = (int)(((long long)A.ntiles * y) / A.n_split);
+    const int te = (int)(((long long)A.ntiles * (y + 1)) / A.n_split);
+    const int nt = te - tb;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int st = 0; st < STAGES; ++st)
+            mbar_init(&bars[st], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int st = 0; st < STAGES && st < nt; ++st) {
+            mbar_arrive_expect_tx(&bars[st], TILE_BYTES);
+            bulk_g2s(tiles + st * TILE_J, J + (size_t)(tb + st) * TILE_J, TILE_BYTES, &bars[st]);
+        }
+    }
+
+    Tile7 t;
+    t.zero();
+    Lane7 acc0, acc1;
+    acc0.zero();
+    acc1.zero();
+
+    int since = 0;
+    int k = 0;
+    bool aborted = false;
+    for (; k < nt; ++k) {
+        const int st = k % STAGES;
+        const uint32_t par = (uint32_t)(k / STAGES) & 1u;
+        const bool ok = mbar_wait_bounded(&bars[st], par);
+        if (ok) {
+            const JMixed *__restrict__ T = tiles + st * TILE_J + g * JG;
+#pragma unroll 4
+            for (int jj = 0; jj < JG; ++jj)
+                pair<GUARD, MODE>(T[jj], I, t);
+            since += JG;
+            if (since >= FLUSH_J) {
+                fold<MODE>(t, acc0, acc1);
+                since = 0;
+            }
+        }
+        // every thread learns whether any wait in the CTA timed out
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        if (tid == 0 && k + STAGES < nt) {
+            mbar_arrive_expect_tx(&bars[st], TILE_BYTES);
+            bulk_g2s(tiles + st * TILE_J, J + (size_t)(tb + k + STAGES) * TILE_J, TILE_BYTES, &bars[st]);
+        }
+    }
+    if (aborted) {
+        // let every copy already issued land before the CTA's shared memory goes away
+        if (tid == 0) {
+            const int last = min(nt, k + STAGES);
+            for (int kk = k; kk < last; ++kk) {
+                if (!mbar_wait_bounded(&bars[kk % STAGES], (uint32_t)(kk / STAGES) & 1u)) {
+                    atomicOr(A.err, ERR_DRAIN);
+                    break;
+                }
+            }
+            atomicOr(A.err, ERR_TIMEOUT);
+        }
+        return;
+    }
+    fold<MODE>(t, acc0, acc1);
+
+    // ---- remove the self pair's potential term where this thread summed it ----
+    if (!ADJ) {
+        const float rs = self_pot_term<GUARD>(1.0f, eps2f, rmin2f);
+        if (rs != 0.f) {
+#pragma unroll
+            for (int L = 0; L < 2; ++L) {
+                const int i = idx[L];
+                if (i < 0)
+                    continue;
+                const int tj = i / TILE_J;
+                const int pos = i - tj * TILE_J;
+                if (tj >= tb && tj < te && pos / JG == g) {
+                    const float m = L == 0 ? I.mk.x : I.mk.y;
+                    const float self = self_pot_term<GUARD>(m, eps2f, rmin2f);
+                    if (L == 0)
+                        two_sum(acc0.h[6], acc0.l[6], -self);
+                    else
+                        two_sum(acc1.h[6], acc1.l[6], -self);
+                }
+            }
+        }
+    }
+
+    double res0[7], res1[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        res0[q] = (double)acc0.h[q] + (double)acc0.l[q];
+        res1[q] = (double)acc1.h[q] + (double)acc1.l[q];
+    }
+
+    if (GROUPS == 1) {
+        const int k0 = blockIdx.x * I_CTA + s;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            write_out(A, q, k0, res0[q]);
+            write_out(A, q, k0 + GT, res1[q]);
+        }
+    } else {
+        __syncthreads();  // all tiles consumed: reuse the ring as reduction space
+        double *red = reinterpret_cast<double *>(smem_raw);  // [GROUPS][7][I_CTA]
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            red[(g * 7 + q) * I_CTA + s] = res0[q];
+            red[(g * 7 + q) * I_CTA + s + GT] = res1[q];
+        }
+        __syncthreads();
+        for (int o = tid; o < 7 * I_CTA; o += FORCE_THREADS) {
+            const int q = o / I_CTA;
+            const int slot = o - q * I_CTA;
+            double sum = 0.0;
+#pragma unroll
+            for (int gg = 0; gg < GROUPS; ++gg)
+                sum += red[(gg * 7 + q) * I_CTA + slot];
+            write_out(A, q, blockIdx.x * I_CTA + slot, sum);
+        }
+    }
+}
+
+template <int GROUPS, bool GUARD, int MODE>
+cudaError_t launch_t(const ForceArgs &a, int n_split, cudaStream_t st)
+{
+    constexpr int I_CTA = 2 * FORCE_THREADS / GROUPS;
+    const int iblocks = (a.n_i + I_CTA - 1) / I_CTA;
+    if (iblocks == 0)
+        return cudaSuccess;
+    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
+    dim3 grid(iblocks, n_split);
+    k_force_mixed<GROUPS, GUARD, MODE><<<grid, FORCE_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int GROUPS, bool GUARD, int MODE>
+int occ_t()
+{
+    int n = 0;
+    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_mixed<GROUPS, GUARD, MODE>,
+                                                  FORCE_THREADS, smem);
+    return n;
+}
+
+template <bool GUARD, int MODE>
+cudaError_t launch_g(const ForceArgs &a, Shape s, cudaStream_t st)
+{
+    switch (s.groups) {
+    case 1: return launch_t<1, GUARD, MODE>(a, s.n_split, st);
+    case 2: return launch_t<2, GUARD, MODE>(a, s.n_split, st);
+    case 4: return launch_t<4, GUARD, MODE>(a, s.n_split, st);
+    case 8: return launch_t<8, GUARD, MODE>(a, s.n_split, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool GUARD, int MODE>
+int occ_g(int groups)
+{
+    switch (groups) {
+    case 1: return occ_t<1, GUARD, MODE>();
+    case 2: return occ_t<2, GUARD, MODE>();
+    case 4: return occ_t<4, GUARD, MODE>();
+    case 8: return occ_t<8, GUARD, MODE>();
+    default: return 0;
+    }
+}
+
+template <int MODE>
+cudaError_t launch_m(const ForceArgs &a, Shape s, bool guard, cudaStream_t st)
+{
+    return guard ? launch_g<true, MODE>(a, s, st) : launch_g<false, MODE>(a, s, st);
+}
+
+}  // namespace
+
+cudaError_t launch_force_mixed(const ForceArgs &a, Shape s, bool guard, int mode, cudaStream_t st)
+{
+    switch (mode) {
+    case MODE_ACC_JERK_POT: return launch_m<MODE_ACC_JERK_POT>(a, s, guard, st);
+    case MODE_ACC_POT: return launch_m<MODE_ACC_POT>(a, s, guard, st);
+    case MODE_ADJOINT: return launch_m<MODE_ADJOINT>(a, s, guard, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int force_mixed_ctas_per_sm(int groups, bool guard, int mode)
+{
+    switch (mode) {
+    case MODE_ACC_JERK_POT: return guard ? occ_g<true, MODE_ACC_JERK_POT>(groups) : occ_g<false, MODE_ACC_JERK_POT>(groups);
+    case MODE_ACC_POT: return guard ? occ_g<true, MODE_ACC_POT>(groups) : occ_g<false, MODE_ACC_POT>(groups);
+    case MODE_ADJOINT: return guard ? occ_g<true, MODE_ADJOINT>(groups) : occ_g<false, MODE_ADJOINT>(groups);
+    default: return 0;
+    }
+}
+
+}  // namespace kirin

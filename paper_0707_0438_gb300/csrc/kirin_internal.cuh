@@ -1,0 +1,111 @@
+// Internal declarations shared by the libkirin translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kirin.h"
+
+namespace kirin {
+
+// ---- j-particle images in HBM ---------------------------------------------
+//
+// Mixed precision: one 80-byte record per j, every scalar stored twice so
+// that a broadcast LDS.128 yields ready-made {v, v} operands for the packed
+// FP32x2 instructions (the two lanes hold two different i-particles).
+//   q[0] = {xh, xh, yh, yh}   q[1] = {zh, zh, m, m}    q[2] = {xl, xl, yl, yl}
+//   q[3] = {zl, zl, vx, vx}   q[4] = {vy, vy, vz, vz}
+// with x = xh + xl (double-single: xh = fl32(x), xl = fl32(x - xh)).
+struct __align__(16) JMixed {
+    float4 q[5];
+};
+// FP64: {x, y}, {z, m}, {vx, vy}, {vz, 0} as double2 (64 bytes).
+struct __align__(16) JF64 {
+    double2 q[4];
+};
+
+// j tile (shared-memory burst) and pipeline depth of the force kernels.
+constexpr int TILE_J = 128;
+constexpr int STAGES = 4;
+constexpr int FORCE_THREADS = 256;
+constexpr int MAX_SPLIT = 1024;
+
+// Padding particle: zero mass, far away (all its contributions are exact zeros).
+constexpr double PAD_POS = 1.0e4;
+
+// Device error bits (ctx->d_err).
+enum : unsigned {
+    ERR_INDEX = 1u,      // i index outside [0, n_j)
+    ERR_TIMEOUT = 2u,    // bounded mbarrier wait gave up
+    ERR_DRAIN = 4u,      // in-flight copies did not land after a timeout
+    ERR_NONFINITE = 8u,  // NaN / Inf in device-uploaded particle data
+};
+
+// Bounded waits: wall-clock limit of one wait, in nanoseconds.
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
+
+// Launch shape of one force evaluation.
+struct Shape {
+    int groups;   // j-groups per CTA (1, 2, 4, 8); i per CTA = 2*256/groups (mixed) or 256/groups (fp64)
+    int n_split;  // CTAs splitting the j range (grid.y)
+};
+
+struct ForceArgs {
+    const void *jimg;       // JMixed* or JF64*, padded to a multiple of TILE_J
+    const int32_t *ilist;   // device, n_i entries; nullptr = identity
+    int n_i;
+    int n_j;
+    int ntiles;             // ceil(n_j / TILE_J)
+    int n_split;
+    double eps2;
+    double rmin2;
+    double G;
+    double *acc;            // final outputs (n_i x 3, n_i x 3, n_i); any may be null
+    double *jerk;
+    double *pot;
+    double *partial;        // [n_split][7][n_i_pad] when n_split > 1
+    int n_i_pad;
+    unsigned *err;
+};
+
+// What a force launch sums (the seven per-i quantities of ForceArgs):
+//  MODE_ACC_JERK_POT: acc, jerk, pot;  MODE_ACC_POT: acc, pot (jerk outputs 0);
+//  MODE_ADJOINT: the velocity slots of the j image hold g = dL/da; the jerk
+//  outputs receive dL/dx and the pot output dL/dm (acc outputs 0).
+enum { MODE_ACC_JERK_POT = 0, MODE_ACC_POT = 1, MODE_ADJOINT = 2 };
+
+// Launchers (force_mixed.cu / force_fp64.cu).
+cudaError_t launch_force_mixed(const ForceArgs &a, Shape s, bool guard, int mode, cudaStream_t st);
+cudaError_t launch_force_fp64(const ForceArgs &a, Shape s, int mode, cudaStream_t st);
+int force_mixed_ctas_per_sm(int groups, bool guard, int mode);
+int force_fp64_ctas_per_sm(int groups, int mode);
+
+// aux_kernels.cu
+cudaError_t launch_reduce_splits(const ForceArgs &a, cudaStream_t st);
+cudaError_t launch_predict_pack(int n, int n_pad, double t, int predict, const double *m,
+                                const double *x, const double *v, const double *a,
+                                const double *jk, const double *t0, double *xp, double *vp,
+                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st);
+cudaError_t launch_pack_xm(int n, int n_pad, const double *m, const double *x, JMixed *jm,
+                           JF64 *jd, unsigned *err, cudaStream_t st);
+cudaError_t launch_scatter_state(int first, int n, const double *m, const double *x,
+                                 const double *v, const double *a, const double *jk,
+                                 const double *t0, double *bm, double *bx, double *bv,
+                                 double *ba, double *bj, double *bt0, unsigned *err,
+                                 cudaStream_t st);
+cudaError_t launch_energy(int n, const double *m, const double *v, const double *pot,
+                          double *out2, cudaStream_t st);
+cudaError_t launch_hermite_init(int n, double t, const double *acc, const double *jerk,
+                                double dt_min, double dt_max, double *ba, double *bj,
+                                double *bt, double *bdt, cudaStream_t st);
+cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end,
+                                int32_t *ilist, double *t_next_out, int32_t *count_out,
+                                cudaStream_t st);
+cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_next, double eta,
+                                   double dt_min, double dt_max, int update_dt,
+                                   const double *xp, const double *vp, const double *acc,
+                                   const double *jerk, double *bx, double *bv, double *ba,
+                                   double *bj, double *bt, double *bdt, cudaStream_t st);
+
+
+}  // namespace kirin

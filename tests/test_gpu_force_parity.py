@@ -1,0 +1,230 @@
+"""GPU parity of the direct sum (acc, jerk, pot) through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0707_0438_gb300 import abi, workloads
+from tests.gpu_util import TOL, assert_parity, errors
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = ["mixed", "fp64"]
+
+
+def _ctx(p, precision, r_min=0.0, n_max=None):
+    k = abi.Kirin(n_max or max(p.n, 1), p.eps, r_min=r_min, precision=precision)
+    k.set_j_particles(p.m, p.x, p.v)
+    return k
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("n", [2, 3, 100, 1000, 1024, 2049, 5000])
+def test_full_evaluation_matches_oracle(kirin_lib, precision, n):
+    """All i against all j, sizes spanning one tile, several tiles and ragged tails."""
+    p = workloads.plummer(n, (1001, n), eps=1.0 / 256.0)
+    with _ctx(p, precision) as k:
+        got = k.forces()
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps)
+    assert_parity(got, ref, precision, f"N={n}")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_single_particle_has_no_force(kirin_lib, precision):
+    p = workloads.plummer(1, 5, eps=0.01)
+    with _ctx(p, precision) as k:
+        acc, jerk, pot = k.forces()
+    assert np.all(acc == 0) and np.all(jerk == 0) and np.all(pot == 0)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("n_i", [1, 31, 32, 127, 511, 4095, 4096, 8192])
+def test_active_blocks_of_every_size(kirin_lib, precision, n_i):
+    """Block-step active lists from 1 particle to all: exercises the j-groups and the j-split (Sect. 3.2)."""
+    p = workloads.plummer(8192, 1002, eps=1e-3)
+    il = workloads.i_subset(p.n, n_i, seed=n_i)
+    with _ctx(p, precision) as k:
+        got = k.forces(il)
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    assert_parity(got, ref, precision, f"n_i={n_i}")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_every_launch_shape_gives_the_same_answer(kirin_lib, precision):
+    p = workloads.plummer(3000, 77, masses="lognormal", eps=0.005)
+    il = workloads.i_subset(p.n, 700, seed=3)
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    results = []
+    with _ctx(p, precision) as k:
+        for groups in (1, 2, 4, 8):
+            for n_split in (1, 2, 3, 7, 24):
+                k.set_launch(groups, n_split)
+                got = k.forces(il)
+                assert_parity(got, ref, precision, f"groups={groups} split={n_split}")
+                results.append(got)
+        k.set_launch(0, 0)
+    if precision == "fp64":
+        for got in results[1:]:
+            assert np.allclose(got[0], results[0][0], rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_duplicate_and_unordered_i_list(kirin_lib, precision):
+    p = workloads.plummer(700, 8, eps=0.01)
+    il = np.array([699, 0, 17, 17, 350, 0], dtype=np.int32)
+    with _ctx(p, precision) as k:
+        got = k.forces(il)
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    assert_parity(got, ref, precision)
+    assert np.array_equal(got[0][2], got[0][3])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_lognormal_masses_and_tiny_softening(kirin_lib, precision):
+    """The large-N workload's mass spectrum and eps = 4/N, at a size the oracle does in a second."""
+    n = 16384
+    p = workloads.plummer(n, 1003, masses="lognormal", eps=4.0 / n)
+    il = workloads.i_subset(n, 2048, seed=5)
+    with _ctx(p, precision) as k:
+        got = k.forces(il)
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    assert_parity(got, ref, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_zero_softening_guard(kirin_lib, precision):
+    """eps = 0 with r_min: coincident distinct particles contribute nothing (Sect. 3.3.1)."""
+    p = workloads.plummer(1500, 31, eps=0.0)
+    x = p.x.copy()
+    x[10] = x[11]                    # a coincident pair
+    x[20] = x[21] + 1e-9             # a pair closer than r_min
+    x[30] = x[31] + 3e-3             # a close pair above r_min
+    r_min = 1e-6
+    with abi.Kirin(p.n, 0.0, r_min=r_min, precision=precision) as k:
+        k.set_j_particles(p.m, x, p.v)
+        got = k.forces()
+    ref = oracle.acc_jerk_pot(p.m, x, p.v, 0.0, r_min=r_min)
+    errs = errors(got, ref)
+    med, mx = TOL[precision]["acc"]
+    assert errs["acc"]["median"] <= med, errs
+    # the pair at 1e-9 sits below the floor in double-single; its force is
+    # m / r_min^2-sized and dominates: compare those two particles separately
+    keep = np.ones(p.n, bool)
+    keep[[20, 21]] = False
+    sub = tuple(q[keep] for q in got), tuple(q[keep] for q in ref)
+    assert_parity(*sub, precision, "eps=0")
+    for i in (20, 21):
+        assert np.linalg.norm(got[0][i] - ref[0][i]) <= 1e-3 * np.linalg.norm(ref[0][i])
+    assert np.all(np.isfinite(got[0])) and np.all(np.isfinite(got[2]))
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_predictor_on_device(kirin_lib, precision):
+    """GPU_set_ti: predicted positions/velocities (FP64 Taylor series) feed the force."""
+    p = workloads.plummer(2000, 42, eps=0.01)
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((p.n, 3))
+    j = rng.standard_normal((p.n, 3))
+    t0 = rng.uniform(0.0, 0.01, p.n)
+    t = 0.0123
+    with abi.Kirin(p.n, p.eps, precision=precision) as k:
+        k.set_j_particles(p.m, p.x, p.v, a, j, t0)
+        k.predict(t)
+        got = k.forces()
+    dt = (t - t0)[:, None]
+    xp = p.x + p.v * dt + a * dt ** 2 / 2 + j * dt ** 3 / 6
+    vp = p.v + a * dt + j * dt ** 2 / 2
+    ref = oracle.acc_jerk_pot(p.m, xp, vp, p.eps)
+    assert_parity(got, ref, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_energy(kirin_lib, precision):
+    p = workloads.config_small()
+    with _ctx(p, precision) as k:
+        kin, pot = k.energy()
+    rk, rw = oracle.energy(p.m, p.x, p.v, p.eps)
+    assert kin == pytest.approx(rk, rel=1e-13)
+    assert pot == pytest.approx(rw, rel=1e-12 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_device_pointer_twin(kirin_lib, precision):
+    import torch
+    p = workloads.plummer(3000, 9, eps=0.01)
+    dev = torch.device("cuda:0")
+    m = torch.tensor(p.m, device=dev)
+    x = torch.tensor(p.x, device=dev)
+    v = torch.tensor(p.v, device=dev)
+    il = torch.tensor(workloads.i_subset(p.n, 1000, 1), device=dev)
+    acc = torch.empty((1000, 3), dtype=torch.float64, device=dev)
+    jerk = torch.empty_like(acc)
+    pot = torch.empty(1000, dtype=torch.float64, device=dev)
+    with abi.Kirin(p.n, p.eps, precision=precision, stream=torch.cuda.current_stream().cuda_stream) as k:
+        k.set_j_particles_dev(m, x, v)
+        k.compute_forces_dev(il, acc, jerk, pot)
+        k.sync()
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il.cpu().numpy())
+    assert_parity((acc.cpu().numpy(), jerk.cpu().numpy(), pot.cpu().numpy()), ref, precision)
+
+
+def test_mixed_and_fp64_paths_agree(kirin_lib):
+    p = workloads.plummer(4096, 1002, eps=1e-3)
+    with _ctx(p, "mixed") as k:
+        gm = k.forces()
+    with _ctx(p, "fp64") as k:
+        gd = k.forces()
+    assert_parity(gm, gd, "mixed")
+
+
+def test_repeated_calls_are_bitwise_reproducible(kirin_lib):
+    p = workloads.plummer(5000, 3, eps=0.01)
+    il = workloads.i_subset(p.n, 300, 4)
+    with _ctx(p, "mixed") as k:
+        a = k.forces(il)
+        b = k.forces(il)
+    for u, w in zip(a, b):
+        assert np.array_equal(u, w)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_errors_are_reported_not_crashed(kirin_lib, precision):
+    p = workloads.plummer(100, 1, eps=0.01)
+    with abi.Kirin(200, p.eps, precision=precision) as k:
+        with pytest.raises(abi.KirinError) as e:
+            k.compute_forces()
+        assert e.value.code == abi.KIRIN_ESTATE
+        k.set_j_particles(p.m, p.x, p.v)
+        with pytest.raises(abi.KirinError) as e:
+            k.compute_forces(np.array([0, 100], dtype=np.int32))
+        assert e.value.code == abi.KIRIN_EINVAL
+        bad = p.x.copy()
+        bad[3, 1] = np.nan
+        with pytest.raises(abi.KirinError) as e:
+            k.set_j_particles(p.m, bad, p.v)
+        assert e.value.code == abi.KIRIN_ENONFINITE
+        with pytest.raises(abi.KirinError) as e:
+            k.get_acc_jerk_pot()
+        assert e.value.code == abi.KIRIN_ESTATE
+        with pytest.raises(abi.KirinError) as e:
+            k.set_j_particles(p.m, p.x, p.v, first=150)
+        assert e.value.code == abi.KIRIN_EINVAL
+        # the context is still usable
+        got = k.forces()
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps)
+    assert_parity(got, ref, precision)
+
+
+def test_device_side_bad_index_is_flagged(kirin_lib):
+    import torch
+    p = workloads.plummer(300, 2, eps=0.01)
+    dev = torch.device("cuda:0")
+    il = torch.tensor([0, 5, 300, 7], dtype=torch.int32, device=dev)  # 300 is out of range
+    out = torch.empty((4, 3), dtype=torch.float64, device=dev)
+    pot = torch.empty(4, dtype=torch.float64, device=dev)
+    with abi.Kirin(p.n, p.eps, stream=torch.cuda.current_stream().cuda_stream) as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        k.compute_forces_dev(il, out, torch.empty_like(out), pot)
+        with pytest.raises(abi.KirinError) as e:
+            k.sync()
+        assert e.value.code == abi.KIRIN_EINVAL
+        k.sync()  # flag cleared, context usable

@@ -1,0 +1,138 @@
+"""GPU parity of the integrator glue (Hermite shared and block steps, energy),
+the acceleration/adjoint entry points and the batched ensemble, against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hermite, leapfrog
+from paper_0707_0438_gb300 import abi, metrics, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-7)])
+def test_hermite_shared_steps_small_config(kirin_lib, precision, tol):
+    """N = 1024, eps = 1/256: one full evaluation and 10 shared Hermite steps, dt = 1/1024."""
+    p = workloads.config_small()
+    dt, steps = 1.0 / 1024, 10
+    xr, vr, ar, jr, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, dt, steps)
+    with abi.Kirin(p.n, p.eps, precision=precision) as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        for _ in range(steps):
+            k.hermite_shared_step(dt)
+        st = k.get_state()
+    scale_x = np.abs(p.x).max()
+    assert np.abs(st["x"] - xr).max() <= tol * scale_x
+    assert np.abs(st["v"] - vr).max() <= tol * 10 * np.abs(p.v).max()
+    assert np.median(metrics.rel_err_vec(st["a"], ar)) <= (1e-12 if precision == "fp64" else 1e-6)
+    assert np.all(st["t"] == steps * dt)
+
+
+def test_hermite_block_steps_fp64_follow_the_oracle(kirin_lib):
+    """Block time-steps (Aarseth criterion, power-of-two levels): same schedule and state as the oracle."""
+    p = workloads.plummer(256, 1002, eps=1e-3)
+    t_end = 1.0 / 32
+    ref = hermite.block_steps(p.m, p.x, p.v, p.eps, t_end=t_end)
+    with abi.Kirin(p.n, p.eps, precision="fp64") as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        blocks = []
+        while True:
+            t, n_act = k.hermite_block_step(t_end)
+            if n_act == 0:
+                break
+            blocks.append(n_act)
+        st = k.get_state()
+        kin, pot = k.energy()
+    assert blocks == ref["blocks"]
+    assert np.all(st["t"] == t_end)
+    assert np.array_equal(st["dt"], ref["dt"])
+    assert np.abs(st["x"] - ref["x"]).max() <= 1e-9
+    e_end = kin + pot
+    assert e_end == pytest.approx(ref["e_end"], rel=1e-10)
+
+
+def test_hermite_block_run_energy_drift_mixed_vs_fp64(kirin_lib):
+    p = workloads.plummer(2048, 1002, eps=1e-3)
+    out = {}
+    for precision in ("fp64", "mixed"):
+        with abi.Kirin(p.n, p.eps, precision=precision) as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            e0 = sum(k.energy())
+            k.hermite_init(0.0)
+            steps, pairs = k.hermite_run(1.0 / 64)
+            e1 = sum(k.energy())
+            out[precision] = metrics.energy_error(e0, e1)
+            assert steps > 0 and pairs > 0
+    assert abs(out["fp64"]) < 1e-6
+    assert abs(out["mixed"]) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_accel_and_adjoint_dev(kirin_lib, precision):
+    import torch
+    p = workloads.plummer(3000, 1005, eps=0.01)
+    dev = torch.device("cuda:0")
+    m = torch.tensor(p.m, device=dev)
+    x = torch.tensor(p.x, device=dev)
+    g = torch.tensor(np.random.default_rng(1).standard_normal((p.n, 3)), device=dev)
+    acc = torch.empty_like(x)
+    pot = torch.empty_like(m)
+    gx = torch.empty_like(x)
+    gm = torch.empty_like(m)
+    with abi.Kirin(p.n, p.eps, precision=precision, stream=torch.cuda.current_stream().cuda_stream) as k:
+        k.accel_dev(m, x, acc, pot)
+        k.accel_adjoint_dev(m, x, g, gx, gm)
+        k.sync()
+    ra, rp = oracle.acc_pot(p.m, p.x, p.eps)
+    rgx, rgm = oracle.force_adjoint(p.m, p.x, g.cpu().numpy(), p.eps)
+    tol_med, tol_max = (1e-12, 1e-10) if precision == "fp64" else (1e-6, 1e-4)
+    for got, ref in ((acc, ra), (gx, rgx)):
+        e = metrics.rel_err_vec(got.cpu().numpy(), ref)
+        assert np.median(e) <= tol_med and e.max() <= tol_max, (np.median(e), e.max())
+    for got, ref in ((pot, rp), (gm, rgm)):
+        e = metrics.rel_err_scalar(got.cpu().numpy(), ref)
+        assert np.median(e) <= tol_med and e.max() <= max(tol_max, 1e-3), (np.median(e), e.max())
+
+
+def _small_ensemble(n_clusters=24, seed=77):
+    return workloads.ensemble(n_clusters, seed=seed, n_lo=64, ratio=40.0)
+
+
+def test_batched_accelerations_match_per_cluster_oracle(kirin_lib):
+    clusters, sizes = _small_ensemble()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    m = np.concatenate([c.m for c in clusters])
+    x = np.concatenate([c.x for c in clusters])
+    v = np.concatenate([c.v for c in clusters])
+    b = abi.KirinBatch(off, [c.eps for c in clusters])
+    b.set_state(m, x, v)
+    acc = b.accel()
+    b.close()
+    for c, cl in enumerate(clusters):
+        ra, _ = oracle.acc_pot(cl.m, cl.x, cl.eps)
+        e = metrics.rel_err_vec(acc[off[c]:off[c + 1]], ra)
+        assert np.median(e) <= 1e-6 and e.max() <= 1e-5, (c, np.median(e), e.max())
+
+
+def test_batched_leapfrog_matches_oracle_and_graph_is_identical(kirin_lib):
+    clusters, sizes = _small_ensemble(12, seed=5)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    m = np.concatenate([c.m for c in clusters])
+    x = np.concatenate([c.x for c in clusters])
+    v = np.concatenate([c.v for c in clusters])
+    dt, steps = 1.0 / 256, 8
+    finals = []
+    for use_graph in (False, True):
+        b = abi.KirinBatch(off, [c.eps for c in clusters])
+        b.set_state(m, x, v)
+        b.leapfrog(dt, steps, use_graph=use_graph)
+        b.sync()
+        finals.append(b.get_state())
+        b.close()
+    assert np.array_equal(finals[0][0], finals[1][0]) and np.array_equal(finals[0][1], finals[1][1])
+    xg = finals[1][0]
+    for c, cl in enumerate(clusters):
+        xs, _ = leapfrog.trajectory(cl.m, cl.x, cl.v, cl.eps, dt, steps)
+        assert np.abs(xg[off[c]:off[c + 1]] - xs[-1]).max() <= 1e-9
