@@ -205,6 +205,29 @@ int kirin_accel_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x,
 int kirin_accel_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x,
                             const double *g, double *gx, double *gm);
 
+/* Kick-drift-kick leapfrog (Sect. 4.3) on device arrays, in place:
+ *   v_h = v + (dt/2) a(x),  x' = x + dt v_h,  v' = v_h + (dt/2) a(x')
+ * for n_steps steps; a is the force-only acceleration of kirin_accel_dev.
+ * acc (n x 3) holds a(x) on entry when acc_valid != 0 (else it is computed)
+ * and a(x) of the final positions on return.  x_hist, if not NULL, receives
+ * the n_steps + 1 positions x_0 ... x_{n_steps} ((n_steps + 1) x n x 3).
+ * FP64 device arrays; asynchronous. */
+int kirin_leapfrog_dev(kirin_ctx *ctx, int64_t n, const double *m, double *x, double *v, double *acc,
+                       double dt, int32_t n_steps, int32_t acc_valid, double *x_hist);
+
+/* Reverse sweep of kirin_leapfrog_dev over one segment of n_steps steps whose
+ * positions are x_hist ((n_steps + 1) x n x 3): on entry lx, lv hold dL/dx and
+ * dL/dv at the segment's last point, on return at its first point; lm (n)
+ * accumulates dL/dm.  The two half-kicks that meet at an interior point are
+ * applied as one adjoint force call of weight dt.  flags bit 0: the segment
+ * ends at the end of the trajectory (its last point gets weight dt/2);
+ * bit 1: it starts at the trajectory's start (the first point gets dt/2).
+ * A trajectory cut into segments is swept from its last segment to its first.
+ * No counterpart in the paper (it is the chain rule of the leapfrog). */
+int kirin_leapfrog_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x_hist,
+                               int32_t n_steps, double dt, double *lx, double *lv, double *lm,
+                               int32_t flags);
+
 /* ---- batched ensembles: many independent clusters in one launch ----
  * Cluster c owns particles [offsets[c], offsets[c+1]) with softening eps[c];
  * clusters do not interact.  State is FP64 on the device; the pair arithmetic

@@ -74,6 +74,8 @@ _SIGS = {
     "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
     "kirin_accel_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P]),
     "kirin_accel_adjoint_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
+    "kirin_leapfrog_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _D, _I32, _I32, _P]),
+    "kirin_leapfrog_adjoint_dev": (ctypes.c_int, [_P, _I64, _P, _P, _I32, _D, _P, _P, _P, _I32]),
     "kirin_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _PI64, _PD, _D, _I32, _P]),
     "kirin_batch_destroy": (ctypes.c_int, [_P]),
     "kirin_batch_set_state": (ctypes.c_int, [_P, _PD, _PD, _PD]),
@@ -301,6 +303,16 @@ class Kirin:
     def accel_adjoint_dev(self, m, x, g, gx, gm):
         self._check(self.lib.kirin_accel_adjoint_dev(self.ctx, int(m.shape[0]), _dev(m), _dev(x), _dev(g), _dev(gx),
                                                      _dev(gm)), "kirin_accel_adjoint_dev")
+
+    def leapfrog_dev(self, m, x, v, acc, dt, n_steps, acc_valid=False, x_hist=None):
+        self._check(self.lib.kirin_leapfrog_dev(self.ctx, int(m.shape[0]), _dev(m), _dev(x), _dev(v), _dev(acc),
+                                                float(dt), int(n_steps), 1 if acc_valid else 0, _dev(x_hist)),
+                    "kirin_leapfrog_dev")
+
+    def leapfrog_adjoint_dev(self, m, x_hist, n_steps, dt, lx, lv, lm, flags):
+        self._check(self.lib.kirin_leapfrog_adjoint_dev(self.ctx, int(m.shape[0]), _dev(m), _dev(x_hist),
+                                                        int(n_steps), float(dt), _dev(lx), _dev(lv), _dev(lm),
+                                                        int(flags)), "kirin_leapfrog_adjoint_dev")
 
 
 class KirinBatch:

@@ -193,7 +193,7 @@ int ensure_images(kirin_ctx *c)
 
 // Enqueue one force launch (plus split reduction) over the current images.
 int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mode, double *acc,
-              double *jerk, double *pot)
+              double *jerk, double *pot, int accumulate = 0)
 {
     if (n_i == 0)
         return KIRIN_OK;
@@ -213,6 +213,7 @@ int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mo
     a.acc = acc;
     a.jerk = jerk;
     a.pot = pot;
+    a.accumulate = accumulate;
     a.err = c->d_err;
     const int i_cta = (c->prec == KIRIN_MIXED ? 2 : 1) * FORCE_THREADS / s.groups;
     a.n_i_pad = (int)round_up(n_i, i_cta);
@@ -840,6 +841,74 @@ int kirin_accel_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const do
                                 nullptr, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
     ctx->images_dirty = true;
     return run_force(ctx, n, nullptr, (int)n, MODE_ADJOINT, nullptr, gx, gm);
+}
+
+// ---- leapfrog on device arrays and its discrete adjoint -------------------------
+
+int kirin_leapfrog_dev(kirin_ctx *ctx, int64_t n, const double *m, double *x, double *v, double *acc, double dt,
+                       int32_t n_steps, int32_t acc_valid, double *x_hist)
+{
+    if (!ctx || !m || !x || !v || !acc || n < 0 || n > ctx->n_max || n_steps < 0 || !isfinite(dt))
+        return set_msg(ctx, KIRIN_EINVAL, "leapfrog_dev: bad argument");
+    if (n == 0)
+        return KIRIN_OK;
+    DeviceGuard dg(ctx->device);
+    const int nn = (int)n;
+    const int64_t n_pad = round_up(n, TILE_J);
+    const double h = 0.5 * dt;
+    auto accel = [&]() -> int {
+        CK(ctx, launch_pack_xm(nn, (int)n_pad, m, x, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
+        return run_force(ctx, n, nullptr, nn, MODE_ACC_POT, acc, nullptr, nullptr);
+    };
+    ctx->images_dirty = true;
+    if (!acc_valid) {
+        const int rc = accel();
+        if (rc)
+            return rc;
+    }
+    if (x_hist)
+        CK(ctx, launch_copy(3 * nn, x, x_hist, ctx->stream));
+    for (int s = 0; s < n_steps; ++s) {
+        CK(ctx, launch_lf_kick_drift(nn, h, dt, acc, v, x, x_hist ? x_hist + 3 * (size_t)n * (s + 1) : nullptr,
+                                     ctx->stream));
+        const int rc = accel();
+        if (rc)
+            return rc;
+        CK(ctx, launch_axpy(3 * nn, h, acc, v, ctx->stream));
+    }
+    return KIRIN_OK;
+}
+
+int kirin_leapfrog_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x_hist, int32_t n_steps,
+                               double dt, double *lx, double *lv, double *lm, int32_t flags)
+{
+    if (!ctx || !m || !x_hist || !lx || !lv || !lm || n < 0 || n > ctx->n_max || n_steps < 0 || !isfinite(dt))
+        return set_msg(ctx, KIRIN_EINVAL, "leapfrog_adjoint_dev: bad argument");
+    if (n == 0)
+        return KIRIN_OK;
+    DeviceGuard dg(ctx->device);
+    const int nn = (int)n;
+    const int64_t n_pad = round_up(n, TILE_J);
+    const double h = 0.5 * dt;
+    const bool at_end = flags & 1, at_start = flags & 2;
+    ctx->images_dirty = true;
+    // lx += J(x)^T (c lv), lm += M(x)^T (c lv)
+    auto adjoint_at = [&](const double *xk, double c) -> int {
+        CK(ctx, launch_pack_adjoint(nn, (int)n_pad, m, xk, lv, c, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
+        return run_force(ctx, n, nullptr, nn, MODE_ADJOINT, nullptr, lx, lm, 1);
+    };
+    for (int k = n_steps - 1; k >= 0; --k) {
+        // the closing half-kick of step k and the opening half-kick of step k + 1
+        // both act at x_{k+1}: one call with the summed weight
+        const double c = (k == n_steps - 1 && at_end) ? h : dt;
+        int rc = adjoint_at(x_hist + 3 * (size_t)n * (k + 1), c);
+        if (rc)
+            return rc;
+        CK(ctx, launch_axpy(3 * nn, dt, lx, lv, ctx->stream));  // drift: lv_h += dt lx
+    }
+    if (at_start)
+        return adjoint_at(x_hist, h);
+    return KIRIN_OK;
 }
 
 }  // extern "C"

@@ -25,15 +25,7 @@ __global__ void k_reduce_splits(const ForceArgs A)
         double sum = 0.0;
         for (int y = 0; y < A.n_split; ++y)
             sum += A.partial[((size_t)y * 7 + q) * A.n_i_pad + k];
-        if (q < 3) {
-            if (A.acc)
-                A.acc[3 * (size_t)k + q] = A.G * sum;
-        } else if (q < 6) {
-            if (A.jerk)
-                A.jerk[3 * (size_t)k + (q - 3)] = A.G * sum;
-        } else if (A.pot) {
-            A.pot[k] = -A.G * sum;
-        }
+        store_final(A, q, k, sum);
     }
 }
 
@@ -322,6 +314,56 @@ __global__ void k_hermite_correct(int n_act, const int32_t *__restrict__ ilist, 
     }
 }
 
+// Leapfrog pieces (Sect. 4.3 integrator): v_h = v + h a; x' = x + dt v_h
+// (optionally recorded into hist); and the closing kick v' = v_h + h a'.
+__global__ void k_lf_kick_drift(int n, double h, double dt, const double *__restrict__ a, double *v, double *x,
+                                double *hist)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * n)
+        return;
+    const double vh = v[k] + h * a[k];
+    const double xn = x[k] + dt * vh;
+    v[k] = vh;
+    x[k] = xn;
+    if (hist)
+        hist[k] = xn;
+}
+
+__global__ void k_axpy(int n, double alpha, const double *__restrict__ xv, double *y)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n)
+        y[k] += alpha * xv[k];
+}
+
+__global__ void k_copy(int n, const double *__restrict__ src, double *dst)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n)
+        dst[k] = src[k];
+}
+
+// Images of (m, x) with c * lv in the velocity slots: the g = dL/da of one
+// adjoint force call of the leapfrog's reverse sweep.
+__global__ void k_pack_adjoint(int n, int n_pad, const double *__restrict__ m, const double *__restrict__ x,
+                               const double *__restrict__ lv, double c, JMixed *jm, JF64 *jd, unsigned *err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_pad)
+        return;
+    if (k >= n) {
+        write_images(k, PAD_POS, PAD_POS, PAD_POS, 0.0, 0.0, 0.0, 0.0, jm, jd);
+        return;
+    }
+    const size_t o = 3 * (size_t)k;
+    const double gx = c * lv[o], gy = c * lv[o + 1], gz = c * lv[o + 2];
+    if (!(isfinite(x[o]) && isfinite(x[o + 1]) && isfinite(x[o + 2]) && isfinite(gx) && isfinite(gy) &&
+          isfinite(gz)))
+        atomicOr(err, ERR_NONFINITE);
+    write_images(k, x[o], x[o + 1], x[o + 2], m[k], gx, gy, gz, jm, jd);
+}
+
 }  // namespace
 
 cudaError_t launch_reduce_splits(const ForceArgs &a, cudaStream_t st)
@@ -403,6 +445,44 @@ cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_nex
     k_hermite_correct<<<blocks_for(n_act, AUX_THREADS), AUX_THREADS, 0, st>>>(
         n_act, ilist, t_next, eta, dt_min, dt_max, update_dt, xp, vp, acc, jerk, bx, bv, ba, bj, bt,
         bdt);
+    return cudaGetLastError();
+}
+
+}  // namespace kirin
+
+namespace kirin {
+
+cudaError_t launch_lf_kick_drift(int n, double h, double dt, const double *a, double *v, double *x,
+                                 double *hist, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_lf_kick_drift<<<blocks_for(3LL * n, AUX_THREADS), AUX_THREADS, 0, st>>>(n, h, dt, a, v, x, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(int n, double alpha, const double *x, double *y, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_axpy<<<blocks_for(n, AUX_THREADS), AUX_THREADS, 0, st>>>(n, alpha, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy(int n, const double *src, double *dst, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_copy<<<blocks_for(n, AUX_THREADS), AUX_THREADS, 0, st>>>(n, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_adjoint(int n, int n_pad, const double *m, const double *x, const double *lv, double c,
+                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st)
+{
+    if (n_pad == 0)
+        return cudaSuccess;
+    k_pack_adjoint<<<blocks_for(n_pad, AUX_THREADS), AUX_THREADS, 0, st>>>(n, n_pad, m, x, lv, c, jm, jd, err);
     return cudaGetLastError();
 }
 

@@ -113,9 +113,18 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
             const bool ok = mbar_wait_bounded(&bars[slot], par);
             if (ok) {
                 const JMixed *__restrict__ T = tiles + slot * TILE_J;
+                const int j0 = k * TILE_J;  // cluster-local index of T[0]
+                const bool mine = (v0 && (unsigned)(k0 - j0) < (unsigned)TILE_J) ||
+                                  (v1 && (unsigned)(k1 - j0) < (unsigned)TILE_J);
+                if (eps2f != 0.f && __any_sync(0xffffffffu, mine)) {
+#pragma unroll 2
+                    for (int jj = 0; jj < TILE_J; ++jj)
+                        pair<GUARD, MODE_ACC_POT, true>(T[jj], I, t, j0 + jj, v0 ? k0 : -1, v1 ? k1 : -1);
+                } else {
 #pragma unroll 4
-                for (int jj = 0; jj < TILE_J; ++jj)
-                    pair<GUARD, MODE_ACC_POT>(T[jj], I, t);
+                    for (int jj = 0; jj < TILE_J; ++jj)
+                        pair<GUARD, MODE_ACC_POT>(T[jj], I, t);
+                }
                 since += TILE_J;
                 if (since >= BATCH_FLUSH_J) {
                     fold<MODE_ACC_POT>(t, acc0, acc1);
@@ -146,11 +155,6 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
         }
         kt += nt;
         fold<MODE_ACC_POT>(t, acc0, acc1);
-        // self pair: every i of the item lies in its own cluster's j range
-        const float s0 = self_pot_term<GUARD>(I.mk.x, eps2f, 0.0f);
-        const float s1 = self_pot_term<GUARD>(I.mk.y, eps2f, 0.0f);
-        two_sum(acc0.h[6], acc0.l[6], -s0);
-        two_sum(acc1.h[6], acc1.l[6], -s1);
         if (v0) {
             const size_t p = (size_t)off + k0;
 #pragma unroll

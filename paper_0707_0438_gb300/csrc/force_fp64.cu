@@ -20,20 +20,10 @@ __device__ __forceinline__ void write_out64(const ForceArgs &A, int q, int k, do
 {
     if (k >= A.n_i)
         return;
-    if (A.n_split > 1) {
+    if (A.n_split > 1)
         A.partial[((size_t)blockIdx.y * 7 + q) * A.n_i_pad + k] = val;
-        return;
-    }
-    if (q < 3) {
-        if (A.acc)
-            A.acc[3 * (size_t)k + q] = A.G * val;
-    } else if (q < 6) {
-        if (A.jerk)
-            A.jerk[3 * (size_t)k + (q - 3)] = A.G * val;
-    } else {
-        if (A.pot)
-            A.pot[k] = -A.G * val;
-    }
+    else
+        store_final(A, q, k, val);
 }
 
 template <int GROUPS, int MODE>

@@ -18,11 +18,12 @@
 //    folded into double-single (hi, lo) accumulators with an error-free
 //    two-sum; jerk is carried as two sums (w/s^3 and (d.w) d/s^5) combined at
 //    each fold.
-//  * The self pair (j = i) is not skipped in the loop: its acceleration and
-//    jerk terms are exact zeros, and its potential term, recomputed with the
-//    same FP32 operations, is subtracted from the compensated accumulator
-//    afterwards (never m/eps in FP32 after the fact).  With eps = 0 the
-//    guarded variant zeroes every pair at zero separation instead (Sect. 3.3.1).
+//  * The self pair (j = i) never enters a sum: only on the tile that holds a
+//    thread's own i (a warp-uniform branch, a few tiles per warp) does the
+//    loop compare j with i and zero that pair, so the large m_i/eps potential
+//    term cannot round the FP32 partial sums.  With eps = 0 the guarded
+//    variant zeroes every pair at zero separation anyway (Sect. 3.3.1), and
+//    every self term of the adjoint is an exact zero.
 //  * Small active blocks: GROUPS > 1 splits each tile over thread groups with
 //    a shared-memory reduction, and grid.y > 1 splits the j range over CTAs
 //    whose partial sums are reduced on the device (Sect. 3.2 does this last
@@ -48,20 +49,10 @@ __device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, doub
 {
     if (k >= A.n_i)
         return;
-    if (A.n_split > 1) {
+    if (A.n_split > 1)
         A.partial[((size_t)blockIdx.y * 7 + q) * A.n_i_pad + k] = val;
-        return;
-    }
-    if (q < 3) {
-        if (A.acc)
-            A.acc[3 * (size_t)k + q] = A.G * val;
-    } else if (q < 6) {
-        if (A.jerk)
-            A.jerk[3 * (size_t)k + (q - 3)] = A.G * val;
-    } else {
-        if (A.pot)
-            A.pot[k] = -A.G * val;
-    }
+    else
+        store_final(A, q, k, val);
 }
 
 template <int GROUPS, bool GUARD, int MODE>
@@ -101,6 +92,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArg
     const float eps2f = (float)A.eps2;
     const float rmin2f = (float)A.rmin2;
     const IPair I = load_ipair(J + (idx[0] >= 0 ? idx[0] : 0), J + (idx[1] >= 0 ? idx[1] : 0), eps2f, rmin2f);
+    // the self pair needs masking unless its terms vanish by themselves
+    const bool need_mask = !ADJ && eps2f != 0.f;
 
     // ---- j range of this CTA (grid.y splits the tiles) ----
     const int y = blockIdx.y;
@@ -137,9 +130,17 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArg
         const bool ok = mbar_wait_bounded(&bars[st], par);
         if (ok) {
             const JMixed *__restrict__ T = tiles + st * TILE_J + g * JG;
+            const int j0 = (tb + k) * TILE_J + g * JG;  // index of T[0]
+            const bool mine = (unsigned)(idx[0] - j0) < (unsigned)JG || (unsigned)(idx[1] - j0) < (unsigned)JG;
+            if (need_mask && __any_sync(0xffffffffu, mine)) {
+#pragma unroll 2
+                for (int jj = 0; jj < JG; ++jj)
+                    pair<GUARD, MODE, true>(T[jj], I, t, j0 + jj, idx[0], idx[1]);
+            } else {
 #pragma unroll 4
-            for (int jj = 0; jj < JG; ++jj)
-                pair<GUARD, MODE>(T[jj], I, t);
+                for (int jj = 0; jj < JG; ++jj)
+                    pair<GUARD, MODE>(T[jj], I, t);
+            }
             since += JG;
             if (since >= FLUSH_J) {
                 fold<MODE>(t, acc0, acc1);
@@ -171,29 +172,6 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArg
         return;
     }
     fold<MODE>(t, acc0, acc1);
-
-    // ---- remove the self pair's potential term where this thread summed it ----
-    if (!ADJ) {
-        const float rs = self_pot_term<GUARD>(1.0f, eps2f, rmin2f);
-        if (rs != 0.f) {
-#pragma unroll
-            for (int L = 0; L < 2; ++L) {
-                const int i = idx[L];
-                if (i < 0)
-                    continue;
-                const int tj = i / TILE_J;
-                const int pos = i - tj * TILE_J;
-                if (tj >= tb && tj < te && pos / JG == g) {
-                    const float m = L == 0 ? I.mk.x : I.mk.y;
-                    const float self = self_pot_term<GUARD>(m, eps2f, rmin2f);
-                    if (L == 0)
-                        two_sum(acc0.h[6], acc0.l[6], -self);
-                    else
-                        two_sum(acc1.h[6], acc1.l[6], -self);
-                }
-            }
-        }
-    }
 
     double res0[7], res1[7];
 #pragma unroll

@@ -65,8 +65,29 @@ struct ForceArgs {
     double *pot;
     double *partial;        // [n_split][7][n_i_pad] when n_split > 1
     int n_i_pad;
+    int accumulate;         // 1: add the results to the outputs instead of overwriting them
     unsigned *err;
 };
+
+// Final scaling of one of the seven per-i sums and its store (acc and jerk:
+// G * sum; pot: -G * sum); shared by the force kernels and the split reduction.
+__device__ __forceinline__ void store_final(const ForceArgs &A, int q, int k, double sum)
+{
+    double *dst;
+    double val;
+    if (q < 3) {
+        dst = A.acc ? A.acc + 3 * (size_t)k + q : nullptr;
+        val = A.G * sum;
+    } else if (q < 6) {
+        dst = A.jerk ? A.jerk + 3 * (size_t)k + (q - 3) : nullptr;
+        val = A.G * sum;
+    } else {
+        dst = A.pot ? A.pot + k : nullptr;
+        val = -A.G * sum;
+    }
+    if (dst)
+        *dst = A.accumulate ? *dst + val : val;
+}
 
 // What a force launch sums (the seven per-i quantities of ForceArgs):
 //  MODE_ACC_JERK_POT: acc, jerk, pot;  MODE_ACC_POT: acc, pot (jerk outputs 0);
@@ -106,6 +127,11 @@ cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_nex
                                    const double *xp, const double *vp, const double *acc,
                                    const double *jerk, double *bx, double *bv, double *ba,
                                    double *bj, double *bt, double *bdt, cudaStream_t st);
-
+cudaError_t launch_lf_kick_drift(int n, double h, double dt, const double *a, double *v, double *x,
+                                 double *hist, cudaStream_t st);
+cudaError_t launch_axpy(int n, double alpha, const double *x, double *y, cudaStream_t st);
+cudaError_t launch_copy(int n, const double *src, double *dst, cudaStream_t st);
+cudaError_t launch_pack_adjoint(int n, int n_pad, const double *m, const double *x, const double *lv, double c,
+                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st);
 
 }  // namespace kirin

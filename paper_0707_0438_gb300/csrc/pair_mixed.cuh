@@ -7,8 +7,13 @@
 //   s^2 = |d|^2 + eps^2,  r = rsqrt(s^2) (MUFU),  mr = m_j r,  mr3 = mr r^2
 //   pot += mr;  acc += mr3 d;  jerk1 += mr3 w;  jerk2 += mr3 (d.w) r^2 d
 // with w = v_j - v_i; the jerk is jerk1 - 3 jerk2, formed when tile sums are
-// folded.  In adjoint mode the velocity slots carry g and the same registers
-// collect K(d) w with w = m_k g_j - m_j g_k, and g_j.d / s^3.
+// folded.  In adjoint mode the velocity slots carry g and the jerk1 registers
+// collect K(d) w = w/s^3 - 3 (d.w) d/s^5 with w = m_k g_j - m_j g_k, combined
+// per pair (the two parts cancel to the tidal term across j, so summing them
+// separately in FP32 would lose digits), and the pot registers g_j.d / s^3.
+//
+// MASK: the pair whose j index equals a lane's i index contributes nothing
+// (used only on the tile holding a thread's own i-particles).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -99,7 +104,14 @@ __device__ __forceinline__ void fold(Tile7 &t, Lane7 &L0, Lane7 &L1)
         two_sum(L0.h[2], L0.l[2], t.az.x);
         two_sum(L1.h[2], L1.l[2], t.az.y);
     }
-    if (JERK) {
+    if (MODE == MODE_ADJOINT) {
+        two_sum(L0.h[3], L0.l[3], t.j1x.x);
+        two_sum(L1.h[3], L1.l[3], t.j1x.y);
+        two_sum(L0.h[4], L0.l[4], t.j1y.x);
+        two_sum(L1.h[4], L1.l[4], t.j1y.y);
+        two_sum(L0.h[5], L0.l[5], t.j1z.x);
+        two_sum(L1.h[5], L1.l[5], t.j1z.y);
+    } else if (JERK) {
         two_sum(L0.h[3], L0.l[3], __fmaf_rn(-3.f, t.j2x.x, t.j1x.x));
         two_sum(L1.h[3], L1.l[3], __fmaf_rn(-3.f, t.j2x.y, t.j1x.y));
         two_sum(L0.h[4], L0.l[4], __fmaf_rn(-3.f, t.j2y.x, t.j1y.x));
@@ -112,8 +124,9 @@ __device__ __forceinline__ void fold(Tile7 &t, Lane7 &L0, Lane7 &L1)
     t.zero();
 }
 
-template <bool GUARD, int MODE>
-__device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t)
+template <bool GUARD, int MODE, bool MASK = false>
+__device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, int j = 0, int i0 = -1,
+                                     int i1 = -1)
 {
     constexpr bool JERK = MODE != MODE_ACC_POT;
     constexpr bool ADJ = MODE == MODE_ADJOINT;
@@ -137,6 +150,10 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t)
         ri.x = rsqrt_mufu(r2.x);
         ri.y = rsqrt_mufu(r2.y);
     }
+    if (MASK) {
+        ri.x = (j == i0) ? 0.f : ri.x;
+        ri.y = (j == i1) ? 0.f : ri.y;
+    }
     const float2 ri2 = __fmul2_rn(ri, ri);
     if (ADJ) {
         const float4 q4 = J.q[4];
@@ -150,13 +167,10 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t)
         float2 dw = __fmul2_rn(dx, wx);
         dw = __ffma2_rn(dy, wy, dw);
         dw = __ffma2_rn(dz, wz, dw);
-        const float2 b = __fmul2_rn(__fmul2_rn(dw, ri2), ri3);  // (d.w) / s^5
-        t.j1x = __ffma2_rn(ri3, wx, t.j1x);
-        t.j1y = __ffma2_rn(ri3, wy, t.j1y);
-        t.j1z = __ffma2_rn(ri3, wz, t.j1z);
-        t.j2x = __ffma2_rn(b, dx, t.j2x);
-        t.j2y = __ffma2_rn(b, dy, t.j2y);
-        t.j2z = __ffma2_rn(b, dz, t.j2z);
+        const float2 nb3 = __fmul2_rn(__fmul2_rn(dw, __fmul2_rn(ri2, f2(-3.f, -3.f))), ri3);  // -3 (d.w) / s^5
+        t.j1x = __ffma2_rn(nb3, dx, __ffma2_rn(ri3, wx, t.j1x));
+        t.j1y = __ffma2_rn(nb3, dy, __ffma2_rn(ri3, wy, t.j1y));
+        t.j1z = __ffma2_rn(nb3, dz, __ffma2_rn(ri3, wz, t.j1z));
         float2 gd = __fmul2_rn(gjx, dx);
         gd = __ffma2_rn(gjy, dy, gd);
         gd = __ffma2_rn(gjz, dz, gd);
@@ -185,19 +199,6 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t)
         t.j2y = __ffma2_rn(b, dy, t.j2y);
         t.j2z = __ffma2_rn(b, dz, t.j2z);
     }
-}
-
-// The FP32 potential term the loop adds for the self pair (j = i), recomputed
-// with the same operations so that it can be removed exactly afterwards.
-template <bool GUARD>
-__device__ __forceinline__ float self_pot_term(float m, float eps2, float rmin2)
-{
-    if (GUARD) {
-        if (eps2 == 0.f)
-            return 0.f;
-        return __fmul_rn(m, rsqrt_mufu(fmaxf(eps2, rmin2)));
-    }
-    return __fmul_rn(m, rsqrt_mufu(eps2));
 }
 
 }  // namespace kirin

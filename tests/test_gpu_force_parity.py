@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_0707_0438_gb300 import abi, workloads
+from paper_0707_0438_gb300 import abi, metrics, workloads
 from tests.gpu_util import TOL, assert_parity, errors
 
 pytestmark = pytest.mark.gpu
@@ -63,8 +63,9 @@ def test_every_launch_shape_gives_the_same_answer(kirin_lib, precision):
                 results.append(got)
         k.set_launch(0, 0)
     if precision == "fp64":
+        # different splits only reorder an FP64 sum: vectors agree to a few ulp of their norm
         for got in results[1:]:
-            assert np.allclose(got[0], results[0][0], rtol=1e-13, atol=0)
+            assert np.max(metrics.rel_err_vec(got[0], results[0][0])) <= 1e-13
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)

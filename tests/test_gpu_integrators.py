@@ -32,7 +32,7 @@ def test_hermite_shared_steps_small_config(kirin_lib, precision, tol):
 def test_hermite_block_steps_fp64_follow_the_oracle(kirin_lib):
     """Block time-steps (Aarseth criterion, power-of-two levels): same schedule and state as the oracle."""
     p = workloads.plummer(256, 1002, eps=1e-3)
-    t_end = 1.0 / 32
+    t_end = 1.0 / 8  # a multiple of the largest step, so every particle ends there
     ref = hermite.block_steps(p.m, p.x, p.v, p.eps, t_end=t_end)
     with abi.Kirin(p.n, p.eps, precision="fp64") as k:
         k.set_j_particles(p.m, p.x, p.v)
@@ -46,7 +46,7 @@ def test_hermite_block_steps_fp64_follow_the_oracle(kirin_lib):
         st = k.get_state()
         kin, pot = k.energy()
     assert blocks == ref["blocks"]
-    assert np.all(st["t"] == t_end)
+    assert np.array_equal(st["t"], ref["t"]) and np.all(st["t"] == t_end)
     assert np.array_equal(st["dt"], ref["dt"])
     assert np.abs(st["x"] - ref["x"]).max() <= 1e-9
     e_end = kin + pot
@@ -135,4 +135,8 @@ def test_batched_leapfrog_matches_oracle_and_graph_is_identical(kirin_lib):
     xg = finals[1][0]
     for c, cl in enumerate(clusters):
         xs, _ = leapfrog.trajectory(cl.m, cl.x, cl.v, cl.eps, dt, steps)
-        assert np.abs(xg[off[c]:off[c + 1]] - xs[-1]).max() <= 1e-9
+        # an acceleration error da moves positions by at most ~ (steps dt)^2 / 2 * da over the
+        # trajectory; the mixed forces are within 1e-5 |a| per particle
+        a0, _ = oracle.acc_pot(cl.m, cl.x, cl.eps)
+        bound = 10 * 0.5 * (steps * dt) ** 2 * 1e-5 * np.abs(a0).max()
+        assert np.abs(xg[off[c]:off[c + 1]] - xs[-1]).max() <= bound
