@@ -56,7 +56,8 @@ typedef struct {
                         a pair at exactly zero separation contributes nothing (Sect. 3.3.1) */
     int32_t prec;    /* kirin_precision */
     int32_t device;  /* CUDA device ordinal */
-    void *stream;    /* cudaStream_t to enqueue on; NULL: the context creates its own */
+    void *stream;    /* cudaStream_t to enqueue on; NULL: the context creates its own
+                        non-blocking stream; cudaStreamLegacy for the legacy default stream */
 } kirin_config;
 
 /* GPU_open (Appendix A).  Creates a context for up to n_max particles on
@@ -78,7 +79,8 @@ int kirin_query(const kirin_ctx *ctx, int64_t *n_max, int32_t *tile_i, int32_t *
 /* Change the softening, G, separation floor or precision of an open context. */
 int kirin_set_params(kirin_ctx *ctx, double eps, double G, double r_min, int32_t prec);
 
-/* Make the context enqueue on `stream` (a cudaStream_t, NULL = its own stream). */
+/* Make the context enqueue on `stream` (a cudaStream_t; NULL = a stream of its own;
+ * cudaStreamLegacy = the legacy default stream). */
 int kirin_set_stream(kirin_ctx *ctx, void *stream);
 
 /* Launch shape of the force kernel (the configurable "npipes" of GPU_npipes,

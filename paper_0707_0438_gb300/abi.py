@@ -137,6 +137,19 @@ def _host(a, shape=None, dtype=np.float64):
     return a
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
+
+
+def stream_handle(stream):
+    """ctypes value of a stream argument: None lets the library create its own
+    stream; 0 (the handle torch reports for its default stream) means the legacy
+    default stream, passed as cudaStreamLegacy; anything else is a cudaStream_t."""
+    if stream is None:
+        return None
+    stream = int(stream)
+    return ctypes.c_void_p(CUDA_STREAM_LEGACY if stream == 0 else stream)
+
+
 def _dev(t):
     """Device pointer of a CUDA tensor (or None)."""
     if t is None:
@@ -151,8 +164,7 @@ class Kirin:
 
     def __init__(self, n_max, eps, G=1.0, r_min=0.0, precision="mixed", device=0, stream=None):
         self.lib = lib()
-        cfg = kirin_config(float(eps), float(G), float(r_min), _prec(precision), int(device),
-                           None if stream is None else ctypes.c_void_p(int(stream)))
+        cfg = kirin_config(float(eps), float(G), float(r_min), _prec(precision), int(device), stream_handle(stream))
         h = ctypes.c_void_p()
         self._check(self.lib.kirin_init(ctypes.byref(h), int(n_max), ctypes.byref(cfg)), "kirin_init", ctx=False)
         self.ctx = h
@@ -190,8 +202,7 @@ class Kirin:
                     "kirin_set_params")
 
     def set_stream(self, stream):
-        self._check(self.lib.kirin_set_stream(self.ctx, None if stream is None else ctypes.c_void_p(int(stream))),
-                    "kirin_set_stream")
+        self._check(self.lib.kirin_set_stream(self.ctx, stream_handle(stream)), "kirin_set_stream")
 
     def set_launch(self, groups=0, n_split=0):
         self._check(self.lib.kirin_set_launch(self.ctx, int(groups), int(n_split)), "kirin_set_launch")
@@ -324,7 +335,7 @@ class KirinBatch:
         ep = np.ascontiguousarray(eps, dtype=np.float64)
         h = ctypes.c_void_p()
         rc = self.lib.kirin_batch_create(ctypes.byref(h), off.shape[0] - 1, off.ctypes.data_as(_PI64), _dp(ep),
-                                         float(G), int(device), None if stream is None else ctypes.c_void_p(int(stream)))
+                                         float(G), int(device), stream_handle(stream))
         if rc != KIRIN_OK:
             raise KirinError(rc, "kirin_batch_create")
         self.b = h

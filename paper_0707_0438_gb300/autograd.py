@@ -9,7 +9,9 @@ in kirin_leapfrog_dev / kirin_leapfrog_adjoint_dev.  The paper has no
 adjoint; the leapfrog is the shared-step integrator of Sect. 4.3.
 
 All tensors are float64 CUDA tensors: x, v (n, 3), m (n).  The context must
-run on the current torch stream (pass stream=torch.cuda.current_stream().cuda_stream).
+run on the current torch stream: create it with
+stream=torch.cuda.current_stream().cuda_stream (0, torch's default stream, is
+passed on as the legacy default stream).
 """
 from __future__ import annotations
 

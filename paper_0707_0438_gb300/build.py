@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd = [nvcc] + common + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr[-4000:]}")
         if verbose and r.stderr:
             print(r.stderr)
         return obj

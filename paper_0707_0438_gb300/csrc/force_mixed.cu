@@ -43,7 +43,10 @@
 namespace kirin {
 namespace {
 
-constexpr int FLUSH_J = 256;  // j-particles per FP32 partial sum and thread
+// j-particles per FP32 partial sum and thread; the adjoint's terms cancel
+// across j (tidal sums), so its partial sums are kept shorter
+constexpr int FLUSH_J = 256;
+constexpr int FLUSH_J_ADJOINT = 64;
 
 __device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, double val)
 {
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArg
                     pair<GUARD, MODE>(T[jj], I, t);
             }
             since += JG;
-            if (since >= FLUSH_J) {
+            if (since >= (ADJ ? FLUSH_J_ADJOINT : FLUSH_J)) {
                 fold<MODE>(t, acc0, acc1);
                 since = 0;
             }
