@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
             mbar_init(&bars[st], 1);
         mbar_fence_init();
     }
+    const uint64_t pol = l2_policy_evict_last();
     int kt = 0;  // tiles consumed so far by this CTA (stage / phase bookkeeping)
     while (true) {
         if (tid == 0)
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
             for (int st = 0; st < STAGES && st < nt; ++st) {
                 const int slot = (kt + st) % STAGES;
                 mbar_arrive_expect_tx(&bars[slot], TILE_BYTES);
-                bulk_g2s(tiles + slot * TILE_J, J + (size_t)st * TILE_J, TILE_BYTES, &bars[slot]);
+                bulk_g2s_hint(tiles + slot * TILE_J, J + (size_t)st * TILE_J, TILE_BYTES, &bars[slot], pol);
             }
         }
         Tile7 t;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
             }
             if (tid == 0 && k + STAGES < nt) {
                 mbar_arrive_expect_tx(&bars[slot], TILE_BYTES);
-                bulk_g2s(tiles + slot * TILE_J, J + (size_t)(k + STAGES) * TILE_J, TILE_BYTES, &bars[slot]);
+                bulk_g2s_hint(tiles + slot * TILE_J, J + (size_t)(k + STAGES) * TILE_J, TILE_BYTES, &bars[slot], pol);
             }
         }
         if (aborted) {

@@ -110,11 +110,12 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArg
             mbar_init(&bars[st], 1);
         mbar_fence_init();
     }
+    const uint64_t pol = l2_policy_evict_last();
     __syncthreads();
     if (tid == 0) {
         for (int st = 0; st < STAGES && st < nt; ++st) {
             mbar_arrive_expect_tx(&bars[st], TILE_BYTES);
-            bulk_g2s(tiles + st * TILE_J, J + (size_t)(tb + st) * TILE_J, TILE_BYTES, &bars[st]);
+            bulk_g2s_hint(tiles + st * TILE_J, J + (size_t)(tb + st) * TILE_J, TILE_BYTES, &bars[st], pol);
         }
     }
 
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArg
         }
         if (tid == 0 && k + STAGES < nt) {
             mbar_arrive_expect_tx(&bars[st], TILE_BYTES);
-            bulk_g2s(tiles + st * TILE_J, J + (size_t)(tb + k + STAGES) * TILE_J, TILE_BYTES, &bars[st]);
+            bulk_g2s_hint(tiles + st * TILE_J, J + (size_t)(tb + k + STAGES) * TILE_J, TILE_BYTES, &bars[st], pol);
         }
     }
     if (aborted) {

@@ -14,6 +14,11 @@
 //
 // MASK: the pair whose j index equals a lane's i index contributes nothing
 // (used only on the tile holding a thread's own i-particles).
+//
+// In adjoint mode the MUFU estimate of 1/s is refined by one Newton-Raphson
+// step, y' = y (3 - s^2 y^2) / 2: the hardware estimate's small systematic
+// error enters w/s^3 and d(d.w)/s^5 with different weights (3 and 5), and the
+// two halves cancel across j, which would amplify it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -154,8 +159,11 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, 
         ri.x = (j == i0) ? 0.f : ri.x;
         ri.y = (j == i1) ? 0.f : ri.y;
     }
-    const float2 ri2 = __fmul2_rn(ri, ri);
+    float2 ri2 = __fmul2_rn(ri, ri);
     if (ADJ) {
+        const float2 e = __ffma2_rn(__fmul2_rn(r2, ri2), f2(-0.5f, -0.5f), f2(1.5f, 1.5f));
+        ri = __fmul2_rn(ri, e);
+        ri2 = __fmul2_rn(ri, ri);
         const float4 q4 = J.q[4];
         const float2 mj = f2(q1.z, q1.w);
         const float2 gjx = f2(q3.z, q3.w), gjy = f2(q4.x, q4.y), gjz = f2(q4.z, q4.w);

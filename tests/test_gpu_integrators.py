@@ -87,13 +87,22 @@ def test_accel_and_adjoint_dev(kirin_lib, precision):
         k.sync()
     ra, rp = oracle.acc_pot(p.m, p.x, p.eps)
     rgx, rgm = oracle.force_adjoint(p.m, p.x, g.cpu().numpy(), p.eps)
-    tol_med, tol_max = (1e-12, 1e-10) if precision == "fp64" else (1e-6, 1e-4)
-    for got, ref in ((acc, ra), (gx, rgx)):
-        e = metrics.rel_err_vec(got.cpu().numpy(), ref)
-        assert np.median(e) <= tol_med and e.max() <= tol_max, (np.median(e), e.max())
-    for got, ref in ((pot, rp), (gm, rgm)):
-        e = metrics.rel_err_scalar(got.cpu().numpy(), ref)
-        assert np.median(e) <= tol_med and e.max() <= max(tol_max, 1e-3), (np.median(e), e.max())
+    if precision == "fp64":
+        tol_med, tol_max = 1e-12, 1e-10
+    else:
+        tol_med, tol_max = 1e-6, 1e-5
+    e = metrics.rel_err_vec(acc.cpu().numpy(), ra)
+    assert np.median(e) <= tol_med and e.max() <= tol_max, ("acc", np.median(e), e.max())
+    e = metrics.rel_err_scalar(pot.cpu().numpy(), rp)
+    assert np.median(e) <= tol_med and e.max() <= tol_max, ("pot", np.median(e), e.max())
+    # The adjoint sums are random-sign sums over j (g is random), and some particles' sums
+    # nearly cancel: the per-particle median is held to the force tolerance and the worst
+    # particle's error is measured against the RMS size of the gradient.
+    for name, got, ref in (("dL/dx", gx.cpu().numpy(), rgx), ("dL/dm", gm.cpu().numpy()[:, None], rgm[:, None])):
+        err = np.linalg.norm(got - ref, axis=1)
+        rms = np.sqrt(np.mean(np.sum(ref * ref, axis=1)))
+        med = np.median(err / np.linalg.norm(ref, axis=1))
+        assert med <= tol_med and err.max() / rms <= tol_max, (name, med, err.max() / rms)
 
 
 def _small_ensemble(n_clusters=24, seed=77):
