@@ -22,8 +22,7 @@
 //    thread's own i (a warp-uniform branch, a few tiles per warp) does the
 //    loop compare j with i and zero that pair, so the large m_i/eps potential
 //    term cannot round the FP32 partial sums.  With eps = 0 the guarded
-//    variant zeroes every pair at zero separation anyway (Sect. 3.3.1), and
-//    every self term of the adjoint is an exact zero.
+//    variant zeroes every pair at zero separation anyway (Sect. 3.3.1).
 //  * Small active blocks: GROUPS > 1 splits each tile over thread groups with
 //    a shared-memory reduction, and grid.y > 1 splits the j range over CTAs
 //    whose partial sums are reduced on the device (Sect. 3.2 does this last
@@ -33,7 +32,7 @@
 //    paper): the velocity slots of each record carry g = dL/da and the same
 //    seven sums become dL/dx_k = G sum_j [w/s^3 - 3 (d.w) d/s^5] with
 //    w = m_k g_j - m_j g_k (jerk slots) and dL/dm_k = -G sum_j g_j.d/s^3
-//    (potential slot); every self-pair term of the adjoint is an exact zero.
+//    (potential slot).
 #include <cuda_runtime.h>
 
 #include "kirin_internal.cuh"
@@ -95,8 +94,10 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArg
     const float eps2f = (float)A.eps2;
     const float rmin2f = (float)A.rmin2;
     const IPair I = load_ipair(J + (idx[0] >= 0 ? idx[0] : 0), J + (idx[1] >= 0 ? idx[1] : 0), eps2f, rmin2f);
-    // the self pair needs masking unless its terms vanish by themselves
-    const bool need_mask = !ADJ && eps2f != 0.f;
+    // the self pair is masked unless eps = 0 zeroes it anyway (in the adjoint,
+    // w = m_k g_j - m_j g_k would vanish only if the compiler kept both
+    // products rounded; a contracted multiply-add leaves ~u m g, times 1/eps^3)
+    const bool need_mask = eps2f != 0.f;
 
     // ---- j range of this CTA (grid.y splits the tiles) ----
     const int y = blockIdx.y;
