@@ -256,6 +256,35 @@ int kirin_batch_sync(kirin_batch *b);
 /* Accelerations of every particle of every cluster into a host array (n_total x 3). */
 int kirin_batch_accel(kirin_batch *b, double *acc);
 
+/* ---- allocation-free evaluation ----
+ * No counterpart in the paper.  For callers that cannot allocate device
+ * memory when they need forces (inside another framework's memory pool that
+ * holds the whole device, in callbacks where cudaMalloc/cudaFree would
+ * synchronise the device, or in hosts that forbid allocation after start-up):
+ * the same mixed-precision evaluation as kirin_compute_forces_dev (acc, jerk
+ * and pot of the n_i listed i against all n j, i_list NULL = all), with no
+ * context and no allocation.  Its scratch (the j image and the j-split
+ * partial sums) is one fixed device array of about 6.6 MB inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   n, n_i <= KIRIN_NOALLOC_MAX_N; larger sizes return EINVAL.
+ *   m (n), x, v (n x 3), i_list (n_i, int32), acc, jerk (n_i x 3), pot (n_i):
+ *   FP64 device arrays on the current device; any output may be NULL.
+ *   status: device word set to 0 and then to the OR of KIRIN_STATUS_* bits
+ *   found while the work runs (NULL: not reported).
+ *   stream: cudaStream_t (NULL or cudaStreamLegacy: the legacy default stream).
+ * Asynchronous.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and must come before any stream capture on
+ * that device.  Every call on a device shares the one array, which keeps the
+ * last call's contents: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and must be ordered by the caller. */
+#define KIRIN_NOALLOC_MAX_N 32768
+#define KIRIN_STATUS_BAD_INDEX 1u  /* an i_list entry outside [0, n) */
+#define KIRIN_STATUS_TIMEOUT 2u    /* a bounded device wait gave up */
+#define KIRIN_STATUS_NONFINITE 8u  /* NaN or Inf in m, x or v */
+int kirin_forces_noalloc(int64_t n, const double *m, const double *x, const double *v, int64_t n_i,
+                         const int32_t *i_list, double eps, double G, double r_min, double *acc,
+                         double *jerk, double *pot, unsigned *status, void *stream);
+
 /* Human-readable name of a return code (static string). */
 const char *kirin_strerror(int code);
 

@@ -83,6 +83,7 @@ _SIGS = {
     "kirin_batch_leapfrog": (ctypes.c_int, [_P, _D, _I32, _I32]),
     "kirin_batch_sync": (ctypes.c_int, [_P]),
     "kirin_batch_accel": (ctypes.c_int, [_P, _PD]),
+    "kirin_forces_noalloc": (ctypes.c_int, [_I64, _P, _P, _P, _I64, _P, _D, _D, _D, _P, _P, _P, _P, _P]),
     "kirin_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kirin_last_error": (ctypes.c_char_p, [_P]),
 }
