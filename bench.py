@@ -15,6 +15,7 @@ bounded i-subset (which also gives the per-particle error of the mixed
 results), SM clocks sampled during the timed region, and the roofline entry.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+  python bench.py --workload small|block|ensemble|adjoint   (the other workloads, one JSON line each)
 
 Multi-GPU runs (torchrun, one rank per GPU) are replicas: every rank
 evaluates its own copy of the workload; value = all ranks' pairs / max time.
@@ -144,8 +145,9 @@ def _subset(n, k, seed):
 
 def _calibrated_oracle_size(p, target_s):
     """i-subset size for about target_s seconds of oracle time on this host."""
-    _, _, dt, _ = _time_oracle_sample(p, 32, 99)
-    per_i = max(dt / 32, 1e-6)
+    k0 = min(p.n, 256)
+    _, _, dt, _ = _time_oracle_sample(p, k0, 99)
+    per_i = max(dt / k0, 1e-7)
     return int(max(64, min(p.n, target_s / per_i)))
 
 
@@ -380,6 +382,161 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def _line(metric, value, unit, steps, warmup, seconds, workload, extra, higher=True, dtype="f32 pair math"):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "ms_per_step": 1e3 * seconds / max(steps, 1), "higher_is_better": higher, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": {"workload": workload}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_small(args):
+    """N = 1024, eps = 1/256: one full evaluation and 10 shared Hermite steps dt = 1/1024, mixed and FP64."""
+    import torch
+
+    from paper_0707_0438_gb300 import abi, workloads
+    p = workloads.config_small(1024)
+    res = {}
+    for precision in ("mixed", "fp64"):
+        with abi.Kirin(p.n, p.eps, precision=precision) as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            for _ in range(args.warmup):
+                k.forces()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                k.hermite_init(0.0)
+                for _ in range(10):
+                    k.hermite_shared_step(1.0 / 1024)
+                k.sync()
+            dt = time.perf_counter() - t0
+            res[precision] = {"value": 11 * p.n * p.n * args.steps / dt, "ms_per_run": 1e3 * dt / args.steps}
+    _line("pair interactions/s, 1 evaluation + 10 shared Hermite steps", res["mixed"]["value"], UNIT, args.steps,
+          args.warmup, res["mixed"]["ms_per_run"] * args.steps / 1e3,
+          "plummer N=1024 eps=1/256: 11 acc+jerk+pot evaluations through the host loop", {"fp64": res["fp64"]})
+
+
+def run_block(args):
+    """N = 65536, eps = 1e-3, block-step Hermite (eta 0.01, levels 2^-20..2^-3) to t = 1/8."""
+    import torch
+
+    from paper_0707_0438_gb300 import abi, metrics, workloads
+    n = 65536 if args.n == N_DEFAULT else args.n
+    p = workloads.config_block(n)
+    out = {}
+    for precision, t_end in (("mixed", 0.125), ("fp64", args.fp64_t_end)):
+        with abi.Kirin(n, p.eps, precision=precision) as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            kin0, pot0 = k.energy()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            k.hermite_init(0.0)
+            steps, pairs = k.hermite_run(t_end)
+            dt = time.perf_counter() - t0
+            kin1, pot1 = k.energy()
+            out[precision] = {"t_end": t_end, "block_steps": steps, "pairs": pairs + float(n) * n,
+                              "seconds": dt, "value": (pairs + float(n) * n) / dt,
+                              "dE_E": metrics.energy_error(kin0 + pot0, kin1 + pot1)}
+    # active-block histogram and per-bucket rate (each step synchronised), mixed, to t = 1/32
+    hist = {}
+    with abi.Kirin(n, p.eps, precision="mixed") as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        k.sync()
+        while True:
+            t0 = time.perf_counter()
+            _, n_act = k.hermite_block_step(1.0 / 32)
+            k.sync()
+            dt = time.perf_counter() - t0
+            if n_act == 0:
+                break
+            b = 1 << int(math.log2(n_act))
+            h = hist.setdefault(b, [0, 0.0, 0.0])
+            h[0] += 1
+            h[1] += n_act * float(n)
+            h[2] += dt
+    buckets = {str(b): {"steps": h[0], "pairs_per_s": h[1] / h[2]} for b, h in sorted(hist.items())}
+    m = out["mixed"]
+    _line("pair interactions/s over a block-step Hermite run (acc+jerk+pot, incl. predictor/corrector/scheduler)",
+          m["value"], UNIT, m["block_steps"], 0, m["seconds"],
+          f"plummer N={n} eps=1e-3 seed 1002, Hermite block steps eta=0.01 to t=1/8",
+          {"mixed": m, "fp64": out["fp64"], "n_active_histogram": buckets,
+           "note": "fp64 run integrates to the shorter t_end shown; rates are comparable, ΔE/E is per run"})
+
+
+def run_ensemble(args):
+    """512 clusters, N_c log-uniform in [256, 16384), eps = 1/N_c, leapfrog dt = 1/256, 64 steps."""
+    from paper_0707_0438_gb300 import abi, workloads
+    clusters, sizes = workloads.ensemble()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    m = np.concatenate([c.m for c in clusters])
+    x = np.concatenate([c.x for c in clusters])
+    v = np.concatenate([c.v for c in clusters])
+    pairs_per_step = float(np.sum(sizes.astype(np.float64) ** 2))
+    res = {}
+    for use_graph in (True, False):
+        b = abi.KirinBatch(off, [c.eps for c in clusters])
+        b.set_state(m, x, v)
+        b.leapfrog(1.0 / 256, 64, use_graph=use_graph)  # warm-up (and graph build)
+        b.sync()
+        times = []
+        for _ in range(max(1, args.steps)):
+            b.set_state(m, x, v)
+            t0 = time.perf_counter()
+            b.leapfrog(1.0 / 256, 64, use_graph=use_graph)
+            b.sync()
+            times.append(time.perf_counter() - t0)
+        b.close()
+        t = float(np.median(times))
+        res["graph" if use_graph else "no_graph"] = {"seconds_per_64_steps": t, "value": pairs_per_step * 64 / t}
+    g = res["graph"]
+    _line("pair interactions/s, batched leapfrog (sum_c N_c^2 x 64 / t)", g["value"], UNIT, 64, 1,
+          g["seconds_per_64_steps"], f"512 Plummer clusters N_c=floor(256*64^U) seed 1004, sum N_c^2={pairs_per_step:.4g},"
+          " eps=1/N_c, leapfrog dt=1/256 x 64 steps, one persistent launch per force, CUDA graph",
+          {"no_graph": res["no_graph"], "gflops_k38": 38 * g["value"] / 1e9, "n_total": int(off[-1])})
+
+
+def run_adjoint(args):
+    """N = 16384, eps = 0.01, 64 leapfrog steps dt = 1/128, checkpoint every 8; forward + backward."""
+    import torch
+
+    from paper_0707_0438_gb300 import abi, workloads
+    from paper_0707_0438_gb300 import autograd as kag
+    dev = torch.device("cuda:0")
+    n, steps, dt = 16384, 64, 1.0 / 128
+    p = workloads.config_adjoint(n)
+    q = workloads.perturb(p, 1e-3)
+    stream = torch.cuda.current_stream().cuda_stream
+    k = abi.Kirin(n, p.eps, precision="mixed", stream=stream)
+    T = lambda a, g=False: torch.tensor(a, dtype=torch.float64, device=dev, requires_grad=g)
+    with torch.no_grad():
+        tgt, _ = kag.leapfrog(T(q.x), T(q.v), T(q.m), k, dt, steps)
+
+    def run():
+        x, v, mm = T(p.x, True), T(p.v, True), T(p.m, True)
+        xf, _ = kag.leapfrog(x, v, mm, k, dt, steps, every=8)
+        loss = ((xf - tgt) ** 2).sum(dim=1).mean()
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        loss = run()
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    # force evaluations: 65 forward, 64 recomputed, 65 adjoint (one per distinct position)
+    evals = 65 + 64 + 65
+    k.close()
+    _line("seconds per forward+backward of a 64-step differentiable leapfrog", t, "s", args.steps, args.warmup,
+          t * args.steps, f"plummer N={n} eps=0.01 seed 1005, 64 KDK steps dt=1/128, checkpoints every 8 steps",
+          {"pair_evaluations_per_s": evals * float(n) * n / t, "loss": float(loss.item())}, higher=False)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,13 +546,17 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", choices=["large", "small", "block", "ensemble", "adjoint"], default="large")
+    ap.add_argument("--fp64-t-end", type=float, default=1.0 / 64)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "large":
         run_native(args)
+    else:
+        {"small": run_small, "block": run_block, "ensemble": run_ensemble, "adjoint": run_adjoint}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -92,7 +92,8 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The in-tree libkirin.so, or the library named by $KIRIN_LIBRARY (a tuning variant)."""
+    return os.environ.get("KIRIN_LIBRARY") or _build.LIB
 
 
 def header_functions(path: str = HEADER):

@@ -44,16 +44,22 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libkirin.so unless it is up to date; returns its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, out_dir: str | None = None, defines=()) -> str:
+    """Compile and link libkirin.so unless it is up to date; returns its path.
+
+    out_dir and defines (e.g. ["KIRIN_TILE_J=64"]) build a variant elsewhere
+    (tuning sweeps); the default is the in-tree library."""
+    out_dir = out_dir or OUT_DIR
+    lib = os.path.join(out_dir, "libkirin.so")
+    if out_dir == OUT_DIR and not defines and not force and not _stale():
         return LIB
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    common += [f"-D{d}" for d in defines]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + common + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -65,14 +71,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     srcs = sources()
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     link = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
         "-Xlinker", "-rpath," + _cuda_lib_dir(nvcc)]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link of libkirin.so failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -51,8 +51,9 @@ struct kirin_ctx {
     double *d_partial = nullptr;
     size_t partial_cap = 0;  // doubles
     unsigned *d_err = nullptr;
-    double *d_scal = nullptr;  // [0] t_next, [1..2] energies
-    int32_t *d_count = nullptr;
+    double *d_scal = nullptr;  // [0] t_next, [1..2] energies, [3] block-selection minimum (bits)
+    int32_t *d_count = nullptr;  // [0] block size
+    int32_t *d_sel_counts = nullptr;  // per-CTA counts of the block selection
     double *h_scal = nullptr;  // pinned mirrors
     int32_t *h_count = nullptr;
     unsigned *h_err = nullptr;
@@ -261,7 +262,7 @@ void free_all(kirin_ctx *c)
 {
     void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
                     c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
-                    c->d_count};
+                    c->d_count, c->d_sel_counts};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -367,6 +368,7 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
     dalloc((void **)&c->d_err, sizeof(unsigned));
     dalloc((void **)&c->d_scal, 4 * sizeof(double));
     dalloc((void **)&c->d_count, sizeof(int32_t));
+    dalloc((void **)&c->d_sel_counts, ((n + 1023) / 1024 + 1) * sizeof(int32_t));
     if (ok && cudaMallocHost((void **)&c->h_ilist, n * sizeof(int32_t)) != cudaSuccess)
         ok = false;
     if (ok && cudaMallocHost((void **)&c->h_scal, 4 * sizeof(double)) != cudaSuccess)
@@ -709,6 +711,7 @@ int kirin_hermite_block_step(kirin_ctx *ctx, double t_end, double *t_now, int64_
     DeviceGuard dg(ctx->device);
     const int n = (int)ctx->n_j;
     CK(ctx, launch_block_select(n, ctx->bt, ctx->bdt, t_end, ctx->d_ilist, ctx->d_scal, ctx->d_count,
+                                reinterpret_cast<unsigned long long *>(ctx->d_scal + 3), ctx->d_sel_counts,
                                 ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->h_count, ctx->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));

@@ -4,6 +4,8 @@
 // block-step scheduler (Sect. 3, Sect. 3.1).  All FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kirin_internal.cuh"
 
 namespace kirin {
@@ -214,57 +216,91 @@ __global__ void k_hermite_init(int n, double t, const double *acc, const double 
     bdt[k] = quantise_down(0.01 * norm3(a) / norm3(j), dt_min, dt_max);
 }
 
-// One CTA of 1024 threads: t_next = min(t_i + dt_i) and the ordered list of
-// i with t_i + dt_i == t_next (empty if t_next > t_end).
-__global__ void __launch_bounds__(1024) k_block_select(int n, const double *__restrict__ bt,
-                                                       const double *__restrict__ bdt, double t_end,
-                                                       int32_t *ilist, double *t_next_out,
-                                                       int32_t *count_out)
+// Block selection: t_next = min_i (t_i + dt_i) and the ordered list of the
+// i with t_i + dt_i == t_next (Sect. 3.1 block time-steps).  Three passes
+// over the particles, each fully parallel: an atomic minimum over the bit
+// patterns of the (non-negative) end times, per-CTA counts, then ordered
+// writes at offsets summed from the counts, so the list is in index order.
+constexpr int SEL_THREADS = 256;
+constexpr int SEL_ITEMS = 4;  // particles per thread, SEL_THREADS apart
+constexpr int SEL_PER_CTA = SEL_THREADS * SEL_ITEMS;
+
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_min(int n, const double *__restrict__ bt,
+                                                         const double *__restrict__ bdt,
+                                                         unsigned long long *minw)
 {
-    __shared__ double smin[1024];
-    __shared__ int scan[1024];
-    __shared__ int base;
-    double mn = INFINITY;
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        mn = fmin(mn, bt[i] + bdt[i]);
-    smin[threadIdx.x] = mn;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
-        __syncthreads();
-    }
-    const double tn = smin[0];
-    if (threadIdx.x == 0) {
-        base = 0;
-        *t_next_out = tn;
-    }
-    __syncthreads();
-    if (!(tn <= t_end)) {
-        if (threadIdx.x == 0)
-            *count_out = 0;
-        return;
-    }
-    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
-        const int i = c0 + threadIdx.x;
-        const int flag = (i < n && bt[i] + bdt[i] == tn) ? 1 : 0;
-        scan[threadIdx.x] = flag;
-        __syncthreads();
-        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-            const int add = threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
-            __syncthreads();
-            scan[threadIdx.x] += add;
-            __syncthreads();
-        }
-        if (flag)
-            ilist[base + scan[threadIdx.x] - 1] = i;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1)
-            base += scan[threadIdx.x];
-        __syncthreads();
+    unsigned long long mn = ~0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        mn = min(mn, (unsigned long long)__double_as_longlong(bt[i] + bdt[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMin(minw, mn);
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_count(int n, const double *__restrict__ bt,
+                                                           const double *__restrict__ bdt,
+                                                           const unsigned long long *minw, int32_t *counts)
+{
+    const double tn = __longlong_as_double((long long)*minw);
+    int total = 0;
+#pragma unroll
+    for (int j = 0; j < SEL_ITEMS; ++j) {
+        const int i = blockIdx.x * SEL_PER_CTA + j * SEL_THREADS + threadIdx.x;
+        total += __syncthreads_count(i < n && bt[i] + bdt[i] == tn);
     }
     if (threadIdx.x == 0)
-        *count_out = base;
+        counts[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *__restrict__ bt,
+                                                           const double *__restrict__ bdt,
+                                                           const unsigned long long *minw,
+                                                           const int32_t *__restrict__ counts, double t_end,
+                                                           int32_t *ilist, double *t_next_out,
+                                                           int32_t *count_out)
+{
+    __shared__ int warp_tot[SEL_THREADS / 32];
+    __shared__ int red[SEL_THREADS];
+    const double tn = __longlong_as_double((long long)*minw);
+    const bool due = tn <= t_end;
+    // offset of this CTA: sum of the counts of the CTAs before it
+    int part = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += SEL_THREADS)
+        part += counts[b];
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int w = SEL_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    int base = red[0];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < SEL_ITEMS; ++j) {
+        const int i = blockIdx.x * SEL_PER_CTA + j * SEL_THREADS + threadIdx.x;
+        const bool flag = due && i < n && bt[i] + bdt[i] == tn;
+        const unsigned ballot = __ballot_sync(0xffffffffu, flag);
+        if (lane == 0)
+            warp_tot[warp] = __popc(ballot);
+        __syncthreads();
+        int before = 0, all = 0;
+#pragma unroll
+        for (int w = 0; w < SEL_THREADS / 32; ++w) {
+            before += w < warp ? warp_tot[w] : 0;
+            all += warp_tot[w];
+        }
+        if (flag)
+            ilist[base + before + __popc(ballot & ((1u << lane) - 1u))] = i;
+        base += all;
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        *count_out = due ? base : 0;
+        *t_next_out = tn;
+    }
 }
 
 // Hermite corrector for the block (Sect. 3): a2, a3 from the two (a, jerk)
@@ -426,11 +462,17 @@ cudaError_t launch_hermite_init(int n, double t, const double *acc, const double
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end,
-                                int32_t *ilist, double *t_next_out, int32_t *count_out,
-                                cudaStream_t st)
+cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end, int32_t *ilist,
+                                double *t_next_out, int32_t *count_out, unsigned long long *minw,
+                                int32_t *counts, cudaStream_t st)
 {
-    k_block_select<<<1, 1024, 0, st>>>(n, bt, bdt, t_end, ilist, t_next_out, count_out);
+    const int nblk = blocks_for(n, SEL_PER_CTA);
+    cudaError_t e = cudaMemsetAsync(minw, 0xff, sizeof(unsigned long long), st);
+    if (e != cudaSuccess)
+        return e;
+    k_sel_min<<<std::min(nblk * SEL_ITEMS, 1024), SEL_THREADS, 0, st>>>(n, bt, bdt, minw);
+    k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts);
+    k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, t_end, ilist, t_next_out, count_out);
     return cudaGetLastError();
 }
 

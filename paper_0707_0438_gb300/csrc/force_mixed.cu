@@ -44,8 +44,18 @@ namespace {
 
 // j-particles per FP32 partial sum and thread; the adjoint's terms cancel
 // across j (tidal sums), so its partial sums are kept shorter
-constexpr int FLUSH_J = 256;
+#ifndef KIRIN_FLUSH_J
+#define KIRIN_FLUSH_J 256
+#endif
+#ifndef KIRIN_MIX_UNROLL
+#define KIRIN_MIX_UNROLL 4
+#endif
+#ifndef KIRIN_MIX_MINB
+#define KIRIN_MIX_MINB 2
+#endif
+constexpr int FLUSH_J = KIRIN_FLUSH_J;
 constexpr int FLUSH_J_ADJOINT = 64;
+constexpr int MIX_UNROLL = KIRIN_MIX_UNROLL;
 
 __device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, double val)
 {
@@ -58,7 +68,7 @@ __device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, doub
 }
 
 template <int GROUPS, bool GUARD, int MODE>
-__global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArgs A)
+__global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(const ForceArgs A)
 {
     constexpr bool ADJ = MODE == MODE_ADJOINT;
     constexpr int GT = FORCE_THREADS / GROUPS;  // threads per j-group
@@ -142,7 +152,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_force_mixed(const ForceArg
                 for (int jj = 0; jj < JG; ++jj)
                     pair<GUARD, MODE, true>(T[jj], I, t, j0 + jj, idx[0], idx[1]);
             } else {
-#pragma unroll 4
+#pragma unroll MIX_UNROLL
                 for (int jj = 0; jj < JG; ++jj)
                     pair<GUARD, MODE>(T[jj], I, t);
             }

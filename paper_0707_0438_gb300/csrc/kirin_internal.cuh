@@ -24,9 +24,16 @@ struct __align__(16) JF64 {
     double2 q[4];
 };
 
-// j tile (shared-memory burst) and pipeline depth of the force kernels.
-constexpr int TILE_J = 128;
-constexpr int STAGES = 4;
+// j tile (shared-memory burst) and pipeline depth of the force kernels
+// (overridable at build time for tuning sweeps).
+#ifndef KIRIN_TILE_J
+#define KIRIN_TILE_J 128
+#endif
+#ifndef KIRIN_STAGES
+#define KIRIN_STAGES 4
+#endif
+constexpr int TILE_J = KIRIN_TILE_J;
+constexpr int STAGES = KIRIN_STAGES;
 constexpr int FORCE_THREADS = 256;
 constexpr int MAX_SPLIT = 1024;
 
@@ -119,9 +126,10 @@ cudaError_t launch_energy(int n, const double *m, const double *v, const double 
 cudaError_t launch_hermite_init(int n, double t, const double *acc, const double *jerk,
                                 double dt_min, double dt_max, double *ba, double *bj,
                                 double *bt, double *bdt, cudaStream_t st);
-cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end,
-                                int32_t *ilist, double *t_next_out, int32_t *count_out,
-                                cudaStream_t st);
+// counts: ceil(n / 1024) int32 of scratch; minw: one 64-bit word of scratch.
+cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end, int32_t *ilist,
+                                double *t_next_out, int32_t *count_out, unsigned long long *minw,
+                                int32_t *counts, cudaStream_t st);
 cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_next, double eta,
                                    double dt_min, double dt_max, int update_dt,
                                    const double *xp, const double *vp, const double *acc,
