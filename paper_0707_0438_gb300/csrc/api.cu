@@ -136,7 +136,7 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
         Shape s{c->fix_groups, std::min(c->fix_split, std::max(1, ntiles))};
         return s;
     }
-    const int per_thread = prec == KIRIN_MIXED ? 2 : 1;
+    const int per_thread = prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1;
     Shape best{1, 1};
     double best_cost = 1e300;
     const size_t cap_entries = (size_t)1 << 27;  // bound on n_split * 7 * n_i_pad doubles (1 GiB)
@@ -216,7 +216,7 @@ int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mo
     a.pot = pot;
     a.accumulate = accumulate;
     a.err = c->d_err;
-    const int i_cta = (c->prec == KIRIN_MIXED ? 2 : 1) * FORCE_THREADS / s.groups;
+    const int i_cta = (c->prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1) * FORCE_THREADS / s.groups;
     a.n_i_pad = (int)round_up(n_i, i_cta);
     if (s.n_split > 1) {
         int rc = ensure_partial(c, (size_t)s.n_split * 7 * a.n_i_pad);
@@ -411,7 +411,7 @@ int kirin_query(const kirin_ctx *ctx, int64_t *n_max, int32_t *tile_i, int32_t *
     if (n_max)
         *n_max = ctx->n_max;
     if (tile_i)
-        *tile_i = (ctx->prec == KIRIN_MIXED ? 2 : 1) * FORCE_THREADS;
+        *tile_i = (ctx->prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1) * FORCE_THREADS;
     if (tile_j)
         *tile_j = TILE_J;
     return KIRIN_OK;

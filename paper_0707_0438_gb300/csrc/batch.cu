@@ -462,6 +462,10 @@ int kirin_batch_create(kirin_batch **out, int32_t n_clusters, const int64_t *off
     if (ok) {
         int occ = 0;
         const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
+        if (smem > 48 * 1024) {
+            cudaFuncSetAttribute(k_batch_accel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_batch_accel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        }
         if (b->guard)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_accel<true>, FORCE_THREADS, smem);
         else

@@ -26,6 +26,12 @@ __device__ __forceinline__ void write_out64(const ForceArgs &A, int q, int k, do
         store_final(A, q, k, val);
 }
 
+// Dynamic shared memory: the tile ring, reused as the [GROUPS][7][I_CTA]
+// doubles of the cross-group reduction after the loop.
+constexpr size_t F64_RING_BYTES = (size_t)STAGES * TILE_J * sizeof(JF64);
+constexpr size_t F64_RED_BYTES = (size_t)7 * FORCE_THREADS * sizeof(double);
+constexpr size_t F64_SMEM_BYTES = F64_RING_BYTES > F64_RED_BYTES ? F64_RING_BYTES : F64_RED_BYTES;
+
 template <int GROUPS, int MODE>
 __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
 {
@@ -158,6 +164,7 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
             write_out64(A, q, kslot, res[q]);
     } else {
         __syncthreads();
+        static_assert((size_t)GROUPS * 7 * I_CTA * sizeof(double) <= F64_SMEM_BYTES, "reduction space");
         double *red = reinterpret_cast<double *>(smem_raw);  // [GROUPS][7][I_CTA]
 #pragma unroll
         for (int q = 0; q < 7; ++q)
@@ -182,7 +189,14 @@ cudaError_t launch_t(const ForceArgs &a, int n_split, cudaStream_t st)
     const int iblocks = (a.n_i + I_CTA - 1) / I_CTA;
     if (iblocks == 0)
         return cudaSuccess;
-    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JF64);
+    const size_t smem = F64_SMEM_BYTES;
+    if (smem > 48 * 1024) {
+        static bool opted = false;  // per template instance
+        if (!opted) {
+            cudaFuncSetAttribute(k_force_fp64<GROUPS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            opted = true;
+        }
+    }
     dim3 grid(iblocks, n_split);
     k_force_fp64<GROUPS, MODE><<<grid, FORCE_THREADS, smem, st>>>(a);
     return cudaGetLastError();
@@ -192,7 +206,9 @@ template <int GROUPS, int MODE>
 int occ_t()
 {
     int n = 0;
-    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JF64);
+    const size_t smem = F64_SMEM_BYTES;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_force_fp64<GROUPS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_fp64<GROUPS, MODE>, FORCE_THREADS, smem);
     return n;
 }

@@ -67,12 +67,21 @@ __device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, doub
         store_final(A, q, k, val);
 }
 
+// Dynamic shared memory of one CTA: the tile ring, reused after the loop as
+// the [GROUPS][7][I_CTA] doubles of the cross-group reduction (7 x
+// MIX_I_PER_THREAD x 256 doubles whatever GROUPS is), so the larger of the two.
+constexpr size_t MIX_RING_BYTES = (size_t)STAGES * TILE_J * sizeof(JMixed);
+constexpr size_t MIX_RED_BYTES = (size_t)7 * MIX_I_PER_THREAD * FORCE_THREADS * sizeof(double);
+constexpr size_t MIX_SMEM_BYTES = MIX_RING_BYTES > MIX_RED_BYTES ? MIX_RING_BYTES : MIX_RED_BYTES;
+
 template <int GROUPS, bool GUARD, int MODE>
 __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(const ForceArgs A)
 {
     constexpr bool ADJ = MODE == MODE_ADJOINT;
+    constexpr int NP = MIX_IPAIRS;              // packed i-pairs per thread
+    constexpr int NI = 2 * NP;                  // i-particles per thread
     constexpr int GT = FORCE_THREADS / GROUPS;  // threads per j-group
-    constexpr int I_CTA = 2 * GT;               // i-particles per CTA
+    constexpr int I_CTA = NI * GT;              // i-particles per CTA
     constexpr int JG = TILE_J / GROUPS;         // j per group and tile
     constexpr uint32_t TILE_BYTES = TILE_J * sizeof(JMixed);
     static_assert(GT >= 32, "a warp must read one j at a time (broadcast loads)");
@@ -86,11 +95,12 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
     const int s = tid - g * GT;
     const JMixed *__restrict__ J = static_cast<const JMixed *>(A.jimg);
 
-    // ---- the two i-particles of this thread (lanes x and y) ----
-    int idx[2];
+    // ---- the i-particles of this thread: slot s + q * GT of the CTA's block,
+    //      lanes (x, y) of pair p holding q = 2p and 2p + 1 ----
+    int idx[NI];
 #pragma unroll
-    for (int L = 0; L < 2; ++L) {
-        const int k = blockIdx.x * I_CTA + s + L * GT;
+    for (int q = 0; q < NI; ++q) {
+        const int k = blockIdx.x * I_CTA + s + q * GT;
         int i = -1;
         if (k < A.n_i) {
             i = A.ilist ? A.ilist[k] : k;
@@ -99,11 +109,15 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
                 i = -1;
             }
         }
-        idx[L] = i;
+        idx[q] = i;
     }
     const float eps2f = (float)A.eps2;
     const float rmin2f = (float)A.rmin2;
-    const IPair I = load_ipair(J + (idx[0] >= 0 ? idx[0] : 0), J + (idx[1] >= 0 ? idx[1] : 0), eps2f, rmin2f);
+    IPair I[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+        I[p] = load_ipair(J + (idx[2 * p] >= 0 ? idx[2 * p] : 0), J + (idx[2 * p + 1] >= 0 ? idx[2 * p + 1] : 0),
+                          eps2f, rmin2f);
     // the self pair is masked unless eps = 0 zeroes it anyway (in the adjoint,
     // w = m_k g_j - m_j g_k would vanish only if the compiler kept both
     // products rounded; a contracted multiply-add leaves ~u m g, times 1/eps^3)
@@ -130,11 +144,14 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
         }
     }
 
-    Tile7 t;
-    t.zero();
-    Lane7 acc0, acc1;
-    acc0.zero();
-    acc1.zero();
+    Tile7 t[NP];
+    Lane7 acc[NI];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+        t[p].zero();
+#pragma unroll
+    for (int q = 0; q < NI; ++q)
+        acc[q].zero();
 
     int since = 0;
     int k = 0;
@@ -146,19 +163,30 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
         if (ok) {
             const JMixed *__restrict__ T = tiles + st * TILE_J + g * JG;
             const int j0 = (tb + k) * TILE_J + g * JG;  // index of T[0]
-            const bool mine = (unsigned)(idx[0] - j0) < (unsigned)JG || (unsigned)(idx[1] - j0) < (unsigned)JG;
+            bool mine = false;
+#pragma unroll
+            for (int q = 0; q < NI; ++q)
+                mine = mine || (unsigned)(idx[q] - j0) < (unsigned)JG;
             if (need_mask && __any_sync(0xffffffffu, mine)) {
 #pragma unroll 2
-                for (int jj = 0; jj < JG; ++jj)
-                    pair<GUARD, MODE, true>(T[jj], I, t, j0 + jj, idx[0], idx[1]);
+                for (int jj = 0; jj < JG; ++jj) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        pair<GUARD, MODE, true>(T[jj], I[p], t[p], j0 + jj, idx[2 * p], idx[2 * p + 1]);
+                }
             } else {
 #pragma unroll MIX_UNROLL
-                for (int jj = 0; jj < JG; ++jj)
-                    pair<GUARD, MODE>(T[jj], I, t);
+                for (int jj = 0; jj < JG; ++jj) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        pair<GUARD, MODE>(T[jj], I[p], t[p]);
+                }
             }
             since += JG;
             if (since >= (ADJ ? FLUSH_J_ADJOINT : FLUSH_J)) {
-                fold<MODE>(t, acc0, acc1);
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+                    fold<MODE>(t[p], acc[2 * p], acc[2 * p + 1]);
                 since = 0;
             }
         }
@@ -186,39 +214,36 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
         }
         return;
     }
-    fold<MODE>(t, acc0, acc1);
-
-    double res0[7], res1[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        res0[q] = (double)acc0.h[q] + (double)acc0.l[q];
-        res1[q] = (double)acc1.h[q] + (double)acc1.l[q];
-    }
+    for (int p = 0; p < NP; ++p)
+        fold<MODE>(t[p], acc[2 * p], acc[2 * p + 1]);
 
     if (GROUPS == 1) {
-        const int k0 = blockIdx.x * I_CTA + s;
 #pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            write_out(A, q, k0, res0[q]);
-            write_out(A, q, k0 + GT, res1[q]);
+        for (int q = 0; q < NI; ++q) {
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+                write_out(A, c, blockIdx.x * I_CTA + s + q * GT, (double)acc[q].h[c] + (double)acc[q].l[c]);
         }
     } else {
         __syncthreads();  // all tiles consumed: reuse the ring as reduction space
+        static_assert((size_t)GROUPS * 7 * I_CTA * sizeof(double) <= MIX_SMEM_BYTES, "reduction space");
         double *red = reinterpret_cast<double *>(smem_raw);  // [GROUPS][7][I_CTA]
 #pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            red[(g * 7 + q) * I_CTA + s] = res0[q];
-            red[(g * 7 + q) * I_CTA + s + GT] = res1[q];
+        for (int q = 0; q < NI; ++q) {
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+                red[(g * 7 + c) * I_CTA + s + q * GT] = (double)acc[q].h[c] + (double)acc[q].l[c];
         }
         __syncthreads();
         for (int o = tid; o < 7 * I_CTA; o += FORCE_THREADS) {
-            const int q = o / I_CTA;
-            const int slot = o - q * I_CTA;
+            const int c = o / I_CTA;
+            const int slot = o - c * I_CTA;
             double sum = 0.0;
 #pragma unroll
             for (int gg = 0; gg < GROUPS; ++gg)
-                sum += red[(gg * 7 + q) * I_CTA + slot];
-            write_out(A, q, blockIdx.x * I_CTA + slot, sum);
+                sum += red[(gg * 7 + c) * I_CTA + slot];
+            write_out(A, c, blockIdx.x * I_CTA + slot, sum);
         }
     }
 }
@@ -226,11 +251,19 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
 template <int GROUPS, bool GUARD, int MODE>
 cudaError_t launch_t(const ForceArgs &a, int n_split, cudaStream_t st)
 {
-    constexpr int I_CTA = 2 * FORCE_THREADS / GROUPS;
+    constexpr int I_CTA = MIX_I_PER_THREAD * FORCE_THREADS / GROUPS;
     const int iblocks = (a.n_i + I_CTA - 1) / I_CTA;
     if (iblocks == 0)
         return cudaSuccess;
-    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
+    const size_t smem = MIX_SMEM_BYTES;
+    if (smem > 48 * 1024) {
+        static bool opted = false;  // per template instance
+        if (!opted) {
+            cudaFuncSetAttribute(k_force_mixed<GROUPS, GUARD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            opted = true;
+        }
+    }
     dim3 grid(iblocks, n_split);
     k_force_mixed<GROUPS, GUARD, MODE><<<grid, FORCE_THREADS, smem, st>>>(a);
     return cudaGetLastError();
@@ -240,7 +273,10 @@ template <int GROUPS, bool GUARD, int MODE>
 int occ_t()
 {
     int n = 0;
-    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
+    const size_t smem = MIX_SMEM_BYTES;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_force_mixed<GROUPS, GUARD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_mixed<GROUPS, GUARD, MODE>,
                                                   FORCE_THREADS, smem);
     return n;

@@ -32,8 +32,14 @@ struct __align__(16) JF64 {
 #ifndef KIRIN_STAGES
 #define KIRIN_STAGES 4
 #endif
+#ifndef KIRIN_MIX_IPAIRS
+#define KIRIN_MIX_IPAIRS 1
+#endif
 constexpr int TILE_J = KIRIN_TILE_J;
 constexpr int STAGES = KIRIN_STAGES;
+// Mixed kernel: packed FP32x2 i-pairs per thread, hence i-particles per thread.
+constexpr int MIX_IPAIRS = KIRIN_MIX_IPAIRS;
+constexpr int MIX_I_PER_THREAD = 2 * MIX_IPAIRS;
 constexpr int FORCE_THREADS = 256;
 constexpr int MAX_SPLIT = 1024;
 

@@ -75,7 +75,7 @@ Shape pick_shape(const DeviceSetup &s, int64_t n_i, int ntiles, bool guard)
     double best_cost = 1e300;
     for (int k = 0; k < 4; ++k) {
         const int groups = 1 << k;
-        const int i_cta = 2 * FORCE_THREADS / groups;
+        const int i_cta = MIX_I_PER_THREAD * FORCE_THREADS / groups;
         const int64_t iblocks = (n_i + i_cta - 1) / i_cta;
         const double slots = (double)s.nsm * (guard ? s.occ_guard[k] : s.occ[k]);
         for (int ns = 1; ns <= std::min(ntiles, MAX_SPLIT); ++ns) {
@@ -150,8 +150,8 @@ extern "C" int kirin_forces_noalloc(int64_t n, const double *m, const double *x,
     a.jerk = jerk;
     a.pot = pot;
     a.partial = sh.n_split > 1 ? partial : nullptr;
-    a.n_i_pad = (int)((n_i + 2 * FORCE_THREADS / sh.groups - 1) / (2 * FORCE_THREADS / sh.groups) *
-                      (2 * FORCE_THREADS / sh.groups));
+    const int i_cta = MIX_I_PER_THREAD * FORCE_THREADS / sh.groups;
+    a.n_i_pad = (int)((n_i + i_cta - 1) / i_cta * i_cta);
     a.accumulate = 0;
     a.err = err;
     if (launch_force_mixed(a, sh, guard, MODE_ACC_JERK_POT, st) != cudaSuccess)
