@@ -91,6 +91,15 @@ int kirin_set_stream(kirin_ctx *ctx, void *stream);
  * (a cost model over waves of CTAs).  Errors: EINVAL. */
 int kirin_set_launch(kirin_ctx *ctx, int32_t groups, int32_t n_split);
 
+/* A tuned shape table (the paper wishes CUDA picked threads and bundles by
+ * itself, Sect. 5): entry k gives the (groups, n_split) of full force calls
+ * (acc, jerk, pot) with n_i <= n_i_max[k], for the context's current
+ * precision; n_i_max ascending, at most 64 entries; calls beyond the last
+ * entry use the cost model.  n_entries = 0 clears the table.  A fixed shape
+ * (kirin_set_launch) takes precedence.  Errors: EINVAL. */
+int kirin_set_launch_table(kirin_ctx *ctx, int32_t n_entries, const int64_t *n_i_max,
+                           const int32_t *groups, const int32_t *n_split);
+
 /* The shape that a force call for n_i i-particles would use now. */
 int kirin_get_launch(kirin_ctx *ctx, int64_t n_i, int32_t *groups, int32_t *n_split);
 

@@ -58,6 +58,7 @@ _SIGS = {
     "kirin_set_stream": (ctypes.c_int, [_P, _P]),
     "kirin_set_launch": (ctypes.c_int, [_P, _I32, _I32]),
     "kirin_get_launch": (ctypes.c_int, [_P, _I64, _PI32, _PI32]),
+    "kirin_set_launch_table": (ctypes.c_int, [_P, _I32, _PI64, _PI32, _PI32]),
     "kirin_set_j_particles": (ctypes.c_int, [_P, _I64, _I64, _PD, _PD, _PD, _PD, _PD, _PD]),
     "kirin_set_j_particles_dev": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _P, _P, _P, _P]),
     "kirin_set_nj": (ctypes.c_int, [_P, _I64]),
@@ -208,6 +209,15 @@ class Kirin:
 
     def set_launch(self, groups=0, n_split=0):
         self._check(self.lib.kirin_set_launch(self.ctx, int(groups), int(n_split)), "kirin_set_launch")
+
+    def set_launch_table(self, entries):
+        """entries: [(n_i_max, groups, n_split), ...] ascending in n_i_max; [] clears the table."""
+        ni = np.ascontiguousarray([e[0] for e in entries], dtype=np.int64)
+        gr = np.ascontiguousarray([e[1] for e in entries], dtype=np.int32)
+        sp = np.ascontiguousarray([e[2] for e in entries], dtype=np.int32)
+        self._check(self.lib.kirin_set_launch_table(self.ctx, len(entries), ni.ctypes.data_as(_PI64),
+                                                    gr.ctypes.data_as(_PI32), sp.ctypes.data_as(_PI32)),
+                    "kirin_set_launch_table")
 
     def get_launch(self, n_i):
         g, s = ctypes.c_int32(), ctypes.c_int32()

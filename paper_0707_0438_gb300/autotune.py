@@ -1,0 +1,105 @@
+"""Autotuner of the force kernel's launch shape (j-groups per CTA x j-split CTAs).
+
+Sect. 5 of the paper notes that the best number of threads and bundles
+depends on the GPU and wishes CUDA picked them itself; Sect. 3.2 splits j when
+the active block is small.  Here the candidates are timed on the device,
+through the C ABI, for a ladder of active-block sizes, and the winners become
+the context's launch table (kirin_set_launch_table).  Results are cached in a
+JSON file keyed by GPU name, SM count, precision and n_j.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from .abi import Kirin
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "kirin_gb300", "launch_table.json")
+
+
+def _ladder(n_j: int):
+    """Active-block sizes timed: powers of two below n_j, and n_j."""
+    out, n = [], 1
+    while n < n_j:
+        out.append(n)
+        n *= 2
+    out.append(n_j)
+    return out
+
+
+def _candidates(auto, ntiles):
+    g0, s0 = auto
+    cands = {(g0, s0)}
+    for g in (1, 2, 4, 8):
+        for s in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256):
+            if s <= ntiles:
+                cands.add((g, s))
+    for s in (max(1, s0 // 2), s0 * 2):
+        if s <= ntiles:
+            cands.add((g0, s))
+    return sorted(cands)
+
+
+def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, device_name: str = "",
+         cache: str | None = DEFAULT_CACHE, precision: str = "mixed"):
+    """Time launch shapes for the particles already set in `k` (n_j of them) and install
+    the best as its launch table; returns [(n_i_max, groups, n_split, seconds), ...]."""
+    import torch
+
+    key = f"{device_name}|{precision}|{n_j}"
+    if cache and os.path.exists(cache):
+        try:
+            table = json.load(open(cache)).get(key)
+        except (OSError, ValueError):
+            table = None
+        if table:
+            k.set_launch_table([tuple(e[:3]) for e in table])
+            return table
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rng = np.random.default_rng(seed)
+    ntiles = (n_j + 127) // 128
+    table = []
+    for n_i in _ladder(n_j):
+        il = torch.tensor(np.sort(rng.choice(n_j, n_i, replace=False)).astype(np.int32), device=dev)
+        acc = torch.empty((n_i, 3), dtype=torch.float64, device=dev)
+        jerk = torch.empty_like(acc)
+        pot = torch.empty(n_i, dtype=torch.float64, device=dev)
+        k.set_launch(0, 0)
+        auto = k.get_launch(n_i)
+        cands = _candidates(auto, ntiles)
+        if quick:  # prune: the groups the cost model chose and its neighbours
+            cands = [c for c in cands if c == auto or abs(np.log2(c[0]) - np.log2(auto[0])) <= 1]
+        best = None
+        for g, s in cands:
+            k.set_launch(g, s)
+            k.compute_forces_dev(il, acc, jerk, pot)  # warm-up
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            for _ in range(reps):
+                k.compute_forces_dev(il, acc, jerk, pot)
+            ev[1].record()
+            torch.cuda.synchronize()
+            t = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+            if best is None or t < best[3]:
+                best = (n_i, g, s, t)
+        table.append(best)
+    k.set_launch(0, 0)
+    k.sync()
+    # each timed size covers the sizes up to the geometric mean with the next one
+    entries = []
+    for a, b in zip(table, table[1:] + [None]):
+        hi = int(np.sqrt(float(a[0]) * b[0])) if b is not None else n_j
+        entries.append((int(max(hi, a[0])), int(a[1]), int(a[2]), float(a[3])))
+    k.set_launch_table([e[:3] for e in entries])
+    if cache:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        try:
+            data = json.load(open(cache)) if os.path.exists(cache) else {}
+        except (OSError, ValueError):
+            data = {}
+        data[key] = entries
+        with open(cache, "w") as f:
+            json.dump(data, f)
+    return entries

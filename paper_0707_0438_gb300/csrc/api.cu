@@ -65,8 +65,14 @@ struct kirin_ctx {
     bool hermite_ready = false;
     double eta = 0.01, dt_min = 1.0 / (1 << 20), dt_max = 0.125, t_shared = 0;
 
-    // launch-shape override (0 = automatic) and occupancy cache
+    // launch-shape override (0 = automatic), tuned table and occupancy cache
     int fix_groups = 0, fix_split = 0;
+    static constexpr int MAX_TABLE = 64;
+    int table_n = 0;
+    int64_t table_ni[MAX_TABLE] = {};   // entry k covers n_i <= table_ni[k] (ascending)
+    int32_t table_groups[MAX_TABLE] = {};
+    int32_t table_split[MAX_TABLE] = {};
+    int table_prec = -1;                // the table applies to this precision, full force mode
     int occ[2][3][2][4] = {};  // [prec][mode][guard][log2 groups]
 
     char msg[256] = {0};
@@ -135,6 +141,11 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
     if (c->fix_groups > 0 && c->fix_split > 0) {
         Shape s{c->fix_groups, std::min(c->fix_split, std::max(1, ntiles))};
         return s;
+    }
+    if (c->table_n > 0 && prec == c->table_prec && mode == MODE_ACC_JERK_POT) {
+        for (int k = 0; k < c->table_n; ++k)
+            if (n_i <= c->table_ni[k])
+                return Shape{c->table_groups[k], std::min<int>(c->table_split[k], std::max(1, ntiles))};
     }
     const int per_thread = prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1;
     Shape best{1, 1};
@@ -459,6 +470,29 @@ int kirin_set_launch(kirin_ctx *ctx, int32_t groups, int32_t n_split)
         return KIRIN_EINVAL;
     ctx->fix_groups = groups;
     ctx->fix_split = n_split;
+    return KIRIN_OK;
+}
+
+int kirin_set_launch_table(kirin_ctx *ctx, int32_t n_entries, const int64_t *n_i_max, const int32_t *groups,
+                           const int32_t *n_split)
+{
+    if (!ctx || n_entries < 0 || n_entries > kirin_ctx::MAX_TABLE)
+        return KIRIN_EINVAL;
+    if (n_entries > 0 && (!n_i_max || !groups || !n_split))
+        return KIRIN_EINVAL;
+    for (int k = 0; k < n_entries; ++k) {
+        const int g = groups[k];
+        if ((g != 1 && g != 2 && g != 4 && g != 8) || n_split[k] < 1 || n_split[k] > MAX_SPLIT || n_i_max[k] < 0 ||
+            (k > 0 && n_i_max[k] <= n_i_max[k - 1]))
+            return KIRIN_EINVAL;
+    }
+    for (int k = 0; k < n_entries; ++k) {
+        ctx->table_ni[k] = n_i_max[k];
+        ctx->table_groups[k] = groups[k];
+        ctx->table_split[k] = n_split[k];
+    }
+    ctx->table_n = n_entries;
+    ctx->table_prec = ctx->prec;
     return KIRIN_OK;
 }
 
