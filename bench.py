@@ -218,6 +218,8 @@ def run_native(args):
     k = abi.Kirin(n, p.eps, precision="mixed", device=local, stream=sp)
     k.set_j_particles_dev(m_d, x_d, v_d)
     k.sync()
+    from paper_0707_0438_gb300 import autotune
+    tuned = autotune.install(k, n, torch.cuda.get_device_name(dev), "mixed")
     groups, n_split = k.get_launch(n)
     launches_per_step = 2 + (1 if n_split > 1 else 0)  # predictor/pack, force, split reduction
 
@@ -370,7 +372,8 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 pair math, double-single positions, f64 results", "data": "synthetic",
-        "config": dict(_config(n, "mixed"), launch={"groups": groups, "n_split": n_split}),
+        "config": dict(_config(n, "mixed"), launch={"groups": groups, "n_split": n_split,
+                                                     "from": "tuned table" if tuned else "cost model"}),
         "gflops_k60": 60.0 * value / 1e9, "gflops_k38_equiv": 38.0 * value / 1e9,
         "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
         "roofline": roof, "cpu_baseline": cpu,

@@ -17,6 +17,8 @@ import numpy as np
 from .abi import Kirin
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "kirin_gb300", "launch_table.json")
+# Tables measured on this project's GPUs (python -m paper_0707_0438_gb300.autotune --n N --out FILE).
+PACKAGED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_launch_tables.json")
 
 
 def _ladder(n_j: int):
@@ -29,11 +31,14 @@ def _ladder(n_j: int):
     return out
 
 
-def _candidates(auto, ntiles):
+def _candidates(auto, ntiles, big):
+    """Shapes to time: every j-group count with a ladder of splits (only a few splits
+    when the block alone fills the GPU many times over)."""
     g0, s0 = auto
     cands = {(g0, s0)}
+    splits = (1, 2, 3, 4) if big else (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
     for g in (1, 2, 4, 8):
-        for s in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256):
+        for s in splits:
             if s <= ntiles:
                 cands.add((g, s))
     for s in (max(1, s0 // 2), s0 * 2):
@@ -67,8 +72,10 @@ def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, d
         jerk = torch.empty_like(acc)
         pot = torch.empty(n_i, dtype=torch.float64, device=dev)
         k.set_launch(0, 0)
+        k.set_launch_table([])
         auto = k.get_launch(n_i)
-        cands = _candidates(auto, ntiles)
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        cands = _candidates(auto, ntiles, big=n_i >= 16 * nsm * 512)
         if quick:  # prune: the groups the cost model chose and its neighbours
             cands = [c for c in cands if c == auto or abs(np.log2(c[0]) - np.log2(auto[0])) <= 1]
         best = None
@@ -103,3 +110,44 @@ def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, d
         with open(cache, "w") as f:
             json.dump(data, f)
     return entries
+
+
+def install(k: Kirin, n_j: int, device_name: str, precision: str = "mixed", path: str = PACKAGED) -> bool:
+    """Install a stored table for this GPU, precision and n_j, if there is one."""
+    try:
+        table = json.load(open(path)).get(f"{device_name}|{precision}|{n_j}")
+    except (OSError, ValueError):
+        return False
+    if not table:
+        return False
+    k.set_launch_table([tuple(e[:3]) for e in table])
+    return True
+
+
+def main(argv=None):
+    import argparse
+
+    import torch
+
+    from . import workloads
+    ap = argparse.ArgumentParser(description="time launch shapes and store the winners")
+    ap.add_argument("--n", type=int, nargs="+", default=[1 << 20, 65536])
+    ap.add_argument("--out", default=PACKAGED)
+    ap.add_argument("--reps", type=int, default=2)
+    args = ap.parse_args(argv)
+    name = torch.cuda.get_device_name(0)
+    for n in args.n:
+        p = workloads.config_large(n)
+        k = Kirin(n, p.eps, stream=torch.cuda.current_stream().cuda_stream)
+        k.set_j_particles(p.m, p.x, p.v)
+        if os.path.exists(args.out):  # re-time: drop a stored entry for this key first
+            data = json.load(open(args.out))
+            data.pop(f"{name}|mixed|{n}", None)
+            json.dump(data, open(args.out, "w"), indent=0)
+        entries = tune(k, n, reps=args.reps, device_name=name, cache=args.out)
+        print(n, [(e[0], e[1], e[2], round(n * min(e[0], n) / e[3] / 1e9, 1)) for e in entries], flush=True)
+        k.close()
+
+
+if __name__ == "__main__":
+    main()
