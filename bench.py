@@ -427,9 +427,13 @@ def run_block(args):
     n = 65536 if args.n == N_DEFAULT else args.n
     p = workloads.config_block(n)
     out = {}
+    from paper_0707_0438_gb300 import autotune
+    gpu = torch.cuda.get_device_name(0)
     for precision, t_end in (("mixed", 0.125), ("fp64", args.fp64_t_end)):
         with abi.Kirin(n, p.eps, precision=precision) as k:
             k.set_j_particles(p.m, p.x, p.v)
+            if precision == "mixed":
+                autotune.install(k, n, gpu, "mixed")
             kin0, pot0 = k.energy()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
