@@ -367,6 +367,15 @@ def run_native(args):
                          f"(max SM clock, {peak_src}); achieved counts k=60 flops per pair (Eq. 3)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / _fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
+    # measured FMA rates of this GPU (independent FMA chains on every SM), for context
+    try:
+        fma = {kind: abi.measure_fma_rate(kind, local) / 1e12 for kind in ("fp32", "fp32x2", "fp64")}
+        roof["measured_fma_tflops"] = fma
+        roof["frac_of_measured_fp32x2"] = achieved / fma["fp32x2"]
+        # the FP64 kernel: ~40 FP64 flops per interaction (30 arithmetic + the library rsqrt)
+        extra["fp64"]["frac_of_measured_fp64_at_40_flops"] = 40.0 * fp64_rate / (fma["fp64"] * 1e12)
+    except abi.KirinError:
+        pass
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -294,6 +294,14 @@ int kirin_forces_noalloc(int64_t n, const double *m, const double *x, const doub
                          const int32_t *i_list, double eps, double G, double r_min, double *acc,
                          double *jerk, double *pot, unsigned *status, void *stream);
 
+/* ---- roofline denominators ----
+ * Sustained fused multiply-add rate of the GPU `device` (2 flops per lane):
+ * kind 0 = FP32 FFMA, 1 = packed FP32x2 FFMA2, 2 = FP64 DFMA, measured with
+ * independent FMA chains on every SM (no counterpart in the paper, whose
+ * Sect. 4.1 derives the 8800GTX peak from its unit count and clock).
+ * Synchronous.  Errors: EINVAL, ECUDA. */
+int kirin_measure_fma_rate(int32_t device, int32_t kind, double *flops_per_s);
+
 /* Human-readable name of a return code (static string). */
 const char *kirin_strerror(int code);
 

@@ -85,6 +85,7 @@ _SIGS = {
     "kirin_batch_sync": (ctypes.c_int, [_P]),
     "kirin_batch_accel": (ctypes.c_int, [_P, _PD]),
     "kirin_forces_noalloc": (ctypes.c_int, [_I64, _P, _P, _P, _I64, _P, _D, _D, _D, _P, _P, _P, _P, _P]),
+    "kirin_measure_fma_rate": (ctypes.c_int, [_I32, _I32, _PD]),
     "kirin_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kirin_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -389,6 +390,16 @@ class KirinBatch:
             self.close()
         except Exception:
             pass
+
+
+def measure_fma_rate(kind: str, device: int = 0) -> float:
+    """Measured FMA throughput in flop/s: kind "fp32", "fp32x2" or "fp64"."""
+    code = {"fp32": 0, "fp32x2": 1, "fp64": 2}[kind]
+    out = ctypes.c_double()
+    rc = lib().kirin_measure_fma_rate(int(device), code, ctypes.byref(out))
+    if rc != KIRIN_OK:
+        raise KirinError(rc, "kirin_measure_fma_rate")
+    return out.value
 
 
 def _prec(p) -> int:
