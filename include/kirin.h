@@ -156,6 +156,23 @@ int kirin_get_acc_jerk_pot(kirin_ctx *ctx, double *acc, double *jerk, double *po
 int kirin_compute_forces_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list,
                              double *acc, double *jerk, double *pot);
 
+/* Nearest neighbours (Sect. 3.3.1: the GRAPE hardware returns the nearest
+ * neighbour of every i-particle and kira needs it; the search runs inside the
+ * force loop).  Device twin of compute + get with, in addition, the index of
+ * the nearest j != i (nn, int32, n_i; -1 if there is no other particle) and
+ * its squared distance |x_j - x_i|^2 (nn_r2, FP64, n_i), either may be NULL.
+ * "Nearest" is decided on s^2 = |d|^2 + eps^2 in the precision of the pair
+ * arithmetic (FP32 for KIRIN_MIXED), the smallest index on ties. */
+int kirin_compute_forces_nn_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list, double *acc,
+                                double *jerk, double *pot, int32_t *nn, double *nn_r2);
+
+/* Host-pointer path: with enable != 0, every kirin_compute_forces also
+ * searches neighbours, and kirin_get_nn copies the last call's results (in
+ * i_list order; host arrays of n_i, either may be NULL).  kirin_get_nn
+ * synchronises.  Errors: ESTATE (the last compute did not search). */
+int kirin_set_nn(kirin_ctx *ctx, int32_t enable);
+int kirin_get_nn(kirin_ctx *ctx, int32_t *nn, double *nn_r2);
+
 /* Wait for all work of the context and report device-side errors. */
 int kirin_sync(kirin_ctx *ctx);
 

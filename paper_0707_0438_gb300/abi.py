@@ -66,6 +66,9 @@ _SIGS = {
     "kirin_compute_forces": (ctypes.c_int, [_P, _I64, _PI32]),
     "kirin_get_acc_jerk_pot": (ctypes.c_int, [_P, _PD, _PD, _PD]),
     "kirin_compute_forces_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P]),
+    "kirin_compute_forces_nn_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P]),
+    "kirin_set_nn": (ctypes.c_int, [_P, _I32]),
+    "kirin_get_nn": (ctypes.c_int, [_P, _PI32, _PD]),
     "kirin_sync": (ctypes.c_int, [_P]),
     "kirin_energy": (ctypes.c_int, [_P, _PD, _PD, _PD]),
     "kirin_hermite_init": (ctypes.c_int, [_P, _D, _D, _D, _D]),
@@ -281,6 +284,22 @@ class Kirin:
         n_i = self.n_j if i_list is None else i_list.shape[0]
         self._check(self.lib.kirin_compute_forces_dev(self.ctx, int(n_i), _dev(i_list), _dev(acc), _dev(jerk),
                                                       _dev(pot)), "kirin_compute_forces_dev")
+
+    def compute_forces_nn_dev(self, i_list, acc, jerk, pot, nn, nn_r2):
+        n_i = self.n_j if i_list is None else i_list.shape[0]
+        self._check(self.lib.kirin_compute_forces_nn_dev(self.ctx, int(n_i), _dev(i_list), _dev(acc), _dev(jerk),
+                                                         _dev(pot), _dev(nn), _dev(nn_r2)),
+                    "kirin_compute_forces_nn_dev")
+
+    def set_nn(self, enable=True):
+        self._check(self.lib.kirin_set_nn(self.ctx, 1 if enable else 0), "kirin_set_nn")
+
+    def get_nn(self):
+        n = self._pending
+        nn = np.empty(n, dtype=np.int32)
+        r2 = np.empty(n)
+        self._check(self.lib.kirin_get_nn(self.ctx, nn.ctypes.data_as(_PI32), _dp(r2)), "kirin_get_nn")
+        return nn, r2
 
     def sync(self):
         self._check(self.lib.kirin_sync(self.ctx), "kirin_sync")

@@ -73,7 +73,13 @@ struct kirin_ctx {
     int32_t table_groups[MAX_TABLE] = {};
     int32_t table_split[MAX_TABLE] = {};
     int table_prec = -1;                // the table applies to this precision, full force mode
-    int occ[2][3][2][4] = {};  // [prec][mode][guard][log2 groups]
+    int occ[2][N_MODES][2][4] = {};  // [prec][mode][guard][log2 groups]
+
+    // nearest-neighbour search of the host-pointer path (GRAPE's neighbour list)
+    bool want_nn = false;
+    bool nn_valid = false;
+    int32_t *d_nn = nullptr;
+    double *d_nn_r2 = nullptr;
 
     char msg[256] = {0};
 };
@@ -157,7 +163,7 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
         const double slots = (double)c->nsm * ctas_per_sm(c, prec, mode, guard, groups);
         const int max_split = std::min(ntiles, MAX_SPLIT);
         for (int ns = 1; ns <= max_split; ns = ns < 64 ? ns + 1 : ns * 5 / 4) {
-            if (ns > 1 && (size_t)ns * 7 * iblocks * i_cta > cap_entries)
+            if (ns > 1 && (size_t)ns * 9 * iblocks * i_cta > cap_entries)
                 break;
             const double ctas = (double)iblocks * ns;
             const double waves = ceil(ctas / slots);
@@ -205,7 +211,7 @@ int ensure_images(kirin_ctx *c)
 
 // Enqueue one force launch (plus split reduction) over the current images.
 int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mode, double *acc,
-              double *jerk, double *pot, int accumulate = 0)
+              double *jerk, double *pot, int accumulate = 0, int32_t *nn = nullptr, double *nn_r2 = nullptr)
 {
     if (n_i == 0)
         return KIRIN_OK;
@@ -227,10 +233,13 @@ int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mo
     a.pot = pot;
     a.accumulate = accumulate;
     a.err = c->d_err;
+    a.nn = nn;
+    a.nn_r2 = nn_r2;
+    a.nq = mode == MODE_NN ? 9 : 7;
     const int i_cta = (c->prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1) * FORCE_THREADS / s.groups;
     a.n_i_pad = (int)round_up(n_i, i_cta);
     if (s.n_split > 1) {
-        int rc = ensure_partial(c, (size_t)s.n_split * 7 * a.n_i_pad);
+        int rc = ensure_partial(c, (size_t)s.n_split * a.nq * a.n_i_pad);
         if (rc)
             return rc;
         a.partial = c->d_partial;
@@ -273,7 +282,7 @@ void free_all(kirin_ctx *c)
 {
     void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
                     c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
-                    c->d_count, c->d_sel_counts};
+                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -380,6 +389,8 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
     dalloc((void **)&c->d_scal, 4 * sizeof(double));
     dalloc((void **)&c->d_count, sizeof(int32_t));
     dalloc((void **)&c->d_sel_counts, ((n + 1023) / 1024 + 1) * sizeof(int32_t));
+    dalloc((void **)&c->d_nn, n * sizeof(int32_t));
+    dalloc((void **)&c->d_nn_r2, n * sizeof(double));
     if (ok && cudaMallocHost((void **)&c->h_ilist, n * sizeof(int32_t)) != cudaSuccess)
         ok = false;
     if (ok && cudaMallocHost((void **)&c->h_scal, 4 * sizeof(double)) != cudaSuccess)
@@ -615,12 +626,56 @@ int kirin_compute_forces(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list)
     int rc = ensure_images(ctx);
     if (rc)
         return rc;
-    rc = run_force(ctx, n_i, d_list, (int)ctx->n_j, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
+    const int mode = ctx->want_nn ? MODE_NN : MODE_ACC_JERK_POT;
+    rc = run_force(ctx, n_i, d_list, (int)ctx->n_j, mode, ctx->d_acc, ctx->d_jerk, ctx->d_pot, 0, ctx->d_nn,
+                   ctx->d_nn_r2);
     if (rc)
         return rc;
     ctx->pending = true;
     ctx->pending_n = n_i;
+    ctx->nn_valid = ctx->want_nn;
     return KIRIN_OK;
+}
+
+int kirin_set_nn(kirin_ctx *ctx, int32_t enable)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    ctx->want_nn = enable != 0;
+    return KIRIN_OK;
+}
+
+int kirin_get_nn(kirin_ctx *ctx, int32_t *nn, double *nn_r2)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (!ctx->nn_valid)
+        return set_msg(ctx, KIRIN_ESTATE, "get_nn: the last compute_forces did not search neighbours");
+    DeviceGuard dg(ctx->device);
+    const size_t n = (size_t)ctx->pending_n;
+    if (nn)
+        CK(ctx, cudaMemcpyAsync(nn, ctx->d_nn, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    if (nn_r2)
+        CK(ctx, cudaMemcpyAsync(nn_r2, ctx->d_nn_r2, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return read_device_errors(ctx);
+}
+
+int kirin_compute_forces_nn_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list, double *acc, double *jerk,
+                                double *pot, int32_t *nn, double *nn_r2)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    if (ctx->n_j == 0)
+        return set_msg(ctx, KIRIN_ESTATE, "compute_forces_nn_dev: no particles");
+    if (!i_list)
+        n_i = ctx->n_j;
+    if (n_i < 0 || n_i > ctx->n_max)
+        return set_msg(ctx, KIRIN_EINVAL, "compute_forces_nn_dev: n_i out of range");
+    DeviceGuard dg(ctx->device);
+    int rc = ensure_images(ctx);
+    if (rc)
+        return rc;
+    return run_force(ctx, n_i, i_list, (int)ctx->n_j, MODE_NN, acc, jerk, pot, 0, nn, nn_r2);
 }
 
 int kirin_get_acc_jerk_pot(kirin_ctx *ctx, double *acc, double *jerk, double *pot)

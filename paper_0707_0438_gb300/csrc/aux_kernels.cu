@@ -16,7 +16,8 @@ constexpr int AUX_THREADS = 256;
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // Sum the n_split partial results of every (i, quantity) in split order and
-// write the scaled outputs (acc, jerk: G * sum; pot: -G * sum).
+// write the scaled outputs (acc, jerk: G * sum; pot: -G * sum); with the
+// neighbour search also the nearest (r2, j) over the splits.
 __global__ void k_reduce_splits(const ForceArgs A)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -26,8 +27,15 @@ __global__ void k_reduce_splits(const ForceArgs A)
     for (int q = 0; q < 7; ++q) {
         double sum = 0.0;
         for (int y = 0; y < A.n_split; ++y)
-            sum += A.partial[((size_t)y * 7 + q) * A.n_i_pad + k];
+            sum += A.partial[((size_t)y * A.nq + q) * A.n_i_pad + k];
         store_final(A, q, k, sum);
+    }
+    if (A.nq > 7) {  // nearest neighbour: lexicographic minimum over the splits
+        double r2 = INFINITY, j = -1.0;
+        for (int y = 0; y < A.n_split; ++y)
+            nn_min(r2, j, A.partial[((size_t)y * A.nq + 7) * A.n_i_pad + k],
+                   A.partial[((size_t)y * A.nq + 8) * A.n_i_pad + k]);
+        store_nn(A, k, r2, j);
     }
 }
 

@@ -26,17 +26,31 @@ __device__ __forceinline__ void write_out64(const ForceArgs &A, int q, int k, do
         store_final(A, q, k, val);
 }
 
-// Dynamic shared memory: the tile ring, reused as the [GROUPS][7][I_CTA]
+__device__ __forceinline__ void write_nn64(const ForceArgs &A, int k, double r2, double j)
+{
+    if (k >= A.n_i)
+        return;
+    if (A.n_split > 1) {
+        A.partial[((size_t)blockIdx.y * A.nq + 7) * A.n_i_pad + k] = r2;
+        A.partial[((size_t)blockIdx.y * A.nq + 8) * A.n_i_pad + k] = j;
+    } else {
+        store_nn(A, k, r2, j);
+    }
+}
+
+// Dynamic shared memory: the tile ring, reused as the [GROUPS][nq][I_CTA]
 // doubles of the cross-group reduction after the loop.
 constexpr size_t F64_RING_BYTES = (size_t)STAGES * TILE_J * sizeof(JF64);
-constexpr size_t F64_RED_BYTES = (size_t)7 * FORCE_THREADS * sizeof(double);
+constexpr size_t F64_RED_BYTES = (size_t)9 * FORCE_THREADS * sizeof(double);
 constexpr size_t F64_SMEM_BYTES = F64_RING_BYTES > F64_RED_BYTES ? F64_RING_BYTES : F64_RED_BYTES;
 
 template <int GROUPS, int MODE>
 __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
 {
     constexpr bool ADJ = MODE == MODE_ADJOINT;
-    constexpr bool JERK = MODE == MODE_ACC_JERK_POT;
+    constexpr bool NN = MODE == MODE_NN;
+    constexpr bool JERK = MODE == MODE_ACC_JERK_POT || NN;
+    constexpr int NQ = NN ? 9 : 7;
     constexpr int GT = FORCE_THREADS / GROUPS;
     constexpr int I_CTA = GT;
     constexpr int JG = TILE_J / GROUPS;
@@ -88,6 +102,8 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
     }
 
     double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0, pt = 0;
+    double nn_r2 = INFINITY;  // nearest j != i so far (strict < in increasing j: smallest index on ties)
+    int nn_j = -1;
     int k = 0;
     bool aborted = false;
     for (; k < nt; ++k) {
@@ -105,6 +121,10 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
                 const double s2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
                 double rinv = rsqrt(fmax(s2, rmin2));
                 rinv = (s2 == 0.0 || jbase + jj == i) ? 0.0 : rinv;
+                if (NN && jbase + jj != i && s2 < nn_r2) {
+                    nn_r2 = s2;
+                    nn_j = jbase + jj;
+                }
                 const double rinv2 = rinv * rinv;
                 if (ADJ) {
                     // w = m_k g_j - m_j g_k;  dL/dx_k += K(d) w;  dL/dm_k -= g_j.d / s^3
@@ -162,13 +182,19 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
 #pragma unroll
         for (int q = 0; q < 7; ++q)
             write_out64(A, q, kslot, res[q]);
+        if (NN)
+            write_nn64(A, kslot, nn_r2, (double)nn_j);
     } else {
         __syncthreads();
-        static_assert((size_t)GROUPS * 7 * I_CTA * sizeof(double) <= F64_SMEM_BYTES, "reduction space");
-        double *red = reinterpret_cast<double *>(smem_raw);  // [GROUPS][7][I_CTA]
+        static_assert((size_t)GROUPS * NQ * I_CTA * sizeof(double) <= F64_SMEM_BYTES, "reduction space");
+        double *red = reinterpret_cast<double *>(smem_raw);  // [GROUPS][NQ][I_CTA]
 #pragma unroll
         for (int q = 0; q < 7; ++q)
-            red[(g * 7 + q) * I_CTA + s] = res[q];
+            red[(g * NQ + q) * I_CTA + s] = res[q];
+        if (NN) {
+            red[(g * NQ + 7) * I_CTA + s] = nn_r2;
+            red[(g * NQ + 8) * I_CTA + s] = (double)nn_j;
+        }
         __syncthreads();
         for (int o = tid; o < 7 * I_CTA; o += FORCE_THREADS) {
             const int q = o / I_CTA;
@@ -176,8 +202,17 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
             double sum = 0.0;
 #pragma unroll
             for (int gg = 0; gg < GROUPS; ++gg)
-                sum += red[(gg * 7 + q) * I_CTA + slot];
+                sum += red[(gg * NQ + q) * I_CTA + slot];
             write_out64(A, q, blockIdx.x * I_CTA + slot, sum);
+        }
+        if (NN) {
+            for (int slot = tid; slot < I_CTA; slot += FORCE_THREADS) {
+                double r2 = INFINITY, j = -1.0;
+#pragma unroll
+                for (int gg = 0; gg < GROUPS; ++gg)
+                    nn_min(r2, j, red[(gg * NQ + 7) * I_CTA + slot], red[(gg * NQ + 8) * I_CTA + slot]);
+                write_nn64(A, blockIdx.x * I_CTA + slot, r2, j);
+            }
         }
     }
 }
@@ -245,6 +280,7 @@ cudaError_t launch_force_fp64(const ForceArgs &a, Shape s, int mode, cudaStream_
     case MODE_ACC_JERK_POT: return launch_g<MODE_ACC_JERK_POT>(a, s, st);
     case MODE_ACC_POT: return launch_g<MODE_ACC_POT>(a, s, st);
     case MODE_ADJOINT: return launch_g<MODE_ADJOINT>(a, s, st);
+    case MODE_NN: return launch_g<MODE_NN>(a, s, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -255,6 +291,7 @@ int force_fp64_ctas_per_sm(int groups, int mode)
     case MODE_ACC_JERK_POT: return occ_g<MODE_ACC_JERK_POT>(groups);
     case MODE_ACC_POT: return occ_g<MODE_ACC_POT>(groups);
     case MODE_ADJOINT: return occ_g<MODE_ADJOINT>(groups);
+    case MODE_NN: return occ_g<MODE_NN>(groups);
     default: return 0;
     }
 }

@@ -62,22 +62,37 @@ __device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, doub
     if (k >= A.n_i)
         return;
     if (A.n_split > 1)
-        A.partial[((size_t)blockIdx.y * 7 + q) * A.n_i_pad + k] = val;
+        A.partial[((size_t)blockIdx.y * A.nq + q) * A.n_i_pad + k] = val;
     else
         store_final(A, q, k, val);
 }
 
+// Nearest-neighbour result of slot k: to the split partials, or final.
+__device__ __forceinline__ void write_nn(const ForceArgs &A, int k, double r2, double j)
+{
+    if (k >= A.n_i)
+        return;
+    if (A.n_split > 1) {
+        A.partial[((size_t)blockIdx.y * A.nq + 7) * A.n_i_pad + k] = r2;
+        A.partial[((size_t)blockIdx.y * A.nq + 8) * A.n_i_pad + k] = j;
+    } else {
+        store_nn(A, k, r2, j);
+    }
+}
+
 // Dynamic shared memory of one CTA: the tile ring, reused after the loop as
-// the [GROUPS][7][I_CTA] doubles of the cross-group reduction (7 x
+// the [GROUPS][nq][I_CTA] doubles of the cross-group reduction (up to 9 x
 // MIX_I_PER_THREAD x 256 doubles whatever GROUPS is), so the larger of the two.
 constexpr size_t MIX_RING_BYTES = (size_t)STAGES * TILE_J * sizeof(JMixed);
-constexpr size_t MIX_RED_BYTES = (size_t)7 * MIX_I_PER_THREAD * FORCE_THREADS * sizeof(double);
+constexpr size_t MIX_RED_BYTES = (size_t)9 * MIX_I_PER_THREAD * FORCE_THREADS * sizeof(double);
 constexpr size_t MIX_SMEM_BYTES = MIX_RING_BYTES > MIX_RED_BYTES ? MIX_RING_BYTES : MIX_RED_BYTES;
 
 template <int GROUPS, bool GUARD, int MODE>
 __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(const ForceArgs A)
 {
     constexpr bool ADJ = MODE == MODE_ADJOINT;
+    constexpr bool NN = MODE == MODE_NN;
+    constexpr int NQ = NN ? 9 : 7;              // reduced quantities per i
     constexpr int NP = MIX_IPAIRS;              // packed i-pairs per thread
     constexpr int NI = 2 * NP;                  // i-particles per thread
     constexpr int GT = FORCE_THREADS / GROUPS;  // threads per j-group
@@ -121,7 +136,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
     // the self pair is masked unless eps = 0 zeroes it anyway (in the adjoint,
     // w = m_k g_j - m_j g_k would vanish only if the compiler kept both
     // products rounded; a contracted multiply-add leaves ~u m g, times 1/eps^3)
-    const bool need_mask = eps2f != 0.f;
+    // (the neighbour search always excludes j = i by index)
+    const bool need_mask = eps2f != 0.f || NN;
 
     // ---- j range of this CTA (grid.y splits the tiles) ----
     const int y = blockIdx.y;
@@ -146,9 +162,12 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
 
     Tile7 t[NP];
     Lane7 acc[NI];
+    NNPair nnp[NP];
 #pragma unroll
-    for (int p = 0; p < NP; ++p)
+    for (int p = 0; p < NP; ++p) {
         t[p].zero();
+        nnp[p].reset();
+    }
 #pragma unroll
     for (int q = 0; q < NI; ++q)
         acc[q].zero();
@@ -172,14 +191,14 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
                 for (int jj = 0; jj < JG; ++jj) {
 #pragma unroll
                     for (int p = 0; p < NP; ++p)
-                        pair<GUARD, MODE, true>(T[jj], I[p], t[p], j0 + jj, idx[2 * p], idx[2 * p + 1]);
+                        pair<GUARD, MODE, true>(T[jj], I[p], t[p], j0 + jj, idx[2 * p], idx[2 * p + 1], &nnp[p]);
                 }
             } else {
 #pragma unroll MIX_UNROLL
                 for (int jj = 0; jj < JG; ++jj) {
 #pragma unroll
                     for (int p = 0; p < NP; ++p)
-                        pair<GUARD, MODE>(T[jj], I[p], t[p]);
+                        pair<GUARD, MODE>(T[jj], I[p], t[p], j0 + jj, -1, -1, &nnp[p]);
                 }
             }
             since += JG;
@@ -218,22 +237,32 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
     for (int p = 0; p < NP; ++p)
         fold<MODE>(t[p], acc[2 * p], acc[2 * p + 1]);
 
+    // neighbour of slot q: lane (q & 1) of pair q / 2
+    auto nn_r = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].r1 : nnp[q >> 1].r0); };
+    auto nn_j = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].j1 : nnp[q >> 1].j0); };
     if (GROUPS == 1) {
 #pragma unroll
         for (int q = 0; q < NI; ++q) {
+            const int slot = blockIdx.x * I_CTA + s + q * GT;
 #pragma unroll
             for (int c = 0; c < 7; ++c)
-                write_out(A, c, blockIdx.x * I_CTA + s + q * GT, (double)acc[q].h[c] + (double)acc[q].l[c]);
+                write_out(A, c, slot, (double)acc[q].h[c] + (double)acc[q].l[c]);
+            if (NN)
+                write_nn(A, slot, nn_r(q), nn_j(q));
         }
     } else {
         __syncthreads();  // all tiles consumed: reuse the ring as reduction space
-        static_assert((size_t)GROUPS * 7 * I_CTA * sizeof(double) <= MIX_SMEM_BYTES, "reduction space");
-        double *red = reinterpret_cast<double *>(smem_raw);  // [GROUPS][7][I_CTA]
+        static_assert((size_t)GROUPS * NQ * I_CTA * sizeof(double) <= MIX_SMEM_BYTES, "reduction space");
+        double *red = reinterpret_cast<double *>(smem_raw);  // [GROUPS][NQ][I_CTA]
 #pragma unroll
         for (int q = 0; q < NI; ++q) {
 #pragma unroll
             for (int c = 0; c < 7; ++c)
-                red[(g * 7 + c) * I_CTA + s + q * GT] = (double)acc[q].h[c] + (double)acc[q].l[c];
+                red[(g * NQ + c) * I_CTA + s + q * GT] = (double)acc[q].h[c] + (double)acc[q].l[c];
+            if (NN) {
+                red[(g * NQ + 7) * I_CTA + s + q * GT] = nn_r(q);
+                red[(g * NQ + 8) * I_CTA + s + q * GT] = nn_j(q);
+            }
         }
         __syncthreads();
         for (int o = tid; o < 7 * I_CTA; o += FORCE_THREADS) {
@@ -242,8 +271,17 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
             double sum = 0.0;
 #pragma unroll
             for (int gg = 0; gg < GROUPS; ++gg)
-                sum += red[(gg * 7 + c) * I_CTA + slot];
+                sum += red[(gg * NQ + c) * I_CTA + slot];
             write_out(A, c, blockIdx.x * I_CTA + slot, sum);
+        }
+        if (NN) {
+            for (int slot = tid; slot < I_CTA; slot += FORCE_THREADS) {
+                double r2 = INFINITY, j = -1.0;
+#pragma unroll
+                for (int gg = 0; gg < GROUPS; ++gg)
+                    nn_min(r2, j, red[(gg * NQ + 7) * I_CTA + slot], red[(gg * NQ + 8) * I_CTA + slot]);
+                write_nn(A, blockIdx.x * I_CTA + slot, r2, j);
+            }
         }
     }
 }
@@ -320,6 +358,7 @@ cudaError_t launch_force_mixed(const ForceArgs &a, Shape s, bool guard, int mode
     case MODE_ACC_JERK_POT: return launch_m<MODE_ACC_JERK_POT>(a, s, guard, st);
     case MODE_ACC_POT: return launch_m<MODE_ACC_POT>(a, s, guard, st);
     case MODE_ADJOINT: return launch_m<MODE_ADJOINT>(a, s, guard, st);
+    case MODE_NN: return launch_m<MODE_NN>(a, s, guard, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -330,6 +369,7 @@ int force_mixed_ctas_per_sm(int groups, bool guard, int mode)
     case MODE_ACC_JERK_POT: return guard ? occ_g<true, MODE_ACC_JERK_POT>(groups) : occ_g<false, MODE_ACC_JERK_POT>(groups);
     case MODE_ACC_POT: return guard ? occ_g<true, MODE_ACC_POT>(groups) : occ_g<false, MODE_ACC_POT>(groups);
     case MODE_ADJOINT: return guard ? occ_g<true, MODE_ADJOINT>(groups) : occ_g<false, MODE_ADJOINT>(groups);
+    case MODE_NN: return guard ? occ_g<true, MODE_NN>(groups) : occ_g<false, MODE_NN>(groups);
     default: return 0;
     }
 }

@@ -76,10 +76,13 @@ struct ForceArgs {
     double *acc;            // final outputs (n_i x 3, n_i x 3, n_i); any may be null
     double *jerk;
     double *pot;
-    double *partial;        // [n_split][7][n_i_pad] when n_split > 1
+    double *partial;        // [n_split][nq][n_i_pad] when n_split > 1
     int n_i_pad;
     int accumulate;         // 1: add the results to the outputs instead of overwriting them
     unsigned *err;
+    int32_t *nn;            // nearest-neighbour mode: index of the nearest j != i (n_i)
+    double *nn_r2;          // and its squared distance |d|^2 (n_i); either may be null
+    int nq;                 // quantities per i in the partials: 7, or 9 with the neighbour
 };
 
 // Final scaling of one of the seven per-i sums and its store (acc and jerk:
@@ -102,11 +105,34 @@ __device__ __forceinline__ void store_final(const ForceArgs &A, int q, int k, do
         *dst = A.accumulate ? *dst + val : val;
 }
 
+// Store the nearest neighbour found for output slot k: r2 = |d|^2 + eps^2 as
+// summed by the kernel (eps^2 removed here), j its index (-1: none).
+__device__ __forceinline__ void store_nn(const ForceArgs &A, int k, double r2, double j)
+{
+    if (A.nn)
+        A.nn[k] = j < 0 ? -1 : (int32_t)j;
+    if (A.nn_r2)
+        A.nn_r2[k] = j < 0 ? INFINITY : fmax(r2 - A.eps2, 0.0);
+}
+
+// Lexicographic (r2, j) minimum: the nearer neighbour, the smaller index on ties.
+__device__ __forceinline__ void nn_min(double &r2, double &j, double r2b, double jb)
+{
+    if (jb >= 0 && (j < 0 || r2b < r2 || (r2b == r2 && jb < j))) {
+        r2 = r2b;
+        j = jb;
+    }
+}
+
 // What a force launch sums (the seven per-i quantities of ForceArgs):
 //  MODE_ACC_JERK_POT: acc, jerk, pot;  MODE_ACC_POT: acc, pot (jerk outputs 0);
 //  MODE_ADJOINT: the velocity slots of the j image hold g = dL/da; the jerk
 //  outputs receive dL/dx and the pot output dL/dm (acc outputs 0).
-enum { MODE_ACC_JERK_POT = 0, MODE_ACC_POT = 1, MODE_ADJOINT = 2 };
+//  MODE_NN: as MODE_ACC_JERK_POT, plus the nearest j != i of every i (the
+//  neighbour search of Sect. 3.3.1): quantities 7 and 8 of the partials hold
+//  its |d|^2 + eps^2 and index, reduced by the lexicographic minimum.
+enum { MODE_ACC_JERK_POT = 0, MODE_ACC_POT = 1, MODE_ADJOINT = 2, MODE_NN = 3 };
+constexpr int N_MODES = 4;
 
 // Launchers (force_mixed.cu / force_fp64.cu).
 cudaError_t launch_force_mixed(const ForceArgs &a, Shape s, bool guard, int mode, cudaStream_t st);

@@ -154,6 +154,7 @@ extern "C" int kirin_forces_noalloc(int64_t n, const double *m, const double *x,
     a.n_i_pad = (int)((n_i + i_cta - 1) / i_cta * i_cta);
     a.accumulate = 0;
     a.err = err;
+    a.nq = 7;
     if (launch_force_mixed(a, sh, guard, MODE_ACC_JERK_POT, st) != cudaSuccess)
         return KIRIN_ECUDA;
     if (sh.n_split > 1 && launch_reduce_splits(a, st) != cudaSuccess)

@@ -97,6 +97,18 @@ struct Lane7 {
     }
 };
 
+// Nearest j of the two lanes so far: s^2 = |d|^2 + eps^2 as computed in FP32
+// (the kernel's own precision decides), and its index.
+struct NNPair {
+    float r0, r1;
+    int j0, j1;
+    __device__ __forceinline__ void reset()
+    {
+        r0 = r1 = INFINITY;
+        j0 = j1 = -1;
+    }
+};
+
 template <int MODE>
 __device__ __forceinline__ void fold(Tile7 &t, Lane7 &L0, Lane7 &L1)
 {
@@ -131,10 +143,11 @@ __device__ __forceinline__ void fold(Tile7 &t, Lane7 &L0, Lane7 &L1)
 
 template <bool GUARD, int MODE, bool MASK = false>
 __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, int j = 0, int i0 = -1,
-                                     int i1 = -1)
+                                     int i1 = -1, NNPair *nn = nullptr)
 {
     constexpr bool JERK = MODE != MODE_ACC_POT;
     constexpr bool ADJ = MODE == MODE_ADJOINT;
+    constexpr bool NN = MODE == MODE_NN;
     const float4 q0 = J.q[0];
     const float4 q1 = J.q[1];
     const float4 q2 = J.q[2];
@@ -145,6 +158,19 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, 
     float2 r2 = __ffma2_rn(dx, dx, I.eps2v);
     r2 = __ffma2_rn(dy, dy, r2);
     r2 = __ffma2_rn(dz, dz, r2);
+    if (NN) {
+        // strict < in increasing j keeps the smallest index on ties
+        const float ra = (MASK && j == i0) ? INFINITY : r2.x;
+        const float rb = (MASK && j == i1) ? INFINITY : r2.y;
+        if (ra < nn->r0) {
+            nn->r0 = ra;
+            nn->j0 = j;
+        }
+        if (rb < nn->r1) {
+            nn->r1 = rb;
+            nn->j1 = j;
+        }
+    }
     float2 ri;
     if (GUARD) {
         ri.x = rsqrt_mufu(fmaxf(r2.x, I.rmin2));
