@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
         for (int q = 0; q < 7; ++q)
             write_out64(A, q, kslot, res[q]);
         if (NN)
-            write_nn64(A, kslot, nn_r2, (double)nn_j);
+            write_nn64(A, kslot, nn_r2 - eps2, (double)nn_j);
     } else {
         __syncthreads();
         static_assert((size_t)GROUPS * NQ * I_CTA * sizeof(double) <= F64_SMEM_BYTES, "reduction space");
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
         for (int q = 0; q < 7; ++q)
             red[(g * NQ + q) * I_CTA + s] = res[q];
         if (NN) {
-            red[(g * NQ + 7) * I_CTA + s] = nn_r2;
+            red[(g * NQ + 7) * I_CTA + s] = nn_r2 - eps2;
             red[(g * NQ + 8) * I_CTA + s] = (double)nn_j;
         }
         __syncthreads();

@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
         fold<MODE>(t[p], acc[2 * p], acc[2 * p + 1]);
 
     // neighbour of slot q: lane (q & 1) of pair q / 2
-    auto nn_r = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].r1 : nnp[q >> 1].r0); };
+    // |d|^2: the FP32 s^2 minus the FP32 eps^2 it contains
+    auto nn_r = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].r1 : nnp[q >> 1].r0) - (double)eps2f; };
     auto nn_j = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].j1 : nnp[q >> 1].j0); };
     if (GROUPS == 1) {
 #pragma unroll

@@ -105,14 +105,14 @@ __device__ __forceinline__ void store_final(const ForceArgs &A, int q, int k, do
         *dst = A.accumulate ? *dst + val : val;
 }
 
-// Store the nearest neighbour found for output slot k: r2 = |d|^2 + eps^2 as
-// summed by the kernel (eps^2 removed here), j its index (-1: none).
-__device__ __forceinline__ void store_nn(const ForceArgs &A, int k, double r2, double j)
+// Store the nearest neighbour found for output slot k: d2 = |d|^2 (the
+// kernel's s^2 minus the eps^2 it added), j its index (-1: none).
+__device__ __forceinline__ void store_nn(const ForceArgs &A, int k, double d2, double j)
 {
     if (A.nn)
         A.nn[k] = j < 0 ? -1 : (int32_t)j;
     if (A.nn_r2)
-        A.nn_r2[k] = j < 0 ? INFINITY : fmax(r2 - A.eps2, 0.0);
+        A.nn_r2[k] = j < 0 ? INFINITY : fmax(d2, 0.0);
 }
 
 // Lexicographic (r2, j) minimum: the nearer neighbour, the smaller index on ties.
@@ -130,7 +130,7 @@ __device__ __forceinline__ void nn_min(double &r2, double &j, double r2b, double
 //  outputs receive dL/dx and the pot output dL/dm (acc outputs 0).
 //  MODE_NN: as MODE_ACC_JERK_POT, plus the nearest j != i of every i (the
 //  neighbour search of Sect. 3.3.1): quantities 7 and 8 of the partials hold
-//  its |d|^2 + eps^2 and index, reduced by the lexicographic minimum.
+//  its |d|^2 and index, reduced by the lexicographic minimum.
 enum { MODE_ACC_JERK_POT = 0, MODE_ACC_POT = 1, MODE_ADJOINT = 2, MODE_NN = 3 };
 constexpr int N_MODES = 4;
 
