@@ -118,13 +118,19 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
                 const double2 p0 = T[jj].q[0], p1 = T[jj].q[1], w0 = T[jj].q[2], w1 = T[jj].q[3];
                 const double dx = p0.x - xi, dy = p0.y - yi, dz = p1.x - zi;
                 const double wx = w0.x - vxi, wy = w0.y - vyi, wz = w1.x - vzi;
-                const double s2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+                double s2;
+                if (NN) {  // the search compares |d|^2 (padding j >= n_j and j = i skipped)
+                    const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                    s2 = d2 + eps2;
+                    if (jbase + jj != i && jbase + jj < A.n_j && d2 < nn_r2) {
+                        nn_r2 = d2;
+                        nn_j = jbase + jj;
+                    }
+                } else {
+                    s2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+                }
                 double rinv = rsqrt(fmax(s2, rmin2));
                 rinv = (s2 == 0.0 || jbase + jj == i) ? 0.0 : rinv;
-                if (NN && jbase + jj != i && s2 < nn_r2) {
-                    nn_r2 = s2;
-                    nn_j = jbase + jj;
-                }
                 const double rinv2 = rinv * rinv;
                 if (ADJ) {
                     // w = m_k g_j - m_j g_k;  dL/dx_k += K(d) w;  dL/dm_k -= g_j.d / s^3
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
         for (int q = 0; q < 7; ++q)
             write_out64(A, q, kslot, res[q]);
         if (NN)
-            write_nn64(A, kslot, nn_r2 - eps2, (double)nn_j);
+            write_nn64(A, kslot, nn_r2, (double)nn_j);
     } else {
         __syncthreads();
         static_assert((size_t)GROUPS * NQ * I_CTA * sizeof(double) <= F64_SMEM_BYTES, "reduction space");
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
         for (int q = 0; q < 7; ++q)
             red[(g * NQ + q) * I_CTA + s] = res[q];
         if (NN) {
-            red[(g * NQ + 7) * I_CTA + s] = nn_r2 - eps2;
+            red[(g * NQ + 7) * I_CTA + s] = nn_r2;
             red[(g * NQ + 8) * I_CTA + s] = (double)nn_j;
         }
         __syncthreads();

@@ -191,14 +191,15 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
                 for (int jj = 0; jj < JG; ++jj) {
 #pragma unroll
                     for (int p = 0; p < NP; ++p)
-                        pair<GUARD, MODE, true>(T[jj], I[p], t[p], j0 + jj, idx[2 * p], idx[2 * p + 1], &nnp[p]);
+                        pair<GUARD, MODE, true>(T[jj], I[p], t[p], j0 + jj, idx[2 * p], idx[2 * p + 1], &nnp[p],
+                                                A.n_j);
                 }
             } else {
 #pragma unroll MIX_UNROLL
                 for (int jj = 0; jj < JG; ++jj) {
 #pragma unroll
                     for (int p = 0; p < NP; ++p)
-                        pair<GUARD, MODE>(T[jj], I[p], t[p], j0 + jj, -1, -1, &nnp[p]);
+                        pair<GUARD, MODE>(T[jj], I[p], t[p], j0 + jj, -1, -1, &nnp[p], A.n_j);
                 }
             }
             since += JG;
@@ -238,8 +239,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
         fold<MODE>(t[p], acc[2 * p], acc[2 * p + 1]);
 
     // neighbour of slot q: lane (q & 1) of pair q / 2
-    // |d|^2: the FP32 s^2 minus the FP32 eps^2 it contains
-    auto nn_r = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].r1 : nnp[q >> 1].r0) - (double)eps2f; };
+    auto nn_r = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].r1 : nnp[q >> 1].r0); };
     auto nn_j = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].j1 : nnp[q >> 1].j0); };
     if (GROUPS == 1) {
 #pragma unroll

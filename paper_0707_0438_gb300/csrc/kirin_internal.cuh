@@ -105,8 +105,8 @@ __device__ __forceinline__ void store_final(const ForceArgs &A, int q, int k, do
         *dst = A.accumulate ? *dst + val : val;
 }
 
-// Store the nearest neighbour found for output slot k: d2 = |d|^2 (the
-// kernel's s^2 minus the eps^2 it added), j its index (-1: none).
+// Store the nearest neighbour found for output slot k: d2 = |d|^2, j its
+// index (-1: none).
 __device__ __forceinline__ void store_nn(const ForceArgs &A, int k, double d2, double j)
 {
     if (A.nn)

@@ -97,8 +97,8 @@ struct Lane7 {
     }
 };
 
-// Nearest j of the two lanes so far: s^2 = |d|^2 + eps^2 as computed in FP32
-// (the kernel's own precision decides), and its index.
+// Nearest j of the two lanes so far: |d|^2 as computed in FP32 (the kernel's
+// own precision decides), and its index.
 struct NNPair {
     float r0, r1;
     int j0, j1;
@@ -143,7 +143,7 @@ __device__ __forceinline__ void fold(Tile7 &t, Lane7 &L0, Lane7 &L1)
 
 template <bool GUARD, int MODE, bool MASK = false>
 __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, int j = 0, int i0 = -1,
-                                     int i1 = -1, NNPair *nn = nullptr)
+                                     int i1 = -1, NNPair *nn = nullptr, int jlim = 0)
 {
     constexpr bool JERK = MODE != MODE_ACC_POT;
     constexpr bool ADJ = MODE == MODE_ADJOINT;
@@ -155,21 +155,31 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, 
     const float2 dx = __fadd2_rn(__fadd2_rn(f2(q0.x, q0.y), I.nxh), __fadd2_rn(f2(q2.x, q2.y), I.nxl));
     const float2 dy = __fadd2_rn(__fadd2_rn(f2(q0.z, q0.w), I.nyh), __fadd2_rn(f2(q2.z, q2.w), I.nyl));
     const float2 dz = __fadd2_rn(__fadd2_rn(f2(q1.x, q1.y), I.nzh), __fadd2_rn(f2(q3.x, q3.y), I.nzl));
-    float2 r2 = __ffma2_rn(dx, dx, I.eps2v);
-    r2 = __ffma2_rn(dy, dy, r2);
-    r2 = __ffma2_rn(dz, dz, r2);
+    float2 r2;
     if (NN) {
-        // strict < in increasing j keeps the smallest index on ties
-        const float ra = (MASK && j == i0) ? INFINITY : r2.x;
-        const float rb = (MASK && j == i1) ? INFINITY : r2.y;
-        if (ra < nn->r0) {
-            nn->r0 = ra;
-            nn->j0 = j;
+        // the search compares |d|^2 itself (one more add than the fused chain);
+        // padding records (j >= jlim) and the self pair are skipped, and strict <
+        // in increasing j keeps the smallest index on ties
+        float2 d2 = __fmul2_rn(dx, dx);
+        d2 = __ffma2_rn(dy, dy, d2);
+        d2 = __ffma2_rn(dz, dz, d2);
+        r2 = __fadd2_rn(d2, I.eps2v);
+        const float ra = (MASK && j == i0) ? INFINITY : d2.x;
+        const float rb = (MASK && j == i1) ? INFINITY : d2.y;
+        if (j < jlim) {
+            if (ra < nn->r0) {
+                nn->r0 = ra;
+                nn->j0 = j;
+            }
+            if (rb < nn->r1) {
+                nn->r1 = rb;
+                nn->j1 = j;
+            }
         }
-        if (rb < nn->r1) {
-            nn->r1 = rb;
-            nn->j1 = j;
-        }
+    } else {
+        r2 = __ffma2_rn(dx, dx, I.eps2v);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
     }
     float2 ri;
     if (GUARD) {
