@@ -124,6 +124,18 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def replica_rate(local_seconds: float, units_per_step: float, steps: int, world: int, dist=None, device=None):
+    """Whole-job rate of `world` replicas: every rank did `steps` steps of `units_per_step`;
+    the job took as long as the slowest rank (MAX over ranks).  Returns (rate, max_seconds)."""
+    t_max = float(local_seconds)
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t_max], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return world * units_per_step * steps / t_max, t_max
+
+
 def _fp32_peak_tflops(nsm: int, mhz: float) -> float:
     """CUDA-core FP32 peak: SMs x 128 lanes x 2 flops (FMA) x clock."""
     return nsm * 128 * 2 * mhz * 1e6 / 1e12
@@ -249,13 +261,8 @@ def run_native(args):
     with ClockSampler(local) as clk:
         t_mixed = timed(k, args.steps, args.warmup)
     clocks = clk.summary()
-    t_max = t_mixed
-    if dist is not None:
-        tt = torch.tensor([t_mixed], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
     pairs_per_step = float(n) * float(n)
-    value = world * pairs_per_step * args.steps / t_max
+    value, t_max = replica_rate(t_mixed, pairs_per_step, args.steps, world, dist, dev)
     ms_per_step = 1e3 * t_max / args.steps
     res_mixed = (acc.cpu().numpy(), jerk.cpu().numpy(), pot.cpu().numpy()) if rank == 0 else None
 
