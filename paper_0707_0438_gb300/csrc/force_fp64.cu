@@ -21,7 +21,7 @@ __device__ __forceinline__ void write_out64(const ForceArgs &A, int q, int k, do
     if (k >= A.n_i)
         return;
     if (A.n_split > 1)
-        A.partial[((size_t)blockIdx.y * 7 + q) * A.n_i_pad + k] = val;
+        A.partial[((size_t)blockIdx.y * A.nq + q) * A.n_i_pad + k] = val;
     else
         store_final(A, q, k, val);
 }

@@ -58,13 +58,15 @@ def test_nearest_through_every_launch_shape_and_host_path(kirin_lib, precision):
     x[100] = x[50] + 1e-7
     il = workloads.i_subset(p.n, 900, 2)
     il = np.concatenate([il, [7, 8, 50, 100]]).astype(np.int32)
+    ref = oracle.acc_jerk_pot(p.m, x, p.v, p.eps, i_idx=il)
     with abi.Kirin(p.n, p.eps, precision=precision) as k:
         k.set_j_particles(p.m, x, p.v)
         k.set_nn(True)
         for groups in (1, 2, 4, 8):
             for n_split in (1, 3, 7):
                 k.set_launch(groups, n_split)
-                k.forces(il)
+                got = k.forces(il)
+                assert_parity(got, ref, precision, f"nn groups={groups} split={n_split}")
                 nn, r2 = k.get_nn()
                 _check_nn(x, il, nn, r2, precision)
                 assert nn[-4] == 8 and nn[-3] == 7 and r2[-4] == 0.0 and r2[-3] == 0.0
