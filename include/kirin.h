@@ -215,6 +215,22 @@ int kirin_hermite_shared_step(kirin_ctx *ctx, double dt);
 int kirin_get_state(kirin_ctx *ctx, double *x, double *v, double *a, double *jerk, double *t,
                     double *dt);
 
+/* Restore an integrator state saved with kirin_get_state (resume after a
+ * checkpoint; no counterpart in the paper): particles 0..n-1 get m, x, v, a,
+ * jerk, their times t and steps dt (host arrays, layouts as in
+ * kirin_get_state), and the block-step parameters eta, dt_min, dt_max.  The
+ * next kirin_hermite_block_step continues exactly where the saved run was.
+ * Errors: EINVAL, ENONFINITE. */
+int kirin_set_state(kirin_ctx *ctx, int64_t n, const double *m, const double *x, const double *v,
+                    const double *a, const double *jerk, const double *t, const double *dt, double eta,
+                    double dt_min, double dt_max);
+
+/* Failure-path self-test: one device thread waits on a barrier phase that never
+ * completes, with a wait limit of limit_ns, exactly as the force kernels wait on
+ * their tile copies; it returns KIRIN_ETIMEOUT (the context stays usable).
+ * No counterpart in the paper. */
+int kirin_selftest_wait_timeout(kirin_ctx *ctx, int64_t limit_ns);
+
 /* ---- accelerations of device particle sets (leapfrog clients, Sect. 4.3) ----
  * Acceleration (and optionally potential) of all n particles of (m, x), every
  * particle against every other, without jerk: the force-only evaluation the

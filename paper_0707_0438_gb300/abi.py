@@ -76,6 +76,8 @@ _SIGS = {
     "kirin_hermite_run": (ctypes.c_int, [_P, _D, _I64, _PI64, _PD]),
     "kirin_hermite_shared_step": (ctypes.c_int, [_P, _D]),
     "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
+    "kirin_set_state": (ctypes.c_int, [_P, _I64, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _D, _D, _D]),
+    "kirin_selftest_wait_timeout": (ctypes.c_int, [_P, _I64]),
     "kirin_accel_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P]),
     "kirin_accel_adjoint_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
     "kirin_leapfrog_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _D, _I32, _I32, _P]),
@@ -337,6 +339,19 @@ class Kirin:
         self._check(self.lib.kirin_get_state(self.ctx, _dp(x), _dp(v), _dp(a), _dp(j), _dp(t), _dp(dt)),
                     "kirin_get_state")
         return {"x": x, "v": v, "a": a, "j": j, "t": t, "dt": dt}
+
+    def set_state(self, m, st, eta=0.01, dt_min=2.0 ** -20, dt_max=2.0 ** -3):
+        """Resume from a get_state() dictionary (plus the masses)."""
+        m = _host(m)
+        n = m.shape[0]
+        arrs = [_host(st[k], (n, 3)) for k in ("x", "v", "a", "j")] + [_host(st["t"], (n,)), _host(st["dt"], (n,))]
+        self._check(self.lib.kirin_set_state(self.ctx, n, _dp(m), *[_dp(a) for a in arrs], float(eta),
+                                             float(dt_min), float(dt_max)), "kirin_set_state")
+        self.n_j = n
+
+    def selftest_wait_timeout(self, limit_ns=1_000_000):
+        """Run the bounded-wait self-test; returns the library's return code (KIRIN_ETIMEOUT expected)."""
+        return self.lib.kirin_selftest_wait_timeout(self.ctx, int(limit_ns))
 
     # -- device particle sets
     def accel_dev(self, m, x, acc, pot=None):

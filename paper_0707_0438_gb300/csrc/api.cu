@@ -904,6 +904,38 @@ int kirin_get_state(kirin_ctx *ctx, double *x, double *v, double *a, double *jer
     return read_device_errors(ctx);
 }
 
+int kirin_set_state(kirin_ctx *ctx, int64_t n, const double *m, const double *x, const double *v, const double *a,
+                    const double *jerk, const double *t, const double *dt, double eta, double dt_min, double dt_max)
+{
+    if (!ctx || !m || !x || !v || !a || !jerk || !t || !dt || n < 1 || n > ctx->n_max || !(eta > 0) ||
+        !(dt_min > 0) || !(dt_max >= dt_min))
+        return set_msg(ctx, KIRIN_EINVAL, "set_state: bad argument");
+    if (!all_finite(dt, n))
+        return set_msg(ctx, KIRIN_ENONFINITE, "set_state: NaN or Inf in dt");
+    int rc = kirin_set_j_particles(ctx, 0, n, m, x, v, a, jerk, t);
+    if (rc)
+        return rc;
+    DeviceGuard dg(ctx->device);
+    CK(ctx, cudaMemcpyAsync(ctx->bdt, dt, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->n_j = n;
+    ctx->eta = eta;
+    ctx->dt_min = dt_min;
+    ctx->dt_max = dt_max;
+    ctx->t_shared = t[0];
+    ctx->hermite_ready = true;
+    return KIRIN_OK;
+}
+
+int kirin_selftest_wait_timeout(kirin_ctx *ctx, int64_t limit_ns)
+{
+    if (!ctx || limit_ns < 0)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    CK(ctx, launch_wait_selftest((unsigned long long)limit_ns, ctx->d_err, ctx->stream));
+    return read_device_errors(ctx);
+}
+
 // ---- device particle sets -------------------------------------------------------
 
 int kirin_accel_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x, double *acc, double *pot)

@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "kirin_internal.cuh"
+#include "tma.cuh"
 
 namespace kirin {
 namespace {
@@ -408,6 +409,24 @@ __global__ void k_pack_adjoint(int n, int n_pad, const double *__restrict__ m, c
     write_images(k, x[o], x[o + 1], x[o + 2], m[k], gx, gy, gz, jm, jd);
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier phase that
+// nothing completes (the barrier expects two arrivals and gets one) and gives
+// up after limit_ns; the CTA then reports ERR_TIMEOUT like a stalled copy would.
+__global__ void k_wait_selftest(unsigned long long limit_ns, unsigned *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+        if (!mbar_wait_bounded(&bar, 0, limit_ns))
+            atomicOr(err, ERR_TIMEOUT);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_reduce_splits(const ForceArgs &a, cudaStream_t st)
@@ -533,6 +552,16 @@ cudaError_t launch_pack_adjoint(int n, int n_pad, const double *m, const double 
     if (n_pad == 0)
         return cudaSuccess;
     k_pack_adjoint<<<blocks_for(n_pad, AUX_THREADS), AUX_THREADS, 0, st>>>(n, n_pad, m, x, lv, c, jm, jd, err);
+    return cudaGetLastError();
+}
+
+}  // namespace kirin
+
+namespace kirin {
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *err, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, err);
     return cudaGetLastError();
 }
 

@@ -170,6 +170,7 @@ cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_nex
 cudaError_t launch_lf_kick_drift(int n, double h, double dt, const double *a, double *v, double *x,
                                  double *hist, cudaStream_t st);
 cudaError_t launch_axpy(int n, double alpha, const double *x, double *y, cudaStream_t st);
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *err, cudaStream_t st);
 cudaError_t launch_copy(int n, const double *src, double *dst, cudaStream_t st);
 cudaError_t launch_pack_adjoint(int n, int n_pad, const double *m, const double *x, const double *lv, double c,
                                 JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st);

@@ -83,8 +83,9 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 // Wait for the phase with the given parity to complete, giving up after
-// WAIT_LIMIT_NS of wall-clock time.  Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// limit_ns of wall-clock time.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = WAIT_LIMIT_NS)
 {
     if (mbar_try_wait(bar, parity))
         return true;
@@ -92,7 +93,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     while (true) {
         if (mbar_try_wait(bar, parity))
             return true;
-        if (global_ns() - t0 > WAIT_LIMIT_NS)
+        if (global_ns() - t0 > limit_ns)
             return false;
     }
 }
