@@ -53,9 +53,6 @@ namespace {
 #ifndef KIRIN_MIX_MINB
 #define KIRIN_MIX_MINB 2
 #endif
-#ifndef KIRIN_TWO_ACC
-#define KIRIN_TWO_ACC 0
-#endif
 constexpr int FLUSH_J = KIRIN_FLUSH_J;
 constexpr int FLUSH_J_ADJOINT = 64;
 constexpr int MIX_UNROLL = KIRIN_MIX_UNROLL;
@@ -171,12 +168,6 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
         t[p].zero();
         nnp[p].reset();
     }
-#if KIRIN_TWO_ACC
-    Tile7 t2[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p)
-        t2[p].zero();
-#endif
 #pragma unroll
     for (int q = 0; q < NI; ++q)
         acc[q].zero();
@@ -204,34 +195,18 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
                                                 A.n_j);
                 }
             } else {
-#if KIRIN_TWO_ACC
-                // even and odd j into separate partial sums: half-length dependency chains
-#pragma unroll MIX_UNROLL
-                for (int jj = 0; jj < JG; jj += 2) {
-#pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        pair<GUARD, MODE>(T[jj], I[p], t[p], j0 + jj, -1, -1, &nnp[p], A.n_j);
-                        pair<GUARD, MODE>(T[jj + 1], I[p], t2[p], j0 + jj + 1, -1, -1, &nnp[p], A.n_j);
-                    }
-                }
-#else
 #pragma unroll MIX_UNROLL
                 for (int jj = 0; jj < JG; ++jj) {
 #pragma unroll
                     for (int p = 0; p < NP; ++p)
                         pair<GUARD, MODE>(T[jj], I[p], t[p], j0 + jj, -1, -1, &nnp[p], A.n_j);
                 }
-#endif
             }
             since += JG;
             if (since >= (ADJ ? FLUSH_J_ADJOINT : FLUSH_J)) {
 #pragma unroll
-                for (int p = 0; p < NP; ++p) {
+                for (int p = 0; p < NP; ++p)
                     fold<MODE>(t[p], acc[2 * p], acc[2 * p + 1]);
-#if KIRIN_TWO_ACC
-                    fold<MODE>(t2[p], acc[2 * p], acc[2 * p + 1]);
-#endif
-                }
                 since = 0;
             }
         }
@@ -260,12 +235,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
         return;
     }
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
+    for (int p = 0; p < NP; ++p)
         fold<MODE>(t[p], acc[2 * p], acc[2 * p + 1]);
-#if KIRIN_TWO_ACC
-        fold<MODE>(t2[p], acc[2 * p], acc[2 * p + 1]);
-#endif
-    }
 
     // neighbour of slot q: lane (q & 1) of pair q / 2
     auto nn_r = [&](int q) { return (double)((q & 1) ? nnp[q >> 1].r1 : nnp[q >> 1].r0); };

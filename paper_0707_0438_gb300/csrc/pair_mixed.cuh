@@ -25,10 +25,6 @@
 
 #include "kirin_internal.cuh"
 
-#ifndef KIRIN_EARLY_DV
-#define KIRIN_EARLY_DV 0
-#endif
-
 namespace kirin {
 
 __device__ __forceinline__ float rsqrt_mufu(float x)
@@ -185,17 +181,6 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, 
         r2 = __ffma2_rn(dy, dy, r2);
         r2 = __ffma2_rn(dz, dz, r2);
     }
-#if KIRIN_EARLY_DV
-    // velocity difference and d.w do not depend on 1/s: form them while MUFU works
-    float2 e_dvx, e_dvy, e_dvz, e_rv;
-    if (JERK && !ADJ) {
-        const float4 q4e = J.q[4];
-        e_dvx = __fadd2_rn(f2(q3.z, q3.w), I.nvx);
-        e_dvy = __fadd2_rn(f2(q4e.x, q4e.y), I.nvy);
-        e_dvz = __fadd2_rn(f2(q4e.z, q4e.w), I.nvz);
-        e_rv = __ffma2_rn(dz, e_dvz, __ffma2_rn(dy, e_dvy, __fmul2_rn(dx, e_dvx)));
-    }
-#endif
     float2 ri;
     if (GUARD) {
         ri.x = rsqrt_mufu(fmaxf(r2.x, I.rmin2));
@@ -243,9 +228,6 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, 
     t.ay = __ffma2_rn(mr3, dy, t.ay);
     t.az = __ffma2_rn(mr3, dz, t.az);
     if (JERK) {
-#if KIRIN_EARLY_DV
-        const float2 dvx = e_dvx, dvy = e_dvy, dvz = e_dvz, rv = e_rv;
-#else
         const float4 q4 = J.q[4];
         const float2 dvx = __fadd2_rn(f2(q3.z, q3.w), I.nvx);
         const float2 dvy = __fadd2_rn(f2(q4.x, q4.y), I.nvy);
@@ -253,7 +235,6 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, 
         float2 rv = __fmul2_rn(dx, dvx);
         rv = __ffma2_rn(dy, dvy, rv);
         rv = __ffma2_rn(dz, dvz, rv);
-#endif
         const float2 b = __fmul2_rn(__fmul2_rn(rv, ri2), mr3);  // m (d.w) / s^5
         t.j1x = __ffma2_rn(mr3, dvx, t.j1x);
         t.j1y = __ffma2_rn(mr3, dvy, t.j1y);
