@@ -445,11 +445,15 @@ def run_block(args):
     out = {}
     from paper_0707_0438_gb300 import autotune
     gpu = torch.cuda.get_device_name(0)
-    for precision, t_end in (("mixed", 0.125), ("fp64", args.fp64_t_end)):
+    # the device-driven loop (one graph launch per run) and, for comparison, one host round trip per step
+    for name, precision, t_end, device_loop in (("mixed", "mixed", 0.125, True),
+                                                ("mixed_host_loop", "mixed", 0.125, False),
+                                                ("fp64", "fp64", args.fp64_t_end, True)):
         with abi.Kirin(n, p.eps, precision=precision) as k:
             k.set_j_particles(p.m, p.x, p.v)
             if precision == "mixed":
                 autotune.install(k, n, gpu, "mixed")
+            k.set_device_loop(device_loop)
             kin0, pot0 = k.energy()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -457,9 +461,9 @@ def run_block(args):
             steps, pairs = k.hermite_run(t_end)
             dt = time.perf_counter() - t0
             kin1, pot1 = k.energy()
-            out[precision] = {"t_end": t_end, "block_steps": steps, "pairs": pairs + float(n) * n,
-                              "seconds": dt, "value": (pairs + float(n) * n) / dt,
-                              "dE_E": metrics.energy_error(kin0 + pot0, kin1 + pot1)}
+            out[name] = {"t_end": t_end, "block_steps": steps, "pairs": pairs + float(n) * n,
+                         "seconds": dt, "value": (pairs + float(n) * n) / dt, "device_loop": device_loop,
+                         "dE_E": metrics.energy_error(kin0 + pot0, kin1 + pot1)}
     # active-block histogram and per-bucket rate (each step synchronised), mixed, to t = 1/32
     hist = {}
     with abi.Kirin(n, p.eps, precision="mixed") as k:
@@ -483,7 +487,8 @@ def run_block(args):
     _line("pair interactions/s over a block-step Hermite run (acc+jerk+pot, incl. predictor/corrector/scheduler)",
           m["value"], UNIT, m["block_steps"], 0, m["seconds"],
           f"plummer N={n} eps=1e-3 seed 1002, Hermite block steps eta=0.01 to t=1/8",
-          {"mixed": m, "fp64": out["fp64"], "n_active_histogram": buckets,
+          {"mixed": m, "mixed_host_loop": out["mixed_host_loop"], "fp64": out["fp64"],
+           "n_active_histogram": buckets,
            "note": "fp64 run integrates to the shorter t_end shown; rates are comparable, ΔE/E is per run"})
 
 

@@ -74,6 +74,7 @@ _SIGS = {
     "kirin_hermite_init": (ctypes.c_int, [_P, _D, _D, _D, _D]),
     "kirin_hermite_block_step": (ctypes.c_int, [_P, _D, _PD, _PI64]),
     "kirin_hermite_run": (ctypes.c_int, [_P, _D, _I64, _PI64, _PD]),
+    "kirin_set_device_loop": (ctypes.c_int, [_P, _I32]),
     "kirin_hermite_shared_step": (ctypes.c_int, [_P, _D]),
     "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
     "kirin_set_state": (ctypes.c_int, [_P, _I64, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _D, _D, _D]),
@@ -324,10 +325,15 @@ class Kirin:
         return t.value, n.value
 
     def hermite_run(self, t_end, max_steps=0):
+        """Block steps to t_end; returns (steps, pairs).  One graph launch per
+        call unless set_device_loop(False)."""
         s, p = ctypes.c_int64(), ctypes.c_double()
         self._check(self.lib.kirin_hermite_run(self.ctx, float(t_end), int(max_steps), ctypes.byref(s),
                                                ctypes.byref(p)), "kirin_hermite_run")
         return s.value, p.value
+
+    def set_device_loop(self, enable=True):
+        self._check(self.lib.kirin_set_device_loop(self.ctx, 1 if enable else 0), "kirin_set_device_loop")
 
     def hermite_shared_step(self, dt):
         self._check(self.lib.kirin_hermite_shared_step(self.ctx, float(dt)), "kirin_hermite_shared_step")

@@ -36,7 +36,8 @@ def _candidates(auto, ntiles, big):
     when the block alone fills the GPU many times over)."""
     g0, s0 = auto
     cands = {(g0, s0)}
-    splits = (1, 2, 3, 4) if big else (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+    splits = (1, 2, 3, 4) if big else (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512,
+                                       768, 1024)
     for g in (1, 2, 4, 8):
         for s in splits:
             if s <= ntiles:
@@ -84,11 +85,17 @@ def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, d
             k.compute_forces_dev(il, acc, jerk, pot)  # warm-up
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             ev[0].record()
-            for _ in range(reps):
+            k.compute_forces_dev(il, acc, jerk, pot)
+            ev[1].record()
+            torch.cuda.synchronize()
+            # short calls: repeat until about 2 ms are timed
+            r = int(min(200, max(reps, 2e-3 / max(ev[0].elapsed_time(ev[1]) / 1e3, 1e-7))))
+            ev[0].record()
+            for _ in range(r):
                 k.compute_forces_dev(il, acc, jerk, pot)
             ev[1].record()
             torch.cuda.synchronize()
-            t = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+            t = ev[0].elapsed_time(ev[1]) / 1e3 / r
             if best is None or t < best[3]:
                 best = (n_i, g, s, t)
         table.append(best)

@@ -22,6 +22,15 @@
 
 using namespace kirin;
 
+// Parameters and counters of a device-driven run, one copy on each side.
+struct RunCounters {
+    double t_end;
+    long long max_steps;  // 0 = unbounded
+    long long steps;      // block steps taken
+    double pairs;         // sum over the steps of n_active * n_j
+    double t_last;        // time of the last block stepped
+};
+
 struct kirin_ctx {
     int device = 0;
     int nsm = 0;
@@ -64,6 +73,15 @@ struct kirin_ctx {
     // Hermite integrator
     bool hermite_ready = false;
     double eta = 0.01, dt_min = 1.0 / (1 << 20), dt_max = 0.125, t_shared = 0;
+
+    // Device-driven block steps: one graph whose WHILE node repeats select ->
+    // predict -> force (a SWITCH over block-size classes) -> correct, so a
+    // run to t_end is one graph launch and one read-back.
+    bool device_loop = true;
+    cudaGraphExec_t run_exec = nullptr;
+    uint64_t run_key = 0;
+    RunCounters *d_run = nullptr;  // run parameters and counters (device)
+    RunCounters *h_run = nullptr;  // pinned mirror
 
     // launch-shape override (0 = automatic), tuned table and occupancy cache
     int fix_groups = 0, fix_split = 0;
@@ -209,19 +227,22 @@ int ensure_images(kirin_ctx *c)
     return KIRIN_OK;
 }
 
-// Enqueue one force launch (plus split reduction) over the current images.
-int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mode, double *acc,
-              double *jerk, double *pot, int accumulate = 0, int32_t *nn = nullptr, double *nn_r2 = nullptr)
+// Enqueue one force launch (plus split reduction) over the current images,
+// with a given shape, on stream st.  n_i bounds the grid; with n_i_dev set the
+// kernels read the actual count from there (device-driven loops).  The split
+// partial buffer must already hold the launch.
+int enqueue_force(kirin_ctx *c, cudaStream_t st, Shape s, int64_t n_i, const int32_t *n_i_dev,
+                  const int32_t *d_ilist, int n_j, int mode, double *acc, double *jerk, double *pot,
+                  int accumulate = 0, int32_t *nn = nullptr, double *nn_r2 = nullptr)
 {
     if (n_i == 0)
         return KIRIN_OK;
     const int ntiles = (int)((std::max(n_j, 1) + TILE_J - 1) / TILE_J);
-    const bool guard = guard_on(c);
-    const Shape s = choose_shape(c, n_i, ntiles, c->prec, mode, guard);
     ForceArgs a{};
     a.jimg = c->prec == KIRIN_MIXED ? (const void *)c->jm : (const void *)c->jd;
     a.ilist = d_ilist;
     a.n_i = (int)n_i;
+    a.n_i_dev = n_i_dev;
     a.n_j = n_j;
     a.ntiles = ntiles;
     a.n_split = s.n_split;
@@ -239,18 +260,42 @@ int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mo
     const int i_cta = (c->prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1) * FORCE_THREADS / s.groups;
     a.n_i_pad = (int)round_up(n_i, i_cta);
     if (s.n_split > 1) {
-        int rc = ensure_partial(c, (size_t)s.n_split * a.nq * a.n_i_pad);
-        if (rc)
-            return rc;
+        if ((size_t)s.n_split * a.nq * a.n_i_pad > c->partial_cap)
+            return set_msg(c, KIRIN_ESTATE, "split-partial buffer too small for the launch");
         a.partial = c->d_partial;
     }
     if (c->prec == KIRIN_MIXED)
-        CK(c, launch_force_mixed(a, s, guard, mode, c->stream));
+        CK(c, launch_force_mixed(a, s, guard_on(c), mode, st));
     else
-        CK(c, launch_force_fp64(a, s, mode, c->stream));
+        CK(c, launch_force_fp64(a, s, mode, st));
     if (s.n_split > 1)
-        CK(c, launch_reduce_splits(a, c->stream));
+        CK(c, launch_reduce_splits(a, st));
     return KIRIN_OK;
+}
+
+// Doubles of split partials a launch of n_i i-particles with shape s needs.
+size_t partial_doubles(const kirin_ctx *c, Shape s, int64_t n_i, int mode)
+{
+    if (s.n_split <= 1)
+        return 0;
+    const int i_cta = (c->prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1) * FORCE_THREADS / s.groups;
+    return (size_t)s.n_split * (mode == MODE_NN ? 9 : 7) * (size_t)round_up(n_i, i_cta);
+}
+
+// Enqueue one force launch (plus split reduction) over the current images on
+// the context's stream, with the shape of choose_shape.
+int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mode, double *acc,
+              double *jerk, double *pot, int accumulate = 0, int32_t *nn = nullptr, double *nn_r2 = nullptr)
+{
+    if (n_i == 0)
+        return KIRIN_OK;
+    const int ntiles = (int)((std::max(n_j, 1) + TILE_J - 1) / TILE_J);
+    const Shape s = choose_shape(c, n_i, ntiles, c->prec, mode, guard_on(c));
+    int rc = ensure_partial(c, partial_doubles(c, s, n_i, mode));
+    if (rc)
+        return rc;
+    return enqueue_force(c, c->stream, s, n_i, nullptr, d_ilist, n_j, mode, acc, jerk, pot, accumulate, nn,
+                         nn_r2);
 }
 
 int read_device_errors(kirin_ctx *c)
@@ -265,6 +310,8 @@ int read_device_errors(kirin_ctx *c)
         return set_msg(c, KIRIN_ETIMEOUT, "a bounded device wait gave up (flags 0x%x)", e);
     if (e & ERR_NONFINITE)
         return set_msg(c, KIRIN_ENONFINITE, "non-finite particle data on the device");
+    if (e & ERR_STALL)
+        return set_msg(c, KIRIN_ESTATE, "block time stopped advancing (t + dt == t in FP64)");
     if (e & ERR_INDEX)
         return set_msg(c, KIRIN_EINVAL, "i index outside [0, n_j) on the device");
     return set_msg(c, KIRIN_ECUDA, "device error flags 0x%x", e);
@@ -294,6 +341,12 @@ void free_all(kirin_ctx *c)
         cudaFreeHost(c->h_count);
     if (c->h_err)
         cudaFreeHost(c->h_err);
+    if (c->h_run)
+        cudaFreeHost(c->h_run);
+    if (c->d_run)
+        cudaFree(c->d_run);
+    if (c->run_exec)
+        cudaGraphExecDestroy(c->run_exec);
     if (c->own_stream && c->stream)
         cudaStreamDestroy(c->stream);
 }
@@ -304,6 +357,204 @@ int check_params(double eps, double G, double r_min, int prec)
         return KIRIN_EINVAL;
     if (prec != KIRIN_FP64 && prec != KIRIN_MIXED)
         return KIRIN_EINVAL;
+    return KIRIN_OK;
+}
+
+
+// ---- device-driven block steps ---------------------------------------------
+//
+// The graph:  WHILE(loop) { reset-min; select; predict; SWITCH(branch)
+// { force launch for block-size class 0 | 1 | ... }; correct }.  The select
+// kernel sets both conditions from the block it finds.  Each class c covers
+// block sizes (class_max[c-1], class_max[c]]; its force launch has a grid for
+// class_max[c] and the shape chosen for a block of about 0.7 class_max[c], and
+// its CTAs beyond the actual block return at once.
+
+struct RunPlan {
+    int n_classes = 0;
+    int32_t class_max[MAX_SEL_CLASSES] = {};
+    Shape shape[MAX_SEL_CLASSES] = {};
+};
+
+RunPlan plan_run(kirin_ctx *c)
+{
+    RunPlan p;
+    const int64_t n = c->n_j;
+    int64_t hi = n;
+    int32_t desc[MAX_SEL_CLASSES];
+    int k = 0;
+    while (hi > 64 && k < MAX_SEL_CLASSES - 1) {
+        desc[k++] = (int32_t)hi;
+        hi = (hi + 1) / 2;
+    }
+    desc[k++] = (int32_t)hi;
+    p.n_classes = k;
+    const int ntiles = (int)((std::max<int64_t>(n, 1) + TILE_J - 1) / TILE_J);
+    for (int q = 0; q < k; ++q) {
+        p.class_max[q] = desc[k - 1 - q];
+        const int64_t rep = std::max<int64_t>(1, (int64_t)(0.7 * p.class_max[q]));
+        p.shape[q] = choose_shape(c, rep, ntiles, c->prec, MODE_ACC_JERK_POT, guard_on(c));
+    }
+    return p;
+}
+
+uint64_t fnv1a(uint64_t h, const void *data, size_t bytes)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(data);
+    for (size_t k = 0; k < bytes; ++k) {
+        h ^= b[k];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Everything the instantiated graph bakes in: sizes, parameters, shapes and
+// the addresses of buffers that can be re-allocated.
+uint64_t run_key(const kirin_ctx *c, const RunPlan &p)
+{
+    uint64_t h = 1469598103934665603ull;
+    const double par[6] = {c->eps, c->G, c->r_min, c->eta, c->dt_min, c->dt_max};
+    h = fnv1a(h, par, sizeof(par));
+    const int64_t sizes[2] = {c->n_j, c->prec};
+    h = fnv1a(h, sizes, sizeof(sizes));
+    h = fnv1a(h, &c->d_partial, sizeof(c->d_partial));
+    h = fnv1a(h, p.class_max, sizeof(int32_t) * p.n_classes);
+    h = fnv1a(h, p.shape, sizeof(Shape) * p.n_classes);
+    return h | 1;  // never 0, the "no graph" key
+}
+
+// Capture onto the body graph `g` with stream cs.
+#define CKG(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            rc = set_msg(c, KIRIN_ECUDA, "device loop: %s: %s", #call, cudaGetErrorString(e_)); \
+            goto done;                                                                         \
+        }                                                                                      \
+    } while (0)
+
+int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
+{
+    int rc = KIRIN_OK;
+    cudaGraph_t top = nullptr;
+    cudaStream_t cs = nullptr;
+    bool capturing = false;
+    cudaGraphConditionalHandle h_loop, h_branch;
+    cudaGraphNodeParams wp{}, sp{};
+    cudaGraphNode_t wnode, snode;
+    cudaGraph_t body, cap_graph;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaStreamCaptureStatus status;
+    const int n = (int)c->n_j;
+    const int64_t n_pad = round_up(std::max<int64_t>(n, 1), TILE_J);
+    RunCounters *r = c->d_run;
+
+    CKG(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CKG(cudaGraphCreate(&top, 0));
+    CKG(cudaGraphConditionalHandleCreate(&h_loop, top, 1, cudaGraphCondAssignDefault));
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    CKG(cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp));
+    body = wp.conditional.phGraph_out[0];
+    CKG(cudaGraphConditionalHandleCreate(&h_branch, body, 0, cudaGraphCondAssignDefault));
+
+    // loop body: select, predict, SWITCH, correct
+    CKG(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capturing = true;
+    CKG(launch_block_select_graph(n, c->bt, c->bdt, &r->t_end, c->d_ilist, c->d_scal, c->d_count,
+                                  reinterpret_cast<unsigned long long *>(c->d_scal + 3), c->d_sel_counts, h_loop,
+                                  h_branch, p.n_classes, p.class_max, &r->max_steps, &r->steps, &r->pairs,
+                                  &r->t_last, c->d_err, n, cs));
+    CKG(launch_predict_pack(n, (int)n_pad, 0.0, 1, c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->xp, c->vp, c->jm,
+                            c->jd, c->d_err, cs, c->d_scal, c->d_count));
+    CKG(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cap_graph, &deps, nullptr, &ndeps));
+    sp.type = cudaGraphNodeTypeConditional;
+    sp.conditional.handle = h_branch;
+    sp.conditional.type = cudaGraphCondTypeSwitch;
+    sp.conditional.size = (unsigned)p.n_classes;
+    CKG(cudaGraphAddNode(&snode, cap_graph, deps, nullptr, ndeps, &sp));
+    CKG(cudaStreamUpdateCaptureDependencies(cs, &snode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CKG(launch_hermite_correct(n, c->d_ilist, 0.0, c->eta, c->dt_min, c->dt_max, 1, c->xp, c->vp, c->d_acc,
+                               c->d_jerk, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, cs, c->d_count, c->d_scal));
+    capturing = false;
+    CKG(cudaStreamEndCapture(cs, &cap_graph));
+
+    // the force branches
+    for (int q = 0; q < p.n_classes; ++q) {
+        CKG(cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[q], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        rc = enqueue_force(c, cs, p.shape[q], p.class_max[q], c->d_count, c->d_ilist, n, MODE_ACC_JERK_POT,
+                           c->d_acc, c->d_jerk, c->d_pot);
+        if (rc)
+            goto done;
+        capturing = false;
+        CKG(cudaStreamEndCapture(cs, &cap_graph));
+    }
+    CKG(cudaGraphInstantiate(exec_out, top, 0));
+
+done:
+    if (capturing) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        cudaGetLastError();
+    }
+    if (top)
+        cudaGraphDestroy(top);
+    if (cs)
+        cudaStreamDestroy(cs);
+    return rc;
+}
+#undef CKG
+
+int hermite_run_device(kirin_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps, double *n_pairs)
+{
+    DeviceGuard dg(c->device);
+    const RunPlan p = plan_run(c);
+    size_t need = 0;
+    for (int q = 0; q < p.n_classes; ++q)
+        need = std::max(need, partial_doubles(c, p.shape[q], p.class_max[q], MODE_ACC_JERK_POT));
+    int rc = ensure_partial(c, need);
+    if (rc)
+        return rc;
+    const uint64_t key = run_key(c, p);
+    if (!c->run_exec || key != c->run_key) {
+        if (c->run_exec) {
+            CK(c, cudaStreamSynchronize(c->stream));
+            cudaGraphExecDestroy(c->run_exec);
+            c->run_exec = nullptr;
+            c->run_key = 0;
+        }
+        rc = build_run_graph(c, p, &c->run_exec);
+        if (rc) {
+            c->run_exec = nullptr;
+            return rc;
+        }
+        c->run_key = key;
+    }
+    // the pinned mirror may still be the source or target of the last run's copies
+    CK(c, cudaStreamSynchronize(c->stream));
+    *c->h_run = RunCounters{t_end, (long long)std::max<int64_t>(max_steps, 0), 0, 0.0, 0.0};
+    CK(c, cudaMemcpyAsync(c->d_run, c->h_run, sizeof(RunCounters), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaGraphLaunch(c->run_exec, c->stream));
+    CK(c, cudaMemcpyAsync(c->h_run, c->d_run, sizeof(RunCounters), cudaMemcpyDeviceToHost, c->stream));
+    rc = read_device_errors(c);  // synchronises the stream
+    if (rc)
+        return rc;
+    const RunCounters out = *c->h_run;
+    if (n_steps)
+        *n_steps = out.steps;
+    if (n_pairs)
+        *n_pairs = out.pairs;
+    if (out.steps > 0) {
+        c->pred_mode = 1;
+        c->pred_t = out.t_last;
+    }
+    c->images_dirty = true;  // base state moved
+    c->pending = false;
     return KIRIN_OK;
 }
 
@@ -398,6 +649,9 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
     if (ok && cudaMallocHost((void **)&c->h_count, sizeof(int32_t)) != cudaSuccess)
         ok = false;
     if (ok && cudaMallocHost((void **)&c->h_err, sizeof(unsigned)) != cudaSuccess)
+        ok = false;
+    dalloc((void **)&c->d_run, sizeof(RunCounters));
+    if (ok && cudaMallocHost((void **)&c->h_run, sizeof(RunCounters)) != cudaSuccess)
         ok = false;
     if (ok && cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream) != cudaSuccess)
         ok = false;
@@ -832,8 +1086,12 @@ int kirin_hermite_block_step(kirin_ctx *ctx, double t_end, double *t_now, int64_
 
 int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *n_steps, double *n_pairs)
 {
-    if (!ctx)
+    if (!ctx || !isfinite(t_end))
         return KIRIN_EINVAL;
+    if (!ctx->hermite_ready)
+        return set_msg(ctx, KIRIN_ESTATE, "hermite_run: call kirin_hermite_init first");
+    if (ctx->device_loop)
+        return hermite_run_device(ctx, t_end, max_steps, n_steps, n_pairs);
     int64_t steps = 0;
     double pairs = 0.0;
     while (max_steps <= 0 || steps < max_steps) {
@@ -853,6 +1111,14 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
         *n_pairs = pairs;
     DeviceGuard dg(ctx->device);
     return read_device_errors(ctx);
+}
+
+int kirin_set_device_loop(kirin_ctx *ctx, int32_t enable)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    ctx->device_loop = enable != 0;
+    return KIRIN_OK;
 }
 
 int kirin_hermite_shared_step(kirin_ctx *ctx, double dt)

@@ -16,27 +16,50 @@ constexpr int AUX_THREADS = 256;
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
-// Sum the n_split partial results of every (i, quantity) in split order and
-// write the scaled outputs (acc, jerk: G * sum; pot: -G * sum); with the
-// neighbour search also the nearest (r2, j) over the splits.
-__global__ void k_reduce_splits(const ForceArgs A)
+// Sum the n_split partial results of every (i, quantity) and write the
+// scaled outputs (acc, jerk: G * sum; pot: -G * sum); with the neighbour
+// search also the nearest (r2, j) over the splits.  L lanes share one output:
+// lane l sums splits l, l + L, ... in order, then the L partial sums meet in
+// a fixed xor tree, so the result does not depend on timing.  Threads are
+// ordered quantity-major, i fastest, so L = 1 reads are coalesced.
+template <int L>
+__global__ void k_reduce_splits(const ForceArgs Ain)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= A.n_i)
-        return;
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
+    ForceArgs A = Ain;
+    if (Ain.n_i_dev)
+        A.n_i = *Ain.n_i_dev;
+    const int nout = A.nq > 7 ? 8 : 7;  // the neighbour pair (r2, j) is output 7
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long g = t / L;
+    const int lane = (int)(t % L);
+    if (g >= (long long)nout * A.n_i)
+        return;  // whole groups leave together (L divides the warp)
+    const int q = (int)(g / A.n_i);
+    const int k = (int)(g - (long long)q * A.n_i);
+    const unsigned wl = threadIdx.x & 31u;
+    const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (wl & ~(unsigned)(L - 1)));
+    if (q < 7) {
         double sum = 0.0;
-        for (int y = 0; y < A.n_split; ++y)
+        for (int y = lane; y < A.n_split; y += L)
             sum += A.partial[((size_t)y * A.nq + q) * A.n_i_pad + k];
-        store_final(A, q, k, sum);
-    }
-    if (A.nq > 7) {  // nearest neighbour: lexicographic minimum over the splits
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1)
+            sum += __shfl_xor_sync(mask, sum, o, L);
+        if (lane == 0)
+            store_final(A, q, k, sum);
+    } else {  // nearest neighbour: lexicographic minimum over the splits
         double r2 = INFINITY, j = -1.0;
-        for (int y = 0; y < A.n_split; ++y)
+        for (int y = lane; y < A.n_split; y += L)
             nn_min(r2, j, A.partial[((size_t)y * A.nq + 7) * A.n_i_pad + k],
                    A.partial[((size_t)y * A.nq + 8) * A.n_i_pad + k]);
-        store_nn(A, k, r2, j);
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) {
+            const double r2b = __shfl_xor_sync(mask, r2, o, L);
+            const double jb = __shfl_xor_sync(mask, j, o, L);
+            nn_min(r2, j, r2b, jb);
+        }
+        if (lane == 0)
+            store_nn(A, k, r2, j);
     }
 }
 
@@ -80,11 +103,15 @@ __global__ void k_predict_pack(int n, int n_pad, double t, int predict, const do
                                const double *__restrict__ x, const double *__restrict__ v,
                                const double *__restrict__ a, const double *__restrict__ jk,
                                const double *__restrict__ t0, double *xp, double *vp, JMixed *jm,
-                               JF64 *jd, unsigned *err)
+                               JF64 *jd, unsigned *err, const double *t_dev, const int32_t *count_dev)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_pad)
         return;
+    if (count_dev && *count_dev == 0)
+        return;  // device-driven loop: no block this iteration
+    if (t_dev)
+        t = *t_dev;
     if (k >= n) {
         write_images(k, PAD_POS, PAD_POS, PAD_POS, 0.0, 0.0, 0.0, 0.0, jm, jd);
         return;
@@ -263,16 +290,39 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_count(int n, const double *
         counts[blockIdx.x] = total;
 }
 
+// Loop control of a device-driven block-step run (graph conditional nodes):
+// the size classes of the force branches and the run's counters.
+struct SelGraph {
+    cudaGraphConditionalHandle loop;    // WHILE: another block step?
+    cudaGraphConditionalHandle branch;  // SWITCH: which force launch (n_classes = none)
+    int n_classes;
+    int32_t class_max[MAX_SEL_CLASSES]; // ascending upper bounds of the block size
+    const double *t_end;                // end time of the run (device, set before each launch)
+    const long long *max_steps;         // step limit of the run, 0 = unbounded (device)
+    long long *steps;                   // device counters of the run
+    double *pairs;
+    double *t_last;                     // time of the last block stepped
+    unsigned *err;
+    int n_j;
+};
+
+// Start value of the atomic minimum, as a kernel node (the conditional body
+// of a graph then holds kernel nodes only).
+__global__ void k_reset_min(unsigned long long *minw) { *minw = ~0ull; }
+
+template <bool GRAPH>
 __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *__restrict__ bt,
                                                            const double *__restrict__ bdt,
                                                            const unsigned long long *minw,
                                                            const int32_t *__restrict__ counts, double t_end,
                                                            int32_t *ilist, double *t_next_out,
-                                                           int32_t *count_out)
+                                                           int32_t *count_out, SelGraph gctl)
 {
     __shared__ int warp_tot[SEL_THREADS / 32];
     __shared__ int red[SEL_THREADS];
     const double tn = __longlong_as_double((long long)*minw);
+    if (GRAPH)
+        t_end = *gctl.t_end;
     const bool due = tn <= t_end;
     // offset of this CTA: sum of the counts of the CTAs before it
     int part = 0;
@@ -307,8 +357,29 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *
         __syncthreads();
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        *count_out = due ? base : 0;
+        int count = due ? base : 0;
+        if (GRAPH && count > 0 && *gctl.steps > 0 && !(tn > *gctl.t_last)) {
+            atomicOr(gctl.err, ERR_STALL);  // no progress: stop rather than repeat the block forever
+            count = 0;
+        }
+        *count_out = count;
         *t_next_out = tn;
+        if (GRAPH) {
+            unsigned cls = (unsigned)gctl.n_classes;  // no branch when the block is empty
+            if (count > 0) {
+                cls = (unsigned)gctl.n_classes - 1;
+                for (int c = gctl.n_classes - 1; c >= 0; --c)
+                    if (count <= gctl.class_max[c])
+                        cls = (unsigned)c;
+                *gctl.steps += 1;
+                *gctl.pairs += (double)count * (double)gctl.n_j;
+                *gctl.t_last = tn;
+            }
+            cudaGraphSetConditional(gctl.branch, cls);
+            const long long lim = *gctl.max_steps;
+            const bool more = count > 0 && (lim <= 0 || *gctl.steps < lim);
+            cudaGraphSetConditional(gctl.loop, more ? 1u : 0u);
+        }
     }
 }
 
@@ -319,8 +390,13 @@ __global__ void k_hermite_correct(int n_act, const int32_t *__restrict__ ilist, 
                                   double eta, double dt_min, double dt_max, int update_dt,
                                   const double *__restrict__ xp, const double *__restrict__ vp,
                                   const double *__restrict__ acc, const double *__restrict__ jerk,
-                                  double *bx, double *bv, double *ba, double *bj, double *bt, double *bdt)
+                                  double *bx, double *bv, double *ba, double *bj, double *bt, double *bdt,
+                                  const int32_t *n_dev, const double *t_dev)
 {
+    if (n_dev)
+        n_act = *n_dev;
+    if (t_dev)
+        t_next = *t_dev;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_act)
         return;
@@ -433,19 +509,33 @@ cudaError_t launch_reduce_splits(const ForceArgs &a, cudaStream_t st)
 {
     if (a.n_i == 0)
         return cudaSuccess;
-    k_reduce_splits<<<blocks_for(a.n_i, AUX_THREADS), AUX_THREADS, 0, st>>>(a);
+    // lanes per output: the smallest power of two that leaves each lane at most 8 splits
+    int lanes = 1;
+    while (lanes < 32 && lanes * 8 < a.n_split)
+        lanes *= 2;
+    const long long threads = (long long)(a.nq > 7 ? 8 : 7) * a.n_i * lanes;
+    const int grid = (int)((threads + AUX_THREADS - 1) / AUX_THREADS);
+    switch (lanes) {
+    case 1: k_reduce_splits<1><<<grid, AUX_THREADS, 0, st>>>(a); break;
+    case 2: k_reduce_splits<2><<<grid, AUX_THREADS, 0, st>>>(a); break;
+    case 4: k_reduce_splits<4><<<grid, AUX_THREADS, 0, st>>>(a); break;
+    case 8: k_reduce_splits<8><<<grid, AUX_THREADS, 0, st>>>(a); break;
+    case 16: k_reduce_splits<16><<<grid, AUX_THREADS, 0, st>>>(a); break;
+    default: k_reduce_splits<32><<<grid, AUX_THREADS, 0, st>>>(a); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_predict_pack(int n, int n_pad, double t, int predict, const double *m,
                                 const double *x, const double *v, const double *a,
                                 const double *jk, const double *t0, double *xp, double *vp,
-                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st)
+                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st, const double *t_dev,
+                                const int32_t *count_dev)
 {
     if (n_pad == 0)
         return cudaSuccess;
     k_predict_pack<<<blocks_for(n_pad, AUX_THREADS), AUX_THREADS, 0, st>>>(
-        n, n_pad, t, predict, m, x, v, a, jk, t0, xp, vp, jm, jd, err);
+        n, n_pad, t, predict, m, x, v, a, jk, t0, xp, vp, jm, jd, err, t_dev, count_dev);
     return cudaGetLastError();
 }
 
@@ -499,7 +589,38 @@ cudaError_t launch_block_select(int n, const double *bt, const double *bdt, doub
         return e;
     k_sel_min<<<std::min(nblk * SEL_ITEMS, 1024), SEL_THREADS, 0, st>>>(n, bt, bdt, minw);
     k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts);
-    k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, t_end, ilist, t_next_out, count_out);
+    k_sel_write<false><<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, t_end, ilist, t_next_out, count_out,
+                                                     SelGraph{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_select_graph(int n, const double *bt, const double *bdt, const double *t_end,
+                                      int32_t *ilist, double *t_next_out, int32_t *count_out,
+                                      unsigned long long *minw, int32_t *counts, cudaGraphConditionalHandle loop,
+                                      cudaGraphConditionalHandle branch, int n_classes, const int32_t *class_max,
+                                      const long long *max_steps, long long *steps, double *pairs,
+                                      double *t_last, unsigned *err, int n_j, cudaStream_t st)
+{
+    if (n_classes < 1 || n_classes > MAX_SEL_CLASSES)
+        return cudaErrorInvalidValue;
+    SelGraph g{};
+    g.loop = loop;
+    g.branch = branch;
+    g.n_classes = n_classes;
+    for (int c = 0; c < n_classes; ++c)
+        g.class_max[c] = class_max[c];
+    g.t_end = t_end;
+    g.max_steps = max_steps;
+    g.steps = steps;
+    g.pairs = pairs;
+    g.t_last = t_last;
+    g.err = err;
+    g.n_j = n_j;
+    const int nblk = blocks_for(n, SEL_PER_CTA);
+    k_reset_min<<<1, 1, 0, st>>>(minw);
+    k_sel_min<<<std::min(nblk * SEL_ITEMS, 1024), SEL_THREADS, 0, st>>>(n, bt, bdt, minw);
+    k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts);
+    k_sel_write<true><<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, 0.0, ilist, t_next_out, count_out, g);
     return cudaGetLastError();
 }
 
@@ -507,13 +628,14 @@ cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_nex
                                    double dt_min, double dt_max, int update_dt,
                                    const double *xp, const double *vp, const double *acc,
                                    const double *jerk, double *bx, double *bv, double *ba,
-                                   double *bj, double *bt, double *bdt, cudaStream_t st)
+                                   double *bj, double *bt, double *bdt, cudaStream_t st, const int32_t *n_dev,
+                                   const double *t_dev)
 {
     if (n_act == 0)
         return cudaSuccess;
     k_hermite_correct<<<blocks_for(n_act, AUX_THREADS), AUX_THREADS, 0, st>>>(
         n_act, ilist, t_next, eta, dt_min, dt_max, update_dt, xp, vp, acc, jerk, bx, bv, ba, bj, bt,
-        bdt);
+        bdt, n_dev, t_dev);
     return cudaGetLastError();
 }
 

@@ -45,8 +45,11 @@ constexpr size_t F64_RED_BYTES = (size_t)9 * FORCE_THREADS * sizeof(double);
 constexpr size_t F64_SMEM_BYTES = F64_RING_BYTES > F64_RED_BYTES ? F64_RING_BYTES : F64_RED_BYTES;
 
 template <int GROUPS, int MODE>
-__global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
+__global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs Ain)
 {
+    ForceArgs A = Ain;
+    if (Ain.n_i_dev)
+        A.n_i = *Ain.n_i_dev;
     constexpr bool ADJ = MODE == MODE_ADJOINT;
     constexpr bool NN = MODE == MODE_NN;
     constexpr bool JERK = MODE == MODE_ACC_JERK_POT || NN;
@@ -60,6 +63,8 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs A)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     JF64 *tiles = reinterpret_cast<JF64 *>(smem_raw);
     __shared__ __align__(8) uint64_t bars[STAGES];
+    if ((long long)blockIdx.x * I_CTA >= A.n_i)
+        return;  // beyond the block of a device-driven launch (uniform over the CTA)
 
     const int tid = threadIdx.x;
     const int g = tid / GT;

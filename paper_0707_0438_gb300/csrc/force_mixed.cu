@@ -88,8 +88,11 @@ constexpr size_t MIX_RED_BYTES = (size_t)9 * MIX_I_PER_THREAD * FORCE_THREADS * 
 constexpr size_t MIX_SMEM_BYTES = MIX_RING_BYTES > MIX_RED_BYTES ? MIX_RING_BYTES : MIX_RED_BYTES;
 
 template <int GROUPS, bool GUARD, int MODE>
-__global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(const ForceArgs A)
+__global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(const ForceArgs Ain)
 {
+    ForceArgs A = Ain;
+    if (Ain.n_i_dev)
+        A.n_i = *Ain.n_i_dev;
     constexpr bool ADJ = MODE == MODE_ADJOINT;
     constexpr bool NN = MODE == MODE_NN;
     constexpr int NQ = NN ? 9 : 7;              // reduced quantities per i
@@ -104,6 +107,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
     extern __shared__ __align__(128) unsigned char smem_raw[];
     JMixed *tiles = reinterpret_cast<JMixed *>(smem_raw);
     __shared__ __align__(8) uint64_t bars[STAGES];
+    if ((long long)blockIdx.x * I_CTA >= A.n_i)
+        return;  // beyond the block of a device-driven launch (uniform over the CTA)
 
     const int tid = threadIdx.x;
     const int g = tid / GT;

@@ -1,0 +1,105 @@
+"""The device-driven block-step loop of kirin_hermite_run (one CUDA graph with a
+conditional WHILE node and a SWITCH over force launches) against the same steps
+taken with one host round trip each (Sect. 3.1 block time-steps), and against
+the oracle's schedule."""
+import numpy as np
+import pytest
+
+from oracle import hermite
+from paper_0707_0438_gb300 import abi, workloads
+
+pytestmark = pytest.mark.gpu
+
+STATE_KEYS = ("x", "v", "a", "j", "t", "dt")
+FIXED = {"mixed": (2, 4), "fp64": (1, 4)}
+
+
+def _run(p, precision, device_loop, t_ends, launch=None, max_steps=0):
+    """Block steps to each t_end in turn; returns [(steps, pairs)], the state and the energy."""
+    with abi.Kirin(p.n, p.eps, precision=precision) as k:
+        if launch:
+            k.set_launch(*launch)
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        k.set_device_loop(device_loop)
+        counts = [k.hermite_run(t, max_steps) for t in t_ends]
+        st = k.get_state()
+        e = sum(k.energy())
+    return counts, st, e
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("n", [4096, 48])
+def test_device_loop_is_bitwise_the_host_loop(kirin_lib, precision, n):
+    """Same fixed launch shape: identical step counts, pair counts and state, over
+    two calls with different end times (one graph, t_end read on the device)."""
+    p = workloads.plummer(n, 1002, eps=1e-3)
+    t_ends = [1.0 / 64, 1.0 / 32]
+    host = _run(p, precision, False, t_ends, FIXED[precision])
+    dev = _run(p, precision, True, t_ends, FIXED[precision])
+    assert dev[0] == host[0]
+    assert all(c[0] > 0 for c in dev[0])
+    for key in STATE_KEYS:
+        assert np.array_equal(dev[1][key], host[1][key]), key
+    assert dev[2] == host[2]
+
+
+def test_device_loop_fp64_follows_the_oracle_schedule(kirin_lib):
+    """Automatic shapes (a ladder of launches by block size): the oracle's block
+    sequence length and pair count, its times and steps exactly, its positions
+    to FP64 rounding."""
+    p = workloads.plummer(256, 1002, eps=1e-3)
+    t_end = 1.0 / 8
+    ref = hermite.block_steps(p.m, p.x, p.v, p.eps, t_end=t_end)
+    [(steps, pairs)], st, e = _run(p, "fp64", True, [t_end])
+    assert steps == len(ref["blocks"])
+    assert pairs == float(sum(ref["blocks"])) * p.n
+    assert np.array_equal(st["t"], ref["t"]) and np.all(st["t"] == t_end)
+    assert np.array_equal(st["dt"], ref["dt"])
+    assert np.abs(st["x"] - ref["x"]).max() <= 1e-9
+    assert e == pytest.approx(ref["e_end"], rel=1e-10)
+
+
+def test_device_loop_max_steps_and_rebuild_on_new_shape(kirin_lib):
+    """max_steps stops the device loop exactly; a later call resumes it; changing
+    the launch shape between calls rebuilds the graph (results stay those of the
+    host loop under the same shapes)."""
+    p = workloads.plummer(2048, 1005, eps=1e-3)
+    t_end = 1.0 / 32
+    with abi.Kirin(p.n, p.eps, precision="mixed") as kd, abi.Kirin(p.n, p.eps, precision="mixed") as kh:
+        for k, dev in ((kd, True), (kh, False)):
+            k.set_launch(2, 4)
+            k.set_j_particles(p.m, p.x, p.v)
+            k.hermite_init(0.0)
+            k.set_device_loop(dev)
+        a = kd.hermite_run(t_end, 5)
+        b = kh.hermite_run(t_end, 5)
+        assert a == b and a[0] == 5
+        for k in (kd, kh):
+            k.set_launch(4, 8)
+        a = kd.hermite_run(t_end)
+        b = kh.hermite_run(t_end)
+        assert a == b and a[0] > 0
+        sd, sh = kd.get_state(), kh.get_state()
+        assert kd.hermite_run(t_end) == (0, 0.0)  # nothing left before t_end
+    for key in STATE_KEYS:
+        assert np.array_equal(sd[key], sh[key]), key
+    # every particle stepped as far as it can without passing t_end
+    assert np.all(sd["t"] <= t_end) and np.all(sd["t"] + sd["dt"] > t_end)
+
+
+def test_device_loop_automatic_shapes_mixed(kirin_lib):
+    """Mixed precision with automatic shapes on both paths (the device ladder and
+    the host's per-block choice differ in summation order only): the same energy
+    to the mixed kernel's rounding, positions to 1e-9 of their scale."""
+    p = workloads.plummer(16384, 1002, eps=1e-3)
+    t_end = 1.0 / 64
+    host = _run(p, "mixed", False, [t_end])
+    dev = _run(p, "mixed", True, [t_end])
+    (sh, ph), (sd, pd) = host[0][0], dev[0][0]
+    assert abs(sd - sh) <= 2 and sd > 0
+    t, dt = dev[1]["t"], dev[1]["dt"]
+    assert np.all(t <= t_end) and np.all(t + dt > t_end)
+    scale = np.abs(p.x).max()
+    assert np.abs(dev[1]["x"] - host[1]["x"]).max() <= 1e-9 * scale
+    assert dev[2] == pytest.approx(host[2], rel=1e-9)

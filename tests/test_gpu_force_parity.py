@@ -69,6 +69,20 @@ def test_every_launch_shape_gives_the_same_answer(kirin_lib, precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+def test_wide_j_split_reduction(kirin_lib, precision):
+    """Few i against many j tiles with up to one split per tile (Sect. 3.2): the
+    split partials are reduced by 1 to 32 lanes per output."""
+    p = workloads.plummer(40000, 91, eps=1e-3)  # 313 tiles, the last one ragged
+    il = workloads.i_subset(p.n, 37, seed=5)
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    with _ctx(p, precision) as k:
+        for groups, n_split in ((8, 9), (8, 64), (4, 130), (1, 257), (8, 1024)):
+            k.set_launch(groups, n_split)
+            assert_parity(k.forces(il), ref, precision, f"groups={groups} split={n_split}")
+        k.set_launch(0, 0)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_duplicate_and_unordered_i_list(kirin_lib, precision):
     p = workloads.plummer(700, 8, eps=0.01)
     il = np.array([699, 0, 17, 17, 350, 0], dtype=np.int32)

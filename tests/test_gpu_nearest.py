@@ -77,6 +77,25 @@ def test_nearest_through_every_launch_shape_and_host_path(kirin_lib, precision):
             k.get_nn()
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_neighbour_minimum_over_wide_splits(kirin_lib, precision):
+    """The lexicographic minimum survives a reduction over up to 313 splits."""
+    p = workloads.plummer(40000, 12, eps=0.01)
+    x = p.x.copy()
+    x[39999] = x[3]  # a coincident pair in the ragged last tile and the first
+    il = np.concatenate([workloads.i_subset(p.n, 20, 4), [3, 39999]]).astype(np.int32)
+    ref = oracle.acc_jerk_pot(p.m, x, p.v, p.eps, i_idx=il)
+    with abi.Kirin(p.n, p.eps, precision=precision) as k:
+        k.set_j_particles(p.m, x, p.v)
+        k.set_nn(True)
+        for groups, n_split in ((8, 40), (2, 200), (8, 1024)):
+            k.set_launch(groups, n_split)
+            assert_parity(k.forces(il), ref, precision, f"nn groups={groups} split={n_split}")
+            nn, r2 = k.get_nn()
+            _check_nn(x, il, nn, r2, precision)
+            assert nn[-2] == 39999 and nn[-1] == 3 and r2[-2] == 0.0 and r2[-1] == 0.0
+
+
 def test_single_particle_has_no_neighbour(kirin_lib):
     import torch
     dev = torch.device("cuda:0")
