@@ -181,6 +181,7 @@ class Kirin:
         self.n_max = int(n_max)
         self.n_j = 0
         self._pending = 0
+        self.stream = stream
 
     def _check(self, rc, what, ctx=True):
         if rc != KIRIN_OK:
@@ -213,6 +214,7 @@ class Kirin:
 
     def set_stream(self, stream):
         self._check(self.lib.kirin_set_stream(self.ctx, stream_handle(stream)), "kirin_set_stream")
+        self.stream = stream
 
     def set_launch(self, groups=0, n_split=0):
         self._check(self.lib.kirin_set_launch(self.ctx, int(groups), int(n_split)), "kirin_set_launch")

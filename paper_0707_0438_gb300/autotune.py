@@ -48,6 +48,48 @@ def _candidates(auto, ntiles, big):
     return sorted(cands)
 
 
+def _seconds_per_call(k: Kirin, call, reps: int, torch) -> float:
+    """Device time of one `call` (a force launch through the C ABI).
+
+    Short calls are replayed from a captured CUDA graph of many calls, so the
+    host's launch rate does not hide the difference between shapes; long ones
+    are timed directly."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    call()  # warm-up: buffers and kernel attributes are set up outside any capture
+    ev[0].record()
+    call()
+    ev[1].record()
+    torch.cuda.synchronize()
+    t1 = ev[0].elapsed_time(ev[1]) / 1e3
+    if t1 > 5e-3:
+        r = max(1, reps)
+        ev[0].record()
+        for _ in range(r):
+            call()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3 / r
+    r = int(min(100, max(reps, 2e-3 / max(t1, 1e-7))))
+    orig = k.stream
+    side = torch.cuda.Stream()
+    k.set_stream(side.cuda_stream)
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            for _ in range(r):
+                call()
+        with torch.cuda.stream(side):
+            g.replay()  # warm; finished before the timed replay, which would otherwise queue behind it
+            torch.cuda.synchronize()
+            ev[0].record()
+            g.replay()
+            ev[1].record()
+        torch.cuda.synchronize()
+    finally:
+        k.set_stream(orig)
+    return ev[0].elapsed_time(ev[1]) / 1e3 / r
+
+
 def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, device_name: str = "",
          cache: str | None = DEFAULT_CACHE, precision: str = "mixed"):
     """Time launch shapes for the particles already set in `k` (n_j of them) and install
@@ -82,20 +124,7 @@ def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, d
         best = None
         for g, s in cands:
             k.set_launch(g, s)
-            k.compute_forces_dev(il, acc, jerk, pot)  # warm-up
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            ev[0].record()
-            k.compute_forces_dev(il, acc, jerk, pot)
-            ev[1].record()
-            torch.cuda.synchronize()
-            # short calls: repeat until about 2 ms are timed
-            r = int(min(200, max(reps, 2e-3 / max(ev[0].elapsed_time(ev[1]) / 1e3, 1e-7))))
-            ev[0].record()
-            for _ in range(r):
-                k.compute_forces_dev(il, acc, jerk, pot)
-            ev[1].record()
-            torch.cuda.synchronize()
-            t = ev[0].elapsed_time(ev[1]) / 1e3 / r
+            t = _seconds_per_call(k, lambda: k.compute_forces_dev(il, acc, jerk, pot), reps, torch)
             if best is None or t < best[3]:
                 best = (n_i, g, s, t)
         table.append(best)

@@ -145,6 +145,10 @@ int ilog2(int g) { return g == 1 ? 0 : g == 2 ? 1 : g == 4 ? 2 : 3; }
 
 bool guard_on(const kirin_ctx *c) { return c->eps == 0.0 || c->r_min > 0.0; }
 
+// The j image the context's precision reads; packs write only that one.
+JMixed *img_m(const kirin_ctx *c) { return c->prec == KIRIN_MIXED ? c->jm : nullptr; }
+JF64 *img_d(const kirin_ctx *c) { return c->prec == KIRIN_MIXED ? nullptr : c->jd; }
+
 int ctas_per_sm(kirin_ctx *c, int prec, int mode, bool guard, int groups)
 {
     int &slot = c->occ[prec == KIRIN_MIXED][mode][guard][ilog2(groups)];
@@ -222,7 +226,7 @@ int ensure_images(kirin_ctx *c)
         return KIRIN_OK;
     const int64_t n_pad = round_up(std::max<int64_t>(c->n_j, 1), TILE_J);
     CK(c, launch_predict_pack((int)c->n_j, (int)n_pad, c->pred_t, c->pred_mode, c->bm, c->bx, c->bv,
-                              c->ba, c->bj, c->bt, c->xp, c->vp, c->jm, c->jd, c->d_err, c->stream));
+                              c->ba, c->bj, c->bt, c->xp, c->vp, img_m(c), img_d(c), c->d_err, c->stream));
     c->images_dirty = false;
     return KIRIN_OK;
 }
@@ -468,8 +472,8 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
                                   reinterpret_cast<unsigned long long *>(c->d_scal + 3), c->d_sel_counts, h_loop,
                                   h_branch, p.n_classes, p.class_max, &r->max_steps, &r->steps, &r->pairs,
                                   &r->t_last, c->d_err, n, cs));
-    CKG(launch_predict_pack(n, (int)n_pad, 0.0, 1, c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->xp, c->vp, c->jm,
-                            c->jd, c->d_err, cs, c->d_scal, c->d_count));
+    CKG(launch_predict_pack(n, (int)n_pad, 0.0, 1, c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->xp, c->vp,
+                            img_m(c), img_d(c), c->d_err, cs, c->d_scal, c->d_count));
     CKG(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cap_graph, &deps, nullptr, &ndeps));
     sp.type = cudaGraphNodeTypeConditional;
     sp.conditional.handle = h_branch;
@@ -700,6 +704,8 @@ int kirin_set_params(kirin_ctx *ctx, double eps, double G, double r_min, int32_t
     ctx->eps = eps;
     ctx->G = G;
     ctx->r_min = r_min;
+    if (prec != ctx->prec)
+        ctx->images_dirty = true;  // only the image of the old precision is current
     ctx->prec = prec;
     return KIRIN_OK;
 }
@@ -1212,7 +1218,7 @@ int kirin_accel_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x,
         return KIRIN_OK;
     DeviceGuard dg(ctx->device);
     const int64_t n_pad = round_up(n, TILE_J);
-    CK(ctx, launch_pack_xm((int)n, (int)n_pad, m, x, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
+    CK(ctx, launch_pack_xm((int)n, (int)n_pad, m, x, img_m(ctx), img_d(ctx), ctx->d_err, ctx->stream));
     ctx->images_dirty = true;  // the images no longer show the context's particles
     return run_force(ctx, n, nullptr, (int)n, MODE_ACC_POT, acc, nullptr, pot);
 }
@@ -1228,7 +1234,7 @@ int kirin_accel_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const do
     const int64_t n_pad = round_up(n, TILE_J);
     // images of (x, m) with g in the velocity slots
     CK(ctx, launch_predict_pack((int)n, (int)n_pad, 0.0, 0, m, x, g, nullptr, nullptr, nullptr, nullptr,
-                                nullptr, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
+                                nullptr, img_m(ctx), img_d(ctx), ctx->d_err, ctx->stream));
     ctx->images_dirty = true;
     return run_force(ctx, n, nullptr, (int)n, MODE_ADJOINT, nullptr, gx, gm);
 }
@@ -1247,7 +1253,7 @@ int kirin_leapfrog_dev(kirin_ctx *ctx, int64_t n, const double *m, double *x, do
     const int64_t n_pad = round_up(n, TILE_J);
     const double h = 0.5 * dt;
     auto accel = [&]() -> int {
-        CK(ctx, launch_pack_xm(nn, (int)n_pad, m, x, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
+        CK(ctx, launch_pack_xm(nn, (int)n_pad, m, x, img_m(ctx), img_d(ctx), ctx->d_err, ctx->stream));
         return run_force(ctx, n, nullptr, nn, MODE_ACC_POT, acc, nullptr, nullptr);
     };
     ctx->images_dirty = true;
@@ -1284,7 +1290,7 @@ int kirin_leapfrog_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const
     ctx->images_dirty = true;
     // lx += J(x)^T (c lv), lm += M(x)^T (c lv)
     auto adjoint_at = [&](const double *xk, double c) -> int {
-        CK(ctx, launch_pack_adjoint(nn, (int)n_pad, m, xk, lv, c, ctx->jm, ctx->jd, ctx->d_err, ctx->stream));
+        CK(ctx, launch_pack_adjoint(nn, (int)n_pad, m, xk, lv, c, img_m(ctx), img_d(ctx), ctx->d_err, ctx->stream));
         return run_force(ctx, n, nullptr, nn, MODE_ADJOINT, nullptr, lx, lm, 1);
     };
     for (int k = n_steps - 1; k >= 0; --k) {

@@ -13,6 +13,8 @@ namespace kirin {
 namespace {
 
 constexpr int AUX_THREADS = 256;
+constexpr int CORR_THREADS = 32;     // one warp per CTA: FP64-bound, spread over SMs
+constexpr int CORR_MAX_CTAS = 1024;  // the corrector loops beyond this
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
@@ -119,7 +121,7 @@ __global__ void k_predict_pack(int n, int n_pad, double t, int predict, const do
     double X[3], V[3];
     if (predict) {
         const double dt = t - t0[k];
-        const double dt2 = dt * dt / 2.0, dt3 = dt * dt * dt / 6.0;
+        const double dt2 = dt * dt * 0.5, dt3 = dt2 * dt * (1.0 / 3.0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t o = 3 * (size_t)k + c;
@@ -386,52 +388,58 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *
 // Hermite corrector for the block (Sect. 3): a2, a3 from the two (a, jerk)
 // pairs, corrected x and v, and (update_dt) Aarseth's step on the
 // power-of-two ladder.
-__global__ void k_hermite_correct(int n_act, const int32_t *__restrict__ ilist, double t_next,
-                                  double eta, double dt_min, double dt_max, int update_dt,
-                                  const double *__restrict__ xp, const double *__restrict__ vp,
-                                  const double *__restrict__ acc, const double *__restrict__ jerk,
-                                  double *bx, double *bv, double *ba, double *bj, double *bt, double *bdt,
-                                  const int32_t *n_dev, const double *t_dev)
+// FP64 is the scarce pipe on this part (about 1 TFLOP/s), so the corrector
+// spends it sparingly: one reciprocal of dt instead of a divide per term, the
+// powers of dt shared by the three components, and small CTAs looping over
+// the block so that even a short block is spread over many SMs.
+__global__ void __launch_bounds__(CORR_THREADS) k_hermite_correct(
+    int n_act, const int32_t *__restrict__ ilist, double t_next, double eta, double dt_min, double dt_max,
+    int update_dt, const double *__restrict__ xp, const double *__restrict__ vp, const double *__restrict__ acc,
+    const double *__restrict__ jerk, double *bx, double *bv, double *ba, double *bj, double *bt, double *bdt,
+    const int32_t *n_dev, const double *t_dev)
 {
     if (n_dev)
         n_act = *n_dev;
     if (t_dev)
         t_next = *t_dev;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_act)
-        return;
-    const size_t i = ilist ? (size_t)ilist[k] : (size_t)k;
-    const double dt = t_next - bt[i];
-    double a2[3], a3[3], a1[3], j1[3], a2e[3];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_act; k += gridDim.x * blockDim.x) {
+        const size_t i = ilist ? (size_t)ilist[k] : (size_t)k;
+        const double dt = t_next - bt[i];
+        const double idt = 1.0 / dt;
+        const double idt2 = idt * idt, idt3 = idt2 * idt;
+        const double dt2 = dt * dt, dt3 = dt2 * dt, dt4 = dt2 * dt2;
+        const double c3 = dt3 * (1.0 / 6.0), c4 = dt4 * (1.0 / 24.0), c5 = dt4 * dt * (1.0 / 120.0);
+        double a1[3], j1[3], a2e[3], a3[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
-        a1[c] = acc[3 * (size_t)k + c];
-        j1[c] = jerk[3 * (size_t)k + c];
-        a2[c] = (-6.0 * (a0 - a1[c]) - dt * (4.0 * j0 + 2.0 * j1[c])) / (dt * dt);
-        a3[c] = (12.0 * (a0 - a1[c]) + 6.0 * dt * (j0 + j1[c])) / (dt * dt * dt);
-        const double dt4 = dt * dt * dt * dt;
-        bx[3 * i + c] = xp[3 * i + c] + a2[c] * dt4 / 24.0 + a3[c] * dt4 * dt / 120.0;
-        bv[3 * i + c] = vp[3 * i + c] + a2[c] * dt * dt * dt / 6.0 + a3[c] * dt4 / 24.0;
-        ba[3 * i + c] = a1[c];
-        bj[3 * i + c] = j1[c];
-        a2e[c] = a2[c] + dt * a3[c];
-    }
-    bt[i] = t_next;
-    if (update_dt) {
-        const double na = norm3(a1), nj = norm3(j1), n2 = norm3(a2e), n3 = norm3(a3);
-        const double raw = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
-        double q;
-        if (raw < dt) {
-            q = dt;
-            while (q > raw && q > dt_min)
-                q *= 0.5;
-        } else if (raw >= 2.0 * dt && 2.0 * dt <= dt_max && fmod(t_next, 2.0 * dt) == 0.0) {
-            q = 2.0 * dt;
-        } else {
-            q = dt;
+        for (int c = 0; c < 3; ++c) {
+            const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
+            a1[c] = acc[3 * (size_t)k + c];
+            j1[c] = jerk[3 * (size_t)k + c];
+            const double da = a0 - a1[c];
+            const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1[c])) * idt2;
+            a3[c] = (12.0 * da + 6.0 * dt * (j0 + j1[c])) * idt3;
+            bx[3 * i + c] = xp[3 * i + c] + a2 * c4 + a3[c] * c5;
+            bv[3 * i + c] = vp[3 * i + c] + a2 * c3 + a3[c] * c4;
+            ba[3 * i + c] = a1[c];
+            bj[3 * i + c] = j1[c];
+            a2e[c] = a2 + dt * a3[c];
         }
-        bdt[i] = fmin(fmax(q, dt_min), dt_max);
+        bt[i] = t_next;
+        if (update_dt) {
+            const double na = norm3(a1), nj = norm3(j1), n2 = norm3(a2e), n3 = norm3(a3);
+            const double raw = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
+            double q;
+            if (raw < dt) {
+                q = dt;
+                while (q > raw && q > dt_min)
+                    q *= 0.5;
+            } else if (raw >= 2.0 * dt && 2.0 * dt <= dt_max && fmod(t_next, 2.0 * dt) == 0.0) {
+                q = 2.0 * dt;
+            } else {
+                q = dt;
+            }
+            bdt[i] = fmin(fmax(q, dt_min), dt_max);
+        }
     }
 }
 
@@ -633,7 +641,7 @@ cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_nex
 {
     if (n_act == 0)
         return cudaSuccess;
-    k_hermite_correct<<<blocks_for(n_act, AUX_THREADS), AUX_THREADS, 0, st>>>(
+    k_hermite_correct<<<std::min(blocks_for(n_act, CORR_THREADS), CORR_MAX_CTAS), CORR_THREADS, 0, st>>>(
         n_act, ilist, t_next, eta, dt_min, dt_max, update_dt, xp, vp, acc, jerk, bx, bv, ba, bj, bt,
         bdt, n_dev, t_dev);
     return cudaGetLastError();
