@@ -207,17 +207,19 @@ int kirin_hermite_block_step(kirin_ctx *ctx, double t_end, double *t_now, int64_
  * over them (either may be NULL).
  *
  * With the device loop on (the default, see kirin_set_device_loop) the whole
- * run is one CUDA graph launch: a conditional WHILE node repeats block
- * selection, prediction, the force evaluation (a SWITCH node picks one of a
- * ladder of launches by block size) and correction, and the selection kernel
- * decides on the device whether another step follows.  The host then waits
+ * run is one CUDA graph launch: a conditional WHILE node repeats two step
+ * kernels (correction of the previous block and the minimum of t_i + dt_i;
+ * selection of the next block and prediction of all j) and the force
+ * evaluation (a SWITCH node picks one of a ladder of launches by block size);
+ * the step kernels decide on the device whether another step follows.  The host then waits
  * once per call instead of once per block step.  The graph is built on the
  * first call and rebuilt only when n_j, the parameters or the launch shapes
  * change.  Results are those of the same steps taken one kirin_hermite_block_step
  * at a time, bit for bit when both use the same launch shape
  * (kirin_set_launch); the automatic shapes of the two paths can differ, and
- * so can the summation order.  Errors: KIRIN_ESTATE before kirin_hermite_init;
- * KIRIN_ECUDA if the graph cannot be built or launched. */
+ * so can the summation order.  Errors: KIRIN_ESTATE before kirin_hermite_init,
+ * or when a block time does not advance (t + dt rounds to t in FP64; the run
+ * stops there); KIRIN_ECUDA if the graph cannot be built or launched. */
 int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *n_steps,
                       double *n_pairs);
 

@@ -19,17 +19,9 @@
 #include <new>
 
 #include "kirin_internal.cuh"
+#include "loop_internal.cuh"
 
 using namespace kirin;
-
-// Parameters and counters of a device-driven run, one copy on each side.
-struct RunCounters {
-    double t_end;
-    long long max_steps;  // 0 = unbounded
-    long long steps;      // block steps taken
-    double pairs;         // sum over the steps of n_active * n_j
-    double t_last;        // time of the last block stepped
-};
 
 struct kirin_ctx {
     int device = 0;
@@ -80,8 +72,10 @@ struct kirin_ctx {
     bool device_loop = true;
     cudaGraphExec_t run_exec = nullptr;
     uint64_t run_key = 0;
-    RunCounters *d_run = nullptr;  // run parameters and counters (device)
-    RunCounters *h_run = nullptr;  // pinned mirror
+    RunState *d_run = nullptr;      // run parameters, counters and barrier words (device)
+    RunState *h_run = nullptr;      // pinned mirror
+    int32_t *d_step_counts = nullptr;  // per-CTA list offsets and counts of the step kernels
+    int step_ctas = 0;
 
     // launch-shape override (0 = automatic), tuned table and occupancy cache
     int fix_groups = 0, fix_split = 0;
@@ -333,7 +327,7 @@ void free_all(kirin_ctx *c)
 {
     void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
                     c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
-                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2};
+                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -367,12 +361,16 @@ int check_params(double eps, double G, double r_min, int prec)
 
 // ---- device-driven block steps ---------------------------------------------
 //
-// The graph:  WHILE(loop) { reset-min; select; predict; SWITCH(branch)
-// { force launch for block-size class 0 | 1 | ... }; correct }.  The select
-// kernel sets both conditions from the block it finds.  Each class c covers
-// block sizes (class_max[c-1], class_max[c]]; its force launch has a grid for
-// class_max[c] and the shape chosen for a block of about 0.7 class_max[c], and
-// its CTAs beyond the actual block return at once.
+// The graph:  WHILE(loop) { correct + minimum; select + predict; SWITCH(branch)
+// { force launch for block-size class 0 | 1 | ... } }.  The step kernels
+// correct the block forced in the previous iteration, select and predict the
+// next one and set both conditions; the iteration that selects nothing ends
+// the loop, so every block of a run is corrected before the graph returns.
+// (Two plain kernels: a dependent kernel node costs about 0.8 us on this
+// part, a grid-wide barrier inside one kernel about 2.4 us.)  Each
+// class c covers block sizes (class_max[c-1], class_max[c]]; its force launch
+// has a grid for class_max[c] and the shape chosen for a block of about
+// 0.7 class_max[c], and its CTAs beyond the actual block return at once.
 
 struct RunPlan {
     int n_classes = 0;
@@ -427,7 +425,7 @@ uint64_t run_key(const kirin_ctx *c, const RunPlan &p)
     return h | 1;  // never 0, the "no graph" key
 }
 
-// Capture onto the body graph `g` with stream cs.
+// Capture onto the body graph with stream cs.
 #define CKG(call)                                                                              \
     do {                                                                                       \
         cudaError_t e_ = (call);                                                               \
@@ -450,9 +448,8 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
     cudaStreamCaptureStatus status;
+    StepArgs a{};
     const int n = (int)c->n_j;
-    const int64_t n_pad = round_up(std::max<int64_t>(n, 1), TILE_J);
-    RunCounters *r = c->d_run;
 
     CKG(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     CKG(cudaGraphCreate(&top, 0));
@@ -465,15 +462,42 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     body = wp.conditional.phGraph_out[0];
     CKG(cudaGraphConditionalHandleCreate(&h_branch, body, 0, cudaGraphCondAssignDefault));
 
-    // loop body: select, predict, SWITCH, correct
+    a.n = n;
+    a.n_pad = (int)round_up(std::max<int64_t>(n, 1), TILE_J);
+    a.bm = c->bm;
+    a.bx = c->bx;
+    a.bv = c->bv;
+    a.ba = c->ba;
+    a.bj = c->bj;
+    a.bt = c->bt;
+    a.bdt = c->bdt;
+    a.xp = c->xp;
+    a.vp = c->vp;
+    a.jm = img_m(c);
+    a.jd = img_d(c);
+    a.acc = c->d_acc;
+    a.jerk = c->d_jerk;
+    a.ilist = c->d_ilist;
+    a.eta = c->eta;
+    a.dt_min = c->dt_min;
+    a.dt_max = c->dt_max;
+    a.run = c->d_run;
+    a.count_out = c->d_count;
+    a.t_next_out = c->d_scal;
+    a.chunk_off = c->d_step_counts;
+    a.chunk_cnt = c->d_step_counts + c->step_ctas;
+    a.err = c->d_err;
+    a.loop = h_loop;
+    a.branch = h_branch;
+    a.n_classes = p.n_classes;
+    for (int q = 0; q < p.n_classes; ++q)
+        a.class_max[q] = p.class_max[q];
+    a.n_j = n;
+
+    // loop body: the two step kernels, then the SWITCH over force launches
     CKG(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     capturing = true;
-    CKG(launch_block_select_graph(n, c->bt, c->bdt, &r->t_end, c->d_ilist, c->d_scal, c->d_count,
-                                  reinterpret_cast<unsigned long long *>(c->d_scal + 3), c->d_sel_counts, h_loop,
-                                  h_branch, p.n_classes, p.class_max, &r->max_steps, &r->steps, &r->pairs,
-                                  &r->t_last, c->d_err, n, cs));
-    CKG(launch_predict_pack(n, (int)n_pad, 0.0, 1, c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->xp, c->vp,
-                            img_m(c), img_d(c), c->d_err, cs, c->d_scal, c->d_count));
+    CKG(launch_block_step(a, c->step_ctas, cs));
     CKG(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cap_graph, &deps, nullptr, &ndeps));
     sp.type = cudaGraphNodeTypeConditional;
     sp.conditional.handle = h_branch;
@@ -481,8 +505,6 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     sp.conditional.size = (unsigned)p.n_classes;
     CKG(cudaGraphAddNode(&snode, cap_graph, deps, nullptr, ndeps, &sp));
     CKG(cudaStreamUpdateCaptureDependencies(cs, &snode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    CKG(launch_hermite_correct(n, c->d_ilist, 0.0, c->eta, c->dt_min, c->dt_max, 1, c->xp, c->vp, c->d_acc,
-                               c->d_jerk, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, cs, c->d_count, c->d_scal));
     capturing = false;
     CKG(cudaStreamEndCapture(cs, &cap_graph));
 
@@ -541,14 +563,18 @@ int hermite_run_device(kirin_ctx *c, double t_end, int64_t max_steps, int64_t *n
     }
     // the pinned mirror may still be the source or target of the last run's copies
     CK(c, cudaStreamSynchronize(c->stream));
-    *c->h_run = RunCounters{t_end, (long long)std::max<int64_t>(max_steps, 0), 0, 0.0, 0.0};
-    CK(c, cudaMemcpyAsync(c->d_run, c->h_run, sizeof(RunCounters), cudaMemcpyHostToDevice, c->stream));
+    RunState init{};
+    init.t_end = t_end;
+    init.max_steps = (long long)std::max<int64_t>(max_steps, 0);
+    init.minw[0] = init.minw[1] = ~0ull;
+    *c->h_run = init;
+    CK(c, cudaMemcpyAsync(c->d_run, c->h_run, sizeof(RunState), cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaGraphLaunch(c->run_exec, c->stream));
-    CK(c, cudaMemcpyAsync(c->h_run, c->d_run, sizeof(RunCounters), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(c->h_run, c->d_run, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream));
     rc = read_device_errors(c);  // synchronises the stream
     if (rc)
         return rc;
-    const RunCounters out = *c->h_run;
+    const RunState out = *c->h_run;
     if (n_steps)
         *n_steps = out.steps;
     if (n_pairs)
@@ -654,9 +680,11 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
         ok = false;
     if (ok && cudaMallocHost((void **)&c->h_err, sizeof(unsigned)) != cudaSuccess)
         ok = false;
-    dalloc((void **)&c->d_run, sizeof(RunCounters));
-    if (ok && cudaMallocHost((void **)&c->h_run, sizeof(RunCounters)) != cudaSuccess)
+    dalloc((void **)&c->d_run, sizeof(RunState));
+    if (ok && cudaMallocHost((void **)&c->h_run, sizeof(RunState)) != cudaSuccess)
         ok = false;
+    c->step_ctas = std::max(c->nsm, 1) * STEP_CTAS_PER_SM;
+    dalloc((void **)&c->d_step_counts, 2 * (size_t)c->step_ctas * sizeof(int32_t));
     if (ok && cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream) != cudaSuccess)
         ok = false;
     if (ok && cudaMemsetAsync(c->bt, 0, n * sizeof(double), c->stream) != cudaSuccess)
@@ -1099,7 +1127,7 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
     if (ctx->device_loop)
         return hermite_run_device(ctx, t_end, max_steps, n_steps, n_pairs);
     int64_t steps = 0;
-    double pairs = 0.0;
+    double pairs = 0.0, t_last = 0.0;
     while (max_steps <= 0 || steps < max_steps) {
         double t_now = 0;
         int64_t n_act = 0;
@@ -1108,6 +1136,9 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
             return rc;
         if (n_act == 0)
             break;
+        if (steps > 0 && !(t_now > t_last))
+            return set_msg(ctx, KIRIN_ESTATE, "block time stopped advancing (t + dt == t in FP64)");
+        t_last = t_now;
         ++steps;
         pairs += (double)n_act * (double)ctx->n_j;
     }

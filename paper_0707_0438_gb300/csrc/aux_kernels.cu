@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "kirin_internal.cuh"
+#include "loop_internal.cuh"
 #include "tma.cuh"
 
 namespace kirin {
@@ -100,39 +101,33 @@ __device__ __forceinline__ void write_images(int k, double X, double Y, double Z
 }
 
 // Predictor x_p = x + v dt + a dt^2/2 + jerk dt^3/6, v_p = v + a dt + jerk dt^2/2
-// (dt = t - t0), then the j images; records [n, n_pad) are zero-mass padding.
-__global__ void k_predict_pack(int n, int n_pad, double t, int predict, const double *__restrict__ m,
-                               const double *__restrict__ x, const double *__restrict__ v,
-                               const double *__restrict__ a, const double *__restrict__ jk,
-                               const double *__restrict__ t0, double *xp, double *vp, JMixed *jm,
-                               JF64 *jd, unsigned *err, const double *t_dev, const int32_t *count_dev)
+// (dt = t - t0) of record k, then its j images; records [n, n_pad) are
+// zero-mass padding.  Loads bypass L1: inside the fused step kernel other
+// CTAs have just corrected some of these particles.
+__device__ __forceinline__ void predict_one(int k, int n, double t, int predict, const double *m, const double *x,
+                                            const double *v, const double *a, const double *jk, const double *t0,
+                                            double *xp, double *vp, JMixed *jm, JF64 *jd, unsigned *err)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_pad)
-        return;
-    if (count_dev && *count_dev == 0)
-        return;  // device-driven loop: no block this iteration
-    if (t_dev)
-        t = *t_dev;
     if (k >= n) {
         write_images(k, PAD_POS, PAD_POS, PAD_POS, 0.0, 0.0, 0.0, 0.0, jm, jd);
         return;
     }
     double X[3], V[3];
     if (predict) {
-        const double dt = t - t0[k];
+        const double dt = t - __ldcg(t0 + k);
         const double dt2 = dt * dt * 0.5, dt3 = dt2 * dt * (1.0 / 3.0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t o = 3 * (size_t)k + c;
-            X[c] = x[o] + v[o] * dt + a[o] * dt2 + jk[o] * dt3;
-            V[c] = v[o] + a[o] * dt + jk[o] * dt2;
+            const double vo = __ldcg(v + o), ao = __ldcg(a + o);
+            X[c] = __ldcg(x + o) + vo * dt + ao * dt2 + __ldcg(jk + o) * dt3;
+            V[c] = vo + ao * dt + __ldcg(jk + o) * dt2;
         }
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            X[c] = x[3 * (size_t)k + c];
-            V[c] = v[3 * (size_t)k + c];
+            X[c] = __ldcg(x + 3 * (size_t)k + c);
+            V[c] = __ldcg(v + 3 * (size_t)k + c);
         }
     }
     if (xp) {
@@ -142,10 +137,22 @@ __global__ void k_predict_pack(int n, int n_pad, double t, int predict, const do
             vp[3 * (size_t)k + c] = V[c];
         }
     }
+    const double M = m[k];
     if (!(isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2]) && isfinite(V[0]) && isfinite(V[1]) &&
-          isfinite(V[2]) && isfinite(m[k])))
+          isfinite(V[2]) && isfinite(M)))
         atomicOr(err, ERR_NONFINITE);
-    write_images(k, X[0], X[1], X[2], m[k], V[0], V[1], V[2], jm, jd);
+    write_images(k, X[0], X[1], X[2], M, V[0], V[1], V[2], jm, jd);
+}
+
+__global__ void k_predict_pack(int n, int n_pad, double t, int predict, const double *__restrict__ m,
+                               const double *__restrict__ x, const double *__restrict__ v,
+                               const double *__restrict__ a, const double *__restrict__ jk,
+                               const double *__restrict__ t0, double *xp, double *vp, JMixed *jm,
+                               JF64 *jd, unsigned *err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_pad)
+        predict_one(k, n, t, predict, m, x, v, a, jk, t0, xp, vp, jm, jd, err);
 }
 
 // Images from (m, x) only (velocities zero), for acceleration-only clients.
@@ -292,39 +299,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_count(int n, const double *
         counts[blockIdx.x] = total;
 }
 
-// Loop control of a device-driven block-step run (graph conditional nodes):
-// the size classes of the force branches and the run's counters.
-struct SelGraph {
-    cudaGraphConditionalHandle loop;    // WHILE: another block step?
-    cudaGraphConditionalHandle branch;  // SWITCH: which force launch (n_classes = none)
-    int n_classes;
-    int32_t class_max[MAX_SEL_CLASSES]; // ascending upper bounds of the block size
-    const double *t_end;                // end time of the run (device, set before each launch)
-    const long long *max_steps;         // step limit of the run, 0 = unbounded (device)
-    long long *steps;                   // device counters of the run
-    double *pairs;
-    double *t_last;                     // time of the last block stepped
-    unsigned *err;
-    int n_j;
-};
-
-// Start value of the atomic minimum, as a kernel node (the conditional body
-// of a graph then holds kernel nodes only).
-__global__ void k_reset_min(unsigned long long *minw) { *minw = ~0ull; }
-
-template <bool GRAPH>
 __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *__restrict__ bt,
                                                            const double *__restrict__ bdt,
                                                            const unsigned long long *minw,
                                                            const int32_t *__restrict__ counts, double t_end,
                                                            int32_t *ilist, double *t_next_out,
-                                                           int32_t *count_out, SelGraph gctl)
+                                                           int32_t *count_out)
 {
     __shared__ int warp_tot[SEL_THREADS / 32];
     __shared__ int red[SEL_THREADS];
     const double tn = __longlong_as_double((long long)*minw);
-    if (GRAPH)
-        t_end = *gctl.t_end;
     const bool due = tn <= t_end;
     // offset of this CTA: sum of the counts of the CTAs before it
     int part = 0;
@@ -359,87 +343,235 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *
         __syncthreads();
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        int count = due ? base : 0;
-        if (GRAPH && count > 0 && *gctl.steps > 0 && !(tn > *gctl.t_last)) {
-            atomicOr(gctl.err, ERR_STALL);  // no progress: stop rather than repeat the block forever
-            count = 0;
-        }
-        *count_out = count;
+        *count_out = due ? base : 0;
         *t_next_out = tn;
-        if (GRAPH) {
-            unsigned cls = (unsigned)gctl.n_classes;  // no branch when the block is empty
-            if (count > 0) {
-                cls = (unsigned)gctl.n_classes - 1;
-                for (int c = gctl.n_classes - 1; c >= 0; --c)
-                    if (count <= gctl.class_max[c])
-                        cls = (unsigned)c;
-                *gctl.steps += 1;
-                *gctl.pairs += (double)count * (double)gctl.n_j;
-                *gctl.t_last = tn;
-            }
-            cudaGraphSetConditional(gctl.branch, cls);
-            const long long lim = *gctl.max_steps;
-            const bool more = count > 0 && (lim <= 0 || *gctl.steps < lim);
-            cudaGraphSetConditional(gctl.loop, more ? 1u : 0u);
-        }
     }
 }
 
 // Hermite corrector for the block (Sect. 3): a2, a3 from the two (a, jerk)
 // pairs, corrected x and v, and (update_dt) Aarseth's step on the
 // power-of-two ladder.
-// FP64 is the scarce pipe on this part (about 1 TFLOP/s), so the corrector
-// spends it sparingly: one reciprocal of dt instead of a divide per term, the
-// powers of dt shared by the three components, and small CTAs looping over
-// the block so that even a short block is spread over many SMs.
+// Hermite corrector of block member k (particle ilist[k], or k) at t_next
+// from its new a, jerk (acc/jerk row k), and with update_dt its new block
+// step: Aarseth's criterion quantised to a power of two that may shrink
+// freely and double only where t_next is a multiple of the doubled step.
+// FP64 is the scarce pipe on this part (about 1 TFLOP/s), so this spends it
+// sparingly: one reciprocal of dt instead of a divide per term, and the
+// powers of dt shared by the three components.
+__device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double t_next, double eta, double dt_min,
+                                            double dt_max, int update_dt, const double *xp, const double *vp,
+                                            const double *acc, const double *jerk, double *bx, double *bv,
+                                            double *ba, double *bj, double *bt, double *bdt)
+{
+    const size_t i = ilist ? (size_t)ilist[k] : (size_t)k;
+    const double dt = t_next - bt[i];
+    const double idt = 1.0 / dt;
+    const double idt2 = idt * idt, idt3 = idt2 * idt;
+    const double dt2 = dt * dt, dt3 = dt2 * dt, dt4 = dt2 * dt2;
+    const double c3 = dt3 * (1.0 / 6.0), c4 = dt4 * (1.0 / 24.0), c5 = dt4 * dt * (1.0 / 120.0);
+    double a1[3], j1[3], a2e[3], a3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
+        a1[c] = acc[3 * (size_t)k + c];
+        j1[c] = jerk[3 * (size_t)k + c];
+        const double da = a0 - a1[c];
+        const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1[c])) * idt2;
+        a3[c] = (12.0 * da + 6.0 * dt * (j0 + j1[c])) * idt3;
+        bx[3 * i + c] = xp[3 * i + c] + a2 * c4 + a3[c] * c5;
+        bv[3 * i + c] = vp[3 * i + c] + a2 * c3 + a3[c] * c4;
+        ba[3 * i + c] = a1[c];
+        bj[3 * i + c] = j1[c];
+        a2e[c] = a2 + dt * a3[c];
+    }
+    bt[i] = t_next;
+    if (update_dt) {
+        const double na = norm3(a1), nj = norm3(j1), n2 = norm3(a2e), n3 = norm3(a3);
+        const double raw = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
+        double q;
+        if (raw < dt) {
+            q = dt;
+            while (q > raw && q > dt_min)
+                q *= 0.5;
+        } else if (raw >= 2.0 * dt && 2.0 * dt <= dt_max && fmod(t_next, 2.0 * dt) == 0.0) {
+            q = 2.0 * dt;
+        } else {
+            q = dt;
+        }
+        bdt[i] = fmin(fmax(q, dt_min), dt_max);
+    }
+}
+
+// One warp per CTA, and member k on CTA k mod gridDim (lane k / gridDim):
+// a short block puts one member on each of many SMs, since an FP64 warp
+// instruction costs the same with one active lane as with 32.
 __global__ void __launch_bounds__(CORR_THREADS) k_hermite_correct(
     int n_act, const int32_t *__restrict__ ilist, double t_next, double eta, double dt_min, double dt_max,
     int update_dt, const double *__restrict__ xp, const double *__restrict__ vp, const double *__restrict__ acc,
-    const double *__restrict__ jerk, double *bx, double *bv, double *ba, double *bj, double *bt, double *bdt,
-    const int32_t *n_dev, const double *t_dev)
+    const double *__restrict__ jerk, double *bx, double *bv, double *ba, double *bj, double *bt, double *bdt)
 {
-    if (n_dev)
-        n_act = *n_dev;
-    if (t_dev)
-        t_next = *t_dev;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_act; k += gridDim.x * blockDim.x) {
-        const size_t i = ilist ? (size_t)ilist[k] : (size_t)k;
-        const double dt = t_next - bt[i];
-        const double idt = 1.0 / dt;
-        const double idt2 = idt * idt, idt3 = idt2 * idt;
-        const double dt2 = dt * dt, dt3 = dt2 * dt, dt4 = dt2 * dt2;
-        const double c3 = dt3 * (1.0 / 6.0), c4 = dt4 * (1.0 / 24.0), c5 = dt4 * dt * (1.0 / 120.0);
-        double a1[3], j1[3], a2e[3], a3[3];
+    for (long long k = blockIdx.x + (long long)threadIdx.x * gridDim.x; k < n_act;
+         k += (long long)CORR_THREADS * gridDim.x)
+        correct_one((int)k, ilist, t_next, eta, dt_min, dt_max, update_dt, xp, vp, acc, jerk, bx, bv, ba, bj, bt,
+                    bdt);
+}
+
+// ---- block step of the device-driven loop -------------------------------------
+
+constexpr int STEP_THREADS = 256;
+constexpr int STEP_WARPS = STEP_THREADS / 32;
+
+__device__ __forceinline__ unsigned long long cta_min_u64(unsigned long long v)
+{
+    __shared__ unsigned long long part[STEP_WARPS];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
-            a1[c] = acc[3 * (size_t)k + c];
-            j1[c] = jerk[3 * (size_t)k + c];
-            const double da = a0 - a1[c];
-            const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1[c])) * idt2;
-            a3[c] = (12.0 * da + 6.0 * dt * (j0 + j1[c])) * idt3;
-            bx[3 * i + c] = xp[3 * i + c] + a2 * c4 + a3[c] * c5;
-            bv[3 * i + c] = vp[3 * i + c] + a2 * c3 + a3[c] * c4;
-            ba[3 * i + c] = a1[c];
-            bj[3 * i + c] = j1[c];
-            a2e[c] = a2 + dt * a3[c];
+    for (int o = 16; o > 0; o >>= 1)
+        v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0)
+        part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < STEP_WARPS; ++w)
+            v = min(v, part[w]);
+    return v;  // valid in thread 0
+}
+
+__device__ __forceinline__ int cta_sum(int v)
+{
+    __shared__ int part[STEP_WARPS];
+    __shared__ int total;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0)
+        part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < STEP_WARPS; ++w)
+            t += part[w];
+        total = t;
+    }
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ void chunk_of(int n, int& c0, int& c1)
+{
+    const int chunk = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    c0 = min(n, (int)blockIdx.x * chunk);
+    c1 = min(n, c0 + chunk);
+}
+
+__global__ void __launch_bounds__(STEP_THREADS) k_step_correct(const StepArgs A)
+{
+    RunState *R = A.run;
+    const int par = (int)(R->steps & 1);
+    int c0, c1;
+    chunk_of(A.n, c0, c1);
+    if (R->pending > 0) {
+        // this CTA's members: one per warp first (an FP64 warp instruction costs
+        // the same with one active lane as with 32)
+        const int off = A.chunk_off[blockIdx.x], cnt = A.chunk_cnt[blockIdx.x];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int m = warp + lane * STEP_WARPS; m < cnt; m += STEP_THREADS)
+            correct_one(off + m, A.ilist, R->t_last, A.eta, A.dt_min, A.dt_max, 1, A.xp, A.vp, A.acc, A.jerk, A.bx,
+                        A.bv, A.ba, A.bj, A.bt, A.bdt);
+        __syncthreads();
+    }
+    unsigned long long mn = ~0ull;
+    for (int i = c0 + threadIdx.x; i < c1; i += STEP_THREADS)
+        mn = min(mn, (unsigned long long)__double_as_longlong(__ldcg(A.bt + i) + __ldcg(A.bdt + i)));
+    mn = cta_min_u64(mn);
+    if (threadIdx.x == 0) {
+        atomicMin(&R->minw[par], mn);
+        if (blockIdx.x == 0) {  // fresh words for the select kernel and the next step
+            R->minw[par ^ 1] = ~0ull;
+            R->list_count = 0;
+            R->done = 0u;
         }
-        bt[i] = t_next;
-        if (update_dt) {
-            const double na = norm3(a1), nj = norm3(j1), n2 = norm3(a2e), n3 = norm3(a3);
-            const double raw = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
-            double q;
-            if (raw < dt) {
-                q = dt;
-                while (q > raw && q > dt_min)
-                    q *= 0.5;
-            } else if (raw >= 2.0 * dt && 2.0 * dt <= dt_max && fmod(t_next, 2.0 * dt) == 0.0) {
-                q = 2.0 * dt;
-            } else {
-                q = dt;
+    }
+}
+
+__global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
+{
+    RunState *R = A.run;
+    const long long steps0 = R->steps;
+    const double tn = __longlong_as_double((long long)R->minw[steps0 & 1]);
+    const long long lim = R->max_steps;
+    bool due = tn <= R->t_end && (lim <= 0 || steps0 < lim);
+    const bool stall = due && steps0 > 0 && !(tn > R->t_last);
+    if (stall)
+        due = false;
+    if (!due) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (stall)
+                atomicOr(A.err, ERR_STALL);  // the block time stopped advancing: stop rather than loop forever
+            *A.count_out = 0;
+            R->pending = 0;
+            cudaGraphSetConditional(A.branch, (unsigned)A.n_classes);
+            cudaGraphSetConditional(A.loop, 0u);
+        }
+        return;
+    }
+    int c0, c1;
+    chunk_of(A.n, c0, c1);
+    for (int k = c0 + threadIdx.x; k < c1; k += STEP_THREADS)
+        predict_one(k, A.n, tn, 1, A.bm, A.bx, A.bv, A.ba, A.bj, A.bt, A.xp, A.vp, A.jm, A.jd, A.err);
+    for (int k = A.n + blockIdx.x * STEP_THREADS + threadIdx.x; k < A.n_pad; k += gridDim.x * STEP_THREADS)
+        predict_one(k, A.n, tn, 1, A.bm, A.bx, A.bv, A.ba, A.bj, A.bt, A.xp, A.vp, A.jm, A.jd, A.err);  // padding
+    int c = 0;
+    for (int i = c0 + threadIdx.x; i < c1; i += STEP_THREADS)
+        c += A.bt[i] + A.bdt[i] == tn;
+    const int cnt = cta_sum(c);
+    __shared__ int base_s;
+    if (threadIdx.x == 0) {
+        base_s = cnt ? atomicAdd(&R->list_count, cnt) : 0;
+        A.chunk_off[blockIdx.x] = base_s;
+        A.chunk_cnt[blockIdx.x] = cnt;
+    }
+    __syncthreads();
+    if (cnt) {
+        __shared__ int warp_tot[STEP_WARPS];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        int base = base_s;
+        for (int i0 = c0; i0 < c1; i0 += STEP_THREADS) {
+            const int i = i0 + threadIdx.x;
+            const bool flag = i < c1 && A.bt[i] + A.bdt[i] == tn;
+            const unsigned ballot = __ballot_sync(0xffffffffu, flag);
+            if (lane == 0)
+                warp_tot[warp] = __popc(ballot);
+            __syncthreads();
+            int ahead = 0, all = 0;
+#pragma unroll
+            for (int w = 0; w < STEP_WARPS; ++w) {
+                ahead += w < warp ? warp_tot[w] : 0;
+                all += warp_tot[w];
             }
-            bdt[i] = fmin(fmax(q, dt_min), dt_max);
+            if (flag)
+                A.ilist[base + ahead + __popc(ballot & ((1u << lane) - 1u))] = i;
+            base += all;
+            __syncthreads();
         }
+    }
+    // the last CTA to finish publishes the block
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(&R->done, 1u) == gridDim.x - 1) {
+        __threadfence();
+        const int count = atomicAdd(&R->list_count, 0);
+        unsigned cls = (unsigned)A.n_classes - 1;
+        for (int q = A.n_classes - 1; q >= 0; --q)
+            if (count <= A.class_max[q])
+                cls = (unsigned)q;
+        *A.count_out = count;
+        *A.t_next_out = tn;
+        R->steps = steps0 + 1;
+        R->pairs += (double)count * (double)A.n_j;
+        R->t_last = tn;
+        R->pending = count;
+        cudaGraphSetConditional(A.branch, cls);
+        cudaGraphSetConditional(A.loop, 1u);
     }
 }
 
@@ -537,13 +669,12 @@ cudaError_t launch_reduce_splits(const ForceArgs &a, cudaStream_t st)
 cudaError_t launch_predict_pack(int n, int n_pad, double t, int predict, const double *m,
                                 const double *x, const double *v, const double *a,
                                 const double *jk, const double *t0, double *xp, double *vp,
-                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st, const double *t_dev,
-                                const int32_t *count_dev)
+                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st)
 {
     if (n_pad == 0)
         return cudaSuccess;
     k_predict_pack<<<blocks_for(n_pad, AUX_THREADS), AUX_THREADS, 0, st>>>(
-        n, n_pad, t, predict, m, x, v, a, jk, t0, xp, vp, jm, jd, err, t_dev, count_dev);
+        n, n_pad, t, predict, m, x, v, a, jk, t0, xp, vp, jm, jd, err);
     return cudaGetLastError();
 }
 
@@ -597,53 +728,21 @@ cudaError_t launch_block_select(int n, const double *bt, const double *bdt, doub
         return e;
     k_sel_min<<<std::min(nblk * SEL_ITEMS, 1024), SEL_THREADS, 0, st>>>(n, bt, bdt, minw);
     k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts);
-    k_sel_write<false><<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, t_end, ilist, t_next_out, count_out,
-                                                     SelGraph{});
+    k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, t_end, ilist, t_next_out, count_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_select_graph(int n, const double *bt, const double *bdt, const double *t_end,
-                                      int32_t *ilist, double *t_next_out, int32_t *count_out,
-                                      unsigned long long *minw, int32_t *counts, cudaGraphConditionalHandle loop,
-                                      cudaGraphConditionalHandle branch, int n_classes, const int32_t *class_max,
-                                      const long long *max_steps, long long *steps, double *pairs,
-                                      double *t_last, unsigned *err, int n_j, cudaStream_t st)
-{
-    if (n_classes < 1 || n_classes > MAX_SEL_CLASSES)
-        return cudaErrorInvalidValue;
-    SelGraph g{};
-    g.loop = loop;
-    g.branch = branch;
-    g.n_classes = n_classes;
-    for (int c = 0; c < n_classes; ++c)
-        g.class_max[c] = class_max[c];
-    g.t_end = t_end;
-    g.max_steps = max_steps;
-    g.steps = steps;
-    g.pairs = pairs;
-    g.t_last = t_last;
-    g.err = err;
-    g.n_j = n_j;
-    const int nblk = blocks_for(n, SEL_PER_CTA);
-    k_reset_min<<<1, 1, 0, st>>>(minw);
-    k_sel_min<<<std::min(nblk * SEL_ITEMS, 1024), SEL_THREADS, 0, st>>>(n, bt, bdt, minw);
-    k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts);
-    k_sel_write<true><<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, 0.0, ilist, t_next_out, count_out, g);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_next, double eta,
                                    double dt_min, double dt_max, int update_dt,
                                    const double *xp, const double *vp, const double *acc,
                                    const double *jerk, double *bx, double *bv, double *ba,
-                                   double *bj, double *bt, double *bdt, cudaStream_t st, const int32_t *n_dev,
-                                   const double *t_dev)
+                                   double *bj, double *bt, double *bdt, cudaStream_t st)
 {
     if (n_act == 0)
         return cudaSuccess;
-    k_hermite_correct<<<std::min(blocks_for(n_act, CORR_THREADS), CORR_MAX_CTAS), CORR_THREADS, 0, st>>>(
-        n_act, ilist, t_next, eta, dt_min, dt_max, update_dt, xp, vp, acc, jerk, bx, bv, ba, bj, bt,
-        bdt, n_dev, t_dev);
+    k_hermite_correct<<<std::min(n_act, CORR_MAX_CTAS), CORR_THREADS, 0, st>>>(
+        n_act, ilist, t_next, eta, dt_min, dt_max, update_dt, xp, vp, acc, jerk, bx, bv, ba, bj, bt, bdt);
     return cudaGetLastError();
 }
 
@@ -692,6 +791,13 @@ namespace kirin {
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *err, cudaStream_t st)
 {
     k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_step(const StepArgs &a, int ctas, cudaStream_t st)
+{
+    k_step_correct<<<ctas, STEP_THREADS, 0, st>>>(a);
+    k_step_select<<<ctas, STEP_THREADS, 0, st>>>(a);
     return cudaGetLastError();
 }
 

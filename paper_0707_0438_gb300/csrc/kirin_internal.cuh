@@ -145,13 +145,10 @@ int force_fp64_ctas_per_sm(int groups, int mode);
 
 // aux_kernels.cu
 cudaError_t launch_reduce_splits(const ForceArgs &a, cudaStream_t st);
-// t_dev / count_dev (optional): take t from device memory, and do nothing when
-// *count_dev == 0 (device-driven loops).
 cudaError_t launch_predict_pack(int n, int n_pad, double t, int predict, const double *m,
                                 const double *x, const double *v, const double *a,
                                 const double *jk, const double *t0, double *xp, double *vp,
-                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st,
-                                const double *t_dev = nullptr, const int32_t *count_dev = nullptr);
+                                JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st);
 cudaError_t launch_pack_xm(int n, int n_pad, const double *m, const double *x, JMixed *jm,
                            JF64 *jd, unsigned *err, cudaStream_t st);
 cudaError_t launch_scatter_state(int first, int n, const double *m, const double *x,
@@ -168,29 +165,11 @@ cudaError_t launch_hermite_init(int n, double t, const double *acc, const double
 cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end, int32_t *ilist,
                                 double *t_next_out, int32_t *count_out, unsigned long long *minw,
                                 int32_t *counts, cudaStream_t st);
-// n_dev / t_dev (optional): block size and time from device memory; the grid
-// must then cover the largest possible block.
 cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_next, double eta,
                                    double dt_min, double dt_max, int update_dt,
                                    const double *xp, const double *vp, const double *acc,
                                    const double *jerk, double *bx, double *bv, double *ba,
-                                   double *bj, double *bt, double *bdt, cudaStream_t st,
-                                   const int32_t *n_dev = nullptr, const double *t_dev = nullptr);
-// Block selection inside a graph: also picks the force branch (SWITCH) by the
-// block size (first class_max[c] >= count; n_classes when the block is empty),
-// counts steps and pairs, records the time of the block, and sets the WHILE
-// condition (more blocks due and fewer than max_steps taken).  A block time
-// that is not later than the previous one ends the loop with ERR_STALL
-// instead of stepping, so the loop always terminates.
-// t_end and max_steps are read from device memory, so one instantiated graph
-// serves runs to any end time.
-constexpr int MAX_SEL_CLASSES = 16;
-cudaError_t launch_block_select_graph(int n, const double *bt, const double *bdt, const double *t_end,
-                                      int32_t *ilist, double *t_next_out, int32_t *count_out,
-                                      unsigned long long *minw, int32_t *counts, cudaGraphConditionalHandle loop,
-                                      cudaGraphConditionalHandle branch, int n_classes, const int32_t *class_max,
-                                      const long long *max_steps, long long *steps, double *pairs,
-                                      double *t_last, unsigned *err, int n_j, cudaStream_t st);
+                                   double *bj, double *bt, double *bdt, cudaStream_t st);
 cudaError_t launch_lf_kick_drift(int n, double h, double dt, const double *a, double *v, double *x,
                                  double *hist, cudaStream_t st);
 cudaError_t launch_axpy(int n, double alpha, const double *x, double *y, cudaStream_t st);

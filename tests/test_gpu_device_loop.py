@@ -103,3 +103,20 @@ def test_device_loop_automatic_shapes_mixed(kirin_lib):
     scale = np.abs(p.x).max()
     assert np.abs(dev[1]["x"] - host[1]["x"]).max() <= 1e-9 * scale
     assert dev[2] == pytest.approx(host[2], rel=1e-9)
+
+
+@pytest.mark.parametrize("device_loop", [True, False])
+def test_block_time_that_stops_advancing_is_an_error(kirin_lib, device_loop):
+    """At t = 2^60 a step of 2^-20 rounds away (t + dt == t in FP64): both loops stop
+    with an error instead of repeating the same block forever."""
+    p = workloads.plummer(256, 1002, eps=1e-3)
+    with abi.Kirin(p.n, p.eps, precision="fp64") as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        st = k.get_state()
+        st["t"][:] = 2.0 ** 60
+        st["dt"][:] = 2.0 ** -20
+        k.set_state(p.m, st, dt_min=2.0 ** -20, dt_max=2.0 ** -3)
+        k.set_device_loop(device_loop)
+        with pytest.raises(abi.KirinError):
+            k.hermite_run(2.0 ** 60 + 2.0 ** 10)
