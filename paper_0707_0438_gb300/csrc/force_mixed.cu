@@ -57,9 +57,9 @@ constexpr int FLUSH_J = KIRIN_FLUSH_J;
 constexpr int FLUSH_J_ADJOINT = 64;
 constexpr int MIX_UNROLL = KIRIN_MIX_UNROLL;
 
-__device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, double val)
+__device__ __forceinline__ void write_out(const ForceArgs &A, int n_i, int q, int k, double val)
 {
-    if (k >= A.n_i)
+    if (k >= n_i)
         return;
     if (A.n_split > 1)
         A.partial[((size_t)blockIdx.y * A.nq + q) * A.n_i_pad + k] = val;
@@ -68,9 +68,9 @@ __device__ __forceinline__ void write_out(const ForceArgs &A, int q, int k, doub
 }
 
 // Nearest-neighbour result of slot k: to the split partials, or final.
-__device__ __forceinline__ void write_nn(const ForceArgs &A, int k, double r2, double j)
+__device__ __forceinline__ void write_nn(const ForceArgs &A, int n_i, int k, double r2, double j)
 {
-    if (k >= A.n_i)
+    if (k >= n_i)
         return;
     if (A.n_split > 1) {
         A.partial[((size_t)blockIdx.y * A.nq + 7) * A.n_i_pad + k] = r2;
@@ -87,12 +87,12 @@ constexpr size_t MIX_RING_BYTES = (size_t)STAGES * TILE_J * sizeof(JMixed);
 constexpr size_t MIX_RED_BYTES = (size_t)9 * MIX_I_PER_THREAD * FORCE_THREADS * sizeof(double);
 constexpr size_t MIX_SMEM_BYTES = MIX_RING_BYTES > MIX_RED_BYTES ? MIX_RING_BYTES : MIX_RED_BYTES;
 
-template <int GROUPS, bool GUARD, int MODE>
-__global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(const ForceArgs Ain)
+// DEVN: the block size is read from A.n_i_dev (device-driven loops); the grid
+// then covers an upper bound and the CTAs beyond the block return at once.
+template <int GROUPS, bool GUARD, int MODE, bool DEVN>
+__global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(const ForceArgs A)
 {
-    ForceArgs A = Ain;
-    if (Ain.n_i_dev)
-        A.n_i = *Ain.n_i_dev;
+    const int n_i = DEVN ? *A.n_i_dev : A.n_i;
     constexpr bool ADJ = MODE == MODE_ADJOINT;
     constexpr bool NN = MODE == MODE_NN;
     constexpr int NQ = NN ? 9 : 7;              // reduced quantities per i
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
     extern __shared__ __align__(128) unsigned char smem_raw[];
     JMixed *tiles = reinterpret_cast<JMixed *>(smem_raw);
     __shared__ __align__(8) uint64_t bars[STAGES];
-    if ((long long)blockIdx.x * I_CTA >= A.n_i)
-        return;  // beyond the block of a device-driven launch (uniform over the CTA)
+    if (DEVN && (long long)blockIdx.x * I_CTA >= n_i)
+        return;  // beyond the block (uniform over the CTA)
 
     const int tid = threadIdx.x;
     const int g = tid / GT;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
     for (int q = 0; q < NI; ++q) {
         const int k = blockIdx.x * I_CTA + s + q * GT;
         int i = -1;
-        if (k < A.n_i) {
+        if (k < n_i) {
             i = A.ilist ? A.ilist[k] : k;
             if (i < 0 || i >= A.n_j) {
                 atomicOr(A.err, ERR_INDEX);
@@ -252,9 +252,9 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
             const int slot = blockIdx.x * I_CTA + s + q * GT;
 #pragma unroll
             for (int c = 0; c < 7; ++c)
-                write_out(A, c, slot, (double)acc[q].h[c] + (double)acc[q].l[c]);
+                write_out(A, n_i, c, slot, (double)acc[q].h[c] + (double)acc[q].l[c]);
             if (NN)
-                write_nn(A, slot, nn_r(q), nn_j(q));
+                write_nn(A, n_i, slot, nn_r(q), nn_j(q));
         }
     } else {
         __syncthreads();  // all tiles consumed: reuse the ring as reduction space
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
 #pragma unroll
             for (int gg = 0; gg < GROUPS; ++gg)
                 sum += red[(gg * NQ + c) * I_CTA + slot];
-            write_out(A, c, blockIdx.x * I_CTA + slot, sum);
+            write_out(A, n_i, c, blockIdx.x * I_CTA + slot, sum);
         }
         if (NN) {
             for (int slot = tid; slot < I_CTA; slot += FORCE_THREADS) {
@@ -286,10 +286,27 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
 #pragma unroll
                 for (int gg = 0; gg < GROUPS; ++gg)
                     nn_min(r2, j, red[(gg * NQ + 7) * I_CTA + slot], red[(gg * NQ + 8) * I_CTA + slot]);
-                write_nn(A, blockIdx.x * I_CTA + slot, r2, j);
+                write_nn(A, n_i, blockIdx.x * I_CTA + slot, r2, j);
             }
         }
     }
+}
+
+template <int GROUPS, bool GUARD, int MODE, bool DEVN>
+cudaError_t launch_v(const ForceArgs &a, int iblocks, int n_split, cudaStream_t st)
+{
+    const size_t smem = MIX_SMEM_BYTES;
+    if (smem > 48 * 1024) {
+        static bool opted = false;  // per template instance
+        if (!opted) {
+            cudaFuncSetAttribute(k_force_mixed<GROUPS, GUARD, MODE, DEVN>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            opted = true;
+        }
+    }
+    dim3 grid(iblocks, n_split);
+    k_force_mixed<GROUPS, GUARD, MODE, DEVN><<<grid, FORCE_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <int GROUPS, bool GUARD, int MODE>
@@ -299,18 +316,13 @@ cudaError_t launch_t(const ForceArgs &a, int n_split, cudaStream_t st)
     const int iblocks = (a.n_i + I_CTA - 1) / I_CTA;
     if (iblocks == 0)
         return cudaSuccess;
-    const size_t smem = MIX_SMEM_BYTES;
-    if (smem > 48 * 1024) {
-        static bool opted = false;  // per template instance
-        if (!opted) {
-            cudaFuncSetAttribute(k_force_mixed<GROUPS, GUARD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-            opted = true;
-        }
+    if (a.n_i_dev) {  // only the block-step force of the device-driven loop reads n_i on the device
+        if constexpr (MODE == MODE_ACC_JERK_POT)
+            return launch_v<GROUPS, GUARD, MODE, true>(a, iblocks, n_split, st);
+        else
+            return cudaErrorInvalidValue;
     }
-    dim3 grid(iblocks, n_split);
-    k_force_mixed<GROUPS, GUARD, MODE><<<grid, FORCE_THREADS, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_v<GROUPS, GUARD, MODE, false>(a, iblocks, n_split, st);
 }
 
 template <int GROUPS, bool GUARD, int MODE>
@@ -319,9 +331,9 @@ int occ_t()
     int n = 0;
     const size_t smem = MIX_SMEM_BYTES;
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_force_mixed<GROUPS, GUARD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_force_mixed<GROUPS, GUARD, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_mixed<GROUPS, GUARD, MODE>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_mixed<GROUPS, GUARD, MODE, false>,
                                                   FORCE_THREADS, smem);
     return n;
 }
