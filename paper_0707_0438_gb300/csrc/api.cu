@@ -372,6 +372,10 @@ int check_params(double eps, double G, double r_min, int prec)
 // has a grid for class_max[c] and the shape chosen for a block of about
 // 0.7 class_max[c], and its CTAs beyond the actual block return at once.
 
+// Block steps per iteration of the WHILE node: one iteration costs about
+// 3.4 us on its own, so the body holds several steps.
+constexpr int RUN_UNROLL = 4;
+
 struct RunPlan {
     int n_classes = 0;
     int32_t class_max[MAX_SEL_CLASSES] = {};
@@ -441,8 +445,8 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     cudaGraph_t top = nullptr;
     cudaStream_t cs = nullptr;
     bool capturing = false;
-    cudaGraphConditionalHandle h_loop, h_branch;
-    cudaGraphNodeParams wp{}, sp{};
+    cudaGraphConditionalHandle h_loop, h_branch[RUN_UNROLL];
+    cudaGraphNodeParams wp{}, sp[RUN_UNROLL] = {};
     cudaGraphNode_t wnode, snode;
     cudaGraph_t body, cap_graph;
     const cudaGraphNode_t *deps = nullptr;
@@ -460,7 +464,8 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     wp.conditional.size = 1;
     CKG(cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp));
     body = wp.conditional.phGraph_out[0];
-    CKG(cudaGraphConditionalHandleCreate(&h_branch, body, 0, cudaGraphCondAssignDefault));
+    for (int u = 0; u < RUN_UNROLL; ++u)
+        CKG(cudaGraphConditionalHandleCreate(&h_branch[u], body, 0, cudaGraphCondAssignDefault));
 
     a.n = n;
     a.n_pad = (int)round_up(std::max<int64_t>(n, 1), TILE_J);
@@ -478,48 +483,53 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     a.acc = c->d_acc;
     a.jerk = c->d_jerk;
     a.ilist = c->d_ilist;
+    a.chunk_off = c->d_step_counts;
+    a.chunk_cnt = c->d_step_counts + c->step_ctas;
     a.eta = c->eta;
     a.dt_min = c->dt_min;
     a.dt_max = c->dt_max;
     a.run = c->d_run;
     a.count_out = c->d_count;
     a.t_next_out = c->d_scal;
-    a.chunk_off = c->d_step_counts;
-    a.chunk_cnt = c->d_step_counts + c->step_ctas;
     a.err = c->d_err;
     a.loop = h_loop;
-    a.branch = h_branch;
     a.n_classes = p.n_classes;
     for (int q = 0; q < p.n_classes; ++q)
         a.class_max[q] = p.class_max[q];
     a.n_j = n;
 
-    // loop body: the two step kernels, then the SWITCH over force launches
+    // loop body: RUN_UNROLL block steps, each the two step kernels and a SWITCH
+    // over force launches (a step after the one that ended the run finds nothing
+    // pending and nothing due, and does nothing)
     CKG(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     capturing = true;
-    CKG(launch_block_step(a, c->step_ctas, cs));
-    CKG(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cap_graph, &deps, nullptr, &ndeps));
-    sp.type = cudaGraphNodeTypeConditional;
-    sp.conditional.handle = h_branch;
-    sp.conditional.type = cudaGraphCondTypeSwitch;
-    sp.conditional.size = (unsigned)p.n_classes;
-    CKG(cudaGraphAddNode(&snode, cap_graph, deps, nullptr, ndeps, &sp));
-    CKG(cudaStreamUpdateCaptureDependencies(cs, &snode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    for (int u = 0; u < RUN_UNROLL; ++u) {
+        a.branch = h_branch[u];
+        CKG(launch_block_step(a, c->step_ctas, cs));
+        CKG(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cap_graph, &deps, nullptr, &ndeps));
+        sp[u].type = cudaGraphNodeTypeConditional;
+        sp[u].conditional.handle = h_branch[u];
+        sp[u].conditional.type = cudaGraphCondTypeSwitch;
+        sp[u].conditional.size = (unsigned)p.n_classes;
+        CKG(cudaGraphAddNode(&snode, cap_graph, deps, nullptr, ndeps, &sp[u]));
+        CKG(cudaStreamUpdateCaptureDependencies(cs, &snode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    }
     capturing = false;
     CKG(cudaStreamEndCapture(cs, &cap_graph));
 
     // the force branches
-    for (int q = 0; q < p.n_classes; ++q) {
-        CKG(cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[q], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal));
-        capturing = true;
-        rc = enqueue_force(c, cs, p.shape[q], p.class_max[q], c->d_count, c->d_ilist, n, MODE_ACC_JERK_POT,
-                           c->d_acc, c->d_jerk, c->d_pot);
-        if (rc)
-            goto done;
-        capturing = false;
-        CKG(cudaStreamEndCapture(cs, &cap_graph));
-    }
+    for (int u = 0; u < RUN_UNROLL; ++u)
+        for (int q = 0; q < p.n_classes; ++q) {
+            CKG(cudaStreamBeginCaptureToGraph(cs, sp[u].conditional.phGraph_out[q], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+            capturing = true;
+            rc = enqueue_force(c, cs, p.shape[q], p.class_max[q], c->d_count, c->d_ilist, n, MODE_ACC_JERK_POT,
+                               c->d_acc, c->d_jerk, c->d_pot);
+            if (rc)
+                goto done;
+            capturing = false;
+            CKG(cudaStreamEndCapture(cs, &cap_graph));
+        }
     CKG(cudaGraphInstantiate(exec_out, top, 0));
 
 done:

@@ -351,13 +351,24 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *
 // Hermite corrector for the block (Sect. 3): a2, a3 from the two (a, jerk)
 // pairs, corrected x and v, and (update_dt) Aarseth's step on the
 // power-of-two ladder.
+__device__ __forceinline__ bool is_pow2(double d)
+{
+    return (__double_as_longlong(d) & 0x000fffffffffffffll) == 0 && d > 0.0 && isfinite(d);
+}
+
 // Hermite corrector of block member k (particle ilist[k], or k) at t_next
 // from its new a, jerk (acc/jerk row k), and with update_dt its new block
 // step: Aarseth's criterion quantised to a power of two that may shrink
 // freely and double only where t_next is a multiple of the doubled step.
-// FP64 is the scarce pipe on this part (about 1 TFLOP/s), so this spends it
-// sparingly: one reciprocal of dt instead of a divide per term, and the
-// powers of dt shared by the three components.
+// FP64 is the scarce pipe on this part (about 1 TFLOP/s, and a single
+// member's dependency chain is latency-bound), so this spends it sparingly:
+//  - 1/dt of a power-of-two step from its exponent (exact), else a divide;
+//  - the powers of dt shared by the three components, fused multiply-adds;
+//  - the criterion dt_A = sqrt(X / Y), X = eta (|a||a2| + |j|^2),
+//    Y = |j||a3| + |a2|^2, compared in squared form (q < dt_A <=> q^2 Y < X),
+//    with |a||a2| = sqrt(|a|^2 |a2|^2): two square roots, no divide;
+//  - "t_next is a multiple of 2 dt" tested exactly by scaling when 2 dt is a
+//    power of two, by fmod otherwise.
 __device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double t_next, double eta, double dt_min,
                                             double dt_max, int update_dt, const double *xp, const double *vp,
                                             const double *acc, const double *jerk, double *bx, double *bv,
@@ -365,38 +376,50 @@ __device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double 
 {
     const size_t i = ilist ? (size_t)ilist[k] : (size_t)k;
     const double dt = t_next - bt[i];
-    const double idt = 1.0 / dt;
+    const bool p2 = is_pow2(dt);
+    const double idt = p2 ? __longlong_as_double((2046ll << 52) - (__double_as_longlong(dt) & 0x7ff0000000000000ll))
+                          : 1.0 / dt;
     const double idt2 = idt * idt, idt3 = idt2 * idt;
-    const double dt2 = dt * dt, dt3 = dt2 * dt, dt4 = dt2 * dt2;
-    const double c3 = dt3 * (1.0 / 6.0), c4 = dt4 * (1.0 / 24.0), c5 = dt4 * dt * (1.0 / 120.0);
-    double a1[3], j1[3], a2e[3], a3[3];
+    const double dt2 = dt * dt, dt4 = dt2 * dt2;
+    const double c3 = dt2 * dt * (1.0 / 6.0), c4 = dt4 * (1.0 / 24.0), c5 = dt4 * dt * (1.0 / 120.0);
+    const double dt6 = 6.0 * dt;
+    double A = 0.0, J = 0.0, N2 = 0.0, N3 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
-        a1[c] = acc[3 * (size_t)k + c];
-        j1[c] = jerk[3 * (size_t)k + c];
-        const double da = a0 - a1[c];
-        const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1[c])) * idt2;
-        a3[c] = (12.0 * da + 6.0 * dt * (j0 + j1[c])) * idt3;
-        bx[3 * i + c] = xp[3 * i + c] + a2 * c4 + a3[c] * c5;
-        bv[3 * i + c] = vp[3 * i + c] + a2 * c3 + a3[c] * c4;
-        ba[3 * i + c] = a1[c];
-        bj[3 * i + c] = j1[c];
-        a2e[c] = a2 + dt * a3[c];
+        const double a1 = acc[3 * (size_t)k + c], j1 = jerk[3 * (size_t)k + c];
+        const double da = a0 - a1;
+        const double a2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da) * idt2;
+        const double a3 = fma(dt6, j0 + j1, 12.0 * da) * idt3;
+        bx[3 * i + c] = fma(a3, c5, fma(a2, c4, xp[3 * i + c]));
+        bv[3 * i + c] = fma(a3, c4, fma(a2, c3, vp[3 * i + c]));
+        ba[3 * i + c] = a1;
+        bj[3 * i + c] = j1;
+        const double a2e = fma(dt, a3, a2);  // a2 at the end of the step
+        A = fma(a1, a1, A);
+        J = fma(j1, j1, J);
+        N2 = fma(a2e, a2e, N2);
+        N3 = fma(a3, a3, N3);
     }
     bt[i] = t_next;
     if (update_dt) {
-        const double na = norm3(a1), nj = norm3(j1), n2 = norm3(a2e), n3 = norm3(a3);
-        const double raw = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
-        double q;
-        if (raw < dt) {
-            q = dt;
-            while (q > raw && q > dt_min)
+        const double X = eta * (sqrt(A * N2) + J), Y = sqrt(J * N3) + N2;
+        double q = dt;
+        if (X == 0.0 && Y == 0.0) {
+            // no criterion (0 / 0): keep the step
+        } else if (X < dt2 * Y) {
+            while (q > dt_min && X < q * q * Y)
                 q *= 0.5;
-        } else if (raw >= 2.0 * dt && 2.0 * dt <= dt_max && fmod(t_next, 2.0 * dt) == 0.0) {
-            q = 2.0 * dt;
-        } else {
-            q = dt;
+        } else if (X >= 4.0 * dt2 * Y && 2.0 * dt <= dt_max) {
+            bool multiple;
+            if (p2) {
+                const double r = t_next * (0.5 * idt);  // exact: a power-of-two scaling
+                multiple = r == trunc(r);
+            } else {
+                multiple = fmod(t_next, 2.0 * dt) == 0.0;
+            }
+            if (multiple)
+                q = 2.0 * dt;
         }
         bdt[i] = fmin(fmax(q, dt_min), dt_max);
     }

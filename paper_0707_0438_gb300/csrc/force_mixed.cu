@@ -257,35 +257,45 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
                 write_nn(A, n_i, slot, nn_r(q), nn_j(q));
         }
     } else {
+        // Cross-group sum in double-single (FP32 two-sums): FP64 is the scarce
+        // pipe on this part, so each output is converted to FP64 once, after
+        // the groups are summed, instead of every group's partial.
         __syncthreads();  // all tiles consumed: reuse the ring as reduction space
-        static_assert((size_t)GROUPS * NQ * I_CTA * sizeof(double) <= MIX_SMEM_BYTES, "reduction space");
-        double *red = reinterpret_cast<double *>(smem_raw);  // [GROUPS][NQ][I_CTA]
+        static_assert((size_t)GROUPS * NQ * I_CTA * sizeof(float2) <= MIX_SMEM_BYTES, "reduction space");
+        float2 *red = reinterpret_cast<float2 *>(smem_raw);  // [GROUPS][NQ][I_CTA] of (hi, lo)
 #pragma unroll
         for (int q = 0; q < NI; ++q) {
 #pragma unroll
             for (int c = 0; c < 7; ++c)
-                red[(g * NQ + c) * I_CTA + s + q * GT] = (double)acc[q].h[c] + (double)acc[q].l[c];
-            if (NN) {
-                red[(g * NQ + 7) * I_CTA + s + q * GT] = nn_r(q);
-                red[(g * NQ + 8) * I_CTA + s + q * GT] = nn_j(q);
+                red[(g * NQ + c) * I_CTA + s + q * GT] = make_float2(acc[q].h[c], acc[q].l[c]);
+            if (NN) {  // (nearest r2, its index as bits)
+                const NNPair &np = nnp[q >> 1];
+                red[(g * NQ + 7) * I_CTA + s + q * GT] =
+                    make_float2((q & 1) ? np.r1 : np.r0, __int_as_float((q & 1) ? np.j1 : np.j0));
             }
         }
         __syncthreads();
         for (int o = tid; o < 7 * I_CTA; o += FORCE_THREADS) {
             const int c = o / I_CTA;
             const int slot = o - c * I_CTA;
-            double sum = 0.0;
+            float2 v = red[c * I_CTA + slot];
+            float hi = v.x, lo = v.y;
 #pragma unroll
-            for (int gg = 0; gg < GROUPS; ++gg)
-                sum += red[(gg * NQ + c) * I_CTA + slot];
-            write_out(A, n_i, c, blockIdx.x * I_CTA + slot, sum);
+            for (int gg = 1; gg < GROUPS; ++gg) {
+                v = red[(gg * NQ + c) * I_CTA + slot];
+                two_sum(hi, lo, v.x);
+                lo = __fadd_rn(lo, v.y);
+            }
+            write_out(A, n_i, c, blockIdx.x * I_CTA + slot, (double)hi + (double)lo);
         }
         if (NN) {
             for (int slot = tid; slot < I_CTA; slot += FORCE_THREADS) {
                 double r2 = INFINITY, j = -1.0;
 #pragma unroll
-                for (int gg = 0; gg < GROUPS; ++gg)
-                    nn_min(r2, j, red[(gg * NQ + 7) * I_CTA + slot], red[(gg * NQ + 8) * I_CTA + slot]);
+                for (int gg = 0; gg < GROUPS; ++gg) {
+                    const float2 v = red[(gg * NQ + 7) * I_CTA + slot];
+                    nn_min(r2, j, (double)v.x, (double)__float_as_int(v.y));
+                }
                 write_nn(A, n_i, blockIdx.x * I_CTA + slot, r2, j);
             }
         }
