@@ -230,6 +230,12 @@ int kirin_set_device_loop(kirin_ctx *ctx, int32_t enable);
 /* One shared step of size dt for all particles (no step-size update). */
 int kirin_hermite_shared_step(kirin_ctx *ctx, double dt);
 
+/* n_steps shared steps of size dt, enqueued back to back with a single
+ * synchronisation (and error check) at the end; the same kernels and
+ * results as n_steps calls of kirin_hermite_shared_step.  Errors: EINVAL
+ * (dt <= 0, n_steps < 0), ESTATE before kirin_hermite_init. */
+int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps);
+
 /* Copy the integrator state (host arrays, each may be NULL): x, v, a, jerk
  * (n_j x 3), t and dt (n_j). */
 int kirin_get_state(kirin_ctx *ctx, double *x, double *v, double *a, double *jerk, double *t,

@@ -75,6 +75,7 @@ _SIGS = {
     "kirin_hermite_block_step": (ctypes.c_int, [_P, _D, _PD, _PI64]),
     "kirin_hermite_run": (ctypes.c_int, [_P, _D, _I64, _PI64, _PD]),
     "kirin_set_device_loop": (ctypes.c_int, [_P, _I32]),
+    "kirin_hermite_shared_run": (ctypes.c_int, [_P, _D, _I64]),
     "kirin_hermite_shared_step": (ctypes.c_int, [_P, _D]),
     "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
     "kirin_set_state": (ctypes.c_int, [_P, _I64, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _D, _D, _D]),
@@ -339,6 +340,10 @@ class Kirin:
 
     def hermite_shared_step(self, dt):
         self._check(self.lib.kirin_hermite_shared_step(self.ctx, float(dt)), "kirin_hermite_shared_step")
+
+    def hermite_shared_run(self, dt, n_steps):
+        """n_steps shared steps, one synchronisation at the end."""
+        self._check(self.lib.kirin_hermite_shared_run(self.ctx, float(dt), int(n_steps)), "kirin_hermite_shared_run")
 
     def get_state(self):
         n = self.n_j

@@ -164,6 +164,12 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
         Shape s{c->fix_groups, std::min(c->fix_split, std::max(1, ntiles))};
         return s;
     }
+    if (prec == KIRIN_MIXED && mode == MODE_ACC_JERK_POT && n_i <= TINY_MAX &&
+        (int64_t)ntiles * TILE_J <= (int64_t)TINY_JCHUNK * 2 * c->nsm) {
+        // tiny block: j ranges of 64..TINY_JCHUNK records, about two CTAs per SM
+        const int ctas = std::max(1, std::min(2 * c->nsm, ntiles * TILE_J / 64));
+        return Shape{0, ctas};
+    }
     if (c->table_n > 0 && prec == c->table_prec && mode == MODE_ACC_JERK_POT) {
         for (int k = 0; k < c->table_n; ++k)
             if (n_i <= c->table_ni[k])
@@ -255,8 +261,7 @@ int enqueue_force(kirin_ctx *c, cudaStream_t st, Shape s, int64_t n_i, const int
     a.nn = nn;
     a.nn_r2 = nn_r2;
     a.nq = mode == MODE_NN ? 9 : 7;
-    const int i_cta = (c->prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1) * FORCE_THREADS / s.groups;
-    a.n_i_pad = (int)round_up(n_i, i_cta);
+    a.n_i_pad = (int)round_up(n_i, shape_i_cta(s, c->prec == KIRIN_MIXED));
     if (s.n_split > 1) {
         if ((size_t)s.n_split * a.nq * a.n_i_pad > c->partial_cap)
             return set_msg(c, KIRIN_ESTATE, "split-partial buffer too small for the launch");
@@ -276,8 +281,7 @@ size_t partial_doubles(const kirin_ctx *c, Shape s, int64_t n_i, int mode)
 {
     if (s.n_split <= 1)
         return 0;
-    const int i_cta = (c->prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1) * FORCE_THREADS / s.groups;
-    return (size_t)s.n_split * (mode == MODE_NN ? 9 : 7) * (size_t)round_up(n_i, i_cta);
+    return (size_t)s.n_split * (mode == MODE_NN ? 9 : 7) * (size_t)round_up(n_i, shape_i_cta(s, c->prec == KIRIN_MIXED));
 }
 
 // Enqueue one force launch (plus split reduction) over the current images on
@@ -389,7 +393,7 @@ RunPlan plan_run(kirin_ctx *c)
     int64_t hi = n;
     int32_t desc[MAX_SEL_CLASSES];
     int k = 0;
-    while (hi > 64 && k < MAX_SEL_CLASSES - 1) {
+    while (hi > TINY_MAX && k < MAX_SEL_CLASSES - 1) {
         desc[k++] = (int32_t)hi;
         hi = (hi + 1) / 2;
     }
@@ -484,7 +488,6 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     a.jerk = c->d_jerk;
     a.ilist = c->d_ilist;
     a.chunk_off = c->d_step_counts;
-    a.chunk_cnt = c->d_step_counts + c->step_ctas;
     a.eta = c->eta;
     a.dt_min = c->dt_min;
     a.dt_max = c->dt_max;
@@ -1168,29 +1171,33 @@ int kirin_set_device_loop(kirin_ctx *ctx, int32_t enable)
     return KIRIN_OK;
 }
 
-int kirin_hermite_shared_step(kirin_ctx *ctx, double dt)
+int kirin_hermite_shared_step(kirin_ctx *ctx, double dt) { return kirin_hermite_shared_run(ctx, dt, 1); }
+
+int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps)
 {
-    if (!ctx || !(dt > 0))
+    if (!ctx || !(dt > 0) || !isfinite(dt) || n_steps < 0)
         return KIRIN_EINVAL;
     if (!ctx->hermite_ready)
-        return set_msg(ctx, KIRIN_ESTATE, "hermite_shared_step: call kirin_hermite_init first");
+        return set_msg(ctx, KIRIN_ESTATE, "hermite_shared_run: call kirin_hermite_init first");
     DeviceGuard dg(ctx->device);
     const int n = (int)ctx->n_j;
-    const double t_next = ctx->t_shared + dt;
-    ctx->pred_mode = 1;
-    ctx->pred_t = t_next;
-    ctx->images_dirty = true;
-    int rc = ensure_images(ctx);
-    if (rc)
-        return rc;
-    rc = run_force(ctx, n, nullptr, n, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
-    if (rc)
-        return rc;
-    CK(ctx, launch_hermite_correct(n, nullptr, t_next, ctx->eta, ctx->dt_min, ctx->dt_max, 0, ctx->xp,
-                                   ctx->vp, ctx->d_acc, ctx->d_jerk, ctx->bx, ctx->bv, ctx->ba, ctx->bj,
-                                   ctx->bt, ctx->bdt, ctx->stream));
-    ctx->t_shared = t_next;
-    ctx->images_dirty = true;
+    for (int64_t s = 0; s < n_steps; ++s) {  // enqueued back to back; one synchronisation at the end
+        const double t_next = ctx->t_shared + dt;
+        ctx->pred_mode = 1;
+        ctx->pred_t = t_next;
+        ctx->images_dirty = true;
+        int rc = ensure_images(ctx);
+        if (rc)
+            return rc;
+        rc = run_force(ctx, n, nullptr, n, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
+        if (rc)
+            return rc;
+        CK(ctx, launch_hermite_correct(n, nullptr, t_next, ctx->eta, ctx->dt_min, ctx->dt_max, 0, ctx->xp,
+                                       ctx->vp, ctx->d_acc, ctx->d_jerk, ctx->bx, ctx->bv, ctx->ba, ctx->bj,
+                                       ctx->bt, ctx->bdt, ctx->stream));
+        ctx->t_shared = t_next;
+        ctx->images_dirty = true;
+    }
     ctx->pending = false;
     return read_device_errors(ctx);
 }

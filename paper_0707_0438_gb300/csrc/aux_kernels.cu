@@ -369,12 +369,12 @@ __device__ __forceinline__ bool is_pow2(double d)
 //    with |a||a2| = sqrt(|a|^2 |a2|^2): two square roots, no divide;
 //  - "t_next is a multiple of 2 dt" tested exactly by scaling when 2 dt is a
 //    power of two, by fmod otherwise.
-__device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double t_next, double eta, double dt_min,
-                                            double dt_max, int update_dt, const double *xp, const double *vp,
-                                            const double *acc, const double *jerk, double *bx, double *bv,
-                                            double *ba, double *bj, double *bt, double *bdt)
+// Member k of the block is particle i; returns its new t_i + dt_i.
+__device__ __forceinline__ double correct_at(size_t i, int k, double t_next, double eta, double dt_min,
+                                             double dt_max, int update_dt, const double *xp, const double *vp,
+                                             const double *acc, const double *jerk, double *bx, double *bv,
+                                             double *ba, double *bj, double *bt, double *bdt)
 {
-    const size_t i = ilist ? (size_t)ilist[k] : (size_t)k;
     const double dt = t_next - bt[i];
     const bool p2 = is_pow2(dt);
     const double idt = p2 ? __longlong_as_double((2046ll << 52) - (__double_as_longlong(dt) & 0x7ff0000000000000ll))
@@ -421,8 +421,20 @@ __device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double 
             if (multiple)
                 q = 2.0 * dt;
         }
-        bdt[i] = fmin(fmax(q, dt_min), dt_max);
+        q = fmin(fmax(q, dt_min), dt_max);
+        bdt[i] = q;
+        return t_next + q;
     }
+    return t_next + bdt[i];
+}
+
+__device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double t_next, double eta, double dt_min,
+                                            double dt_max, int update_dt, const double *xp, const double *vp,
+                                            const double *acc, const double *jerk, double *bx, double *bv,
+                                            double *ba, double *bj, double *bt, double *bdt)
+{
+    correct_at(ilist ? (size_t)ilist[k] : (size_t)k, k, t_next, eta, dt_min, dt_max, update_dt, xp, vp, acc, jerk,
+               bx, bv, ba, bj, bt, bdt);
 }
 
 // One warp per CTA, and member k on CTA k mod gridDim (lane k / gridDim):
@@ -479,43 +491,81 @@ __device__ __forceinline__ int cta_sum(int v)
     return total;
 }
 
-__device__ __forceinline__ void chunk_of(int n, int& c0, int& c1)
+__device__ __forceinline__ void chunk_of(int n, int &c0, int &c1)
 {
     const int chunk = (n + (int)gridDim.x - 1) / (int)gridDim.x;
     c0 = min(n, (int)blockIdx.x * chunk);
     c1 = min(n, c0 + chunk);
 }
 
+// Rank of this thread's flag among the CTA's flags of one pass (index order),
+// and the pass's total; uniform call over the CTA.
+__device__ __forceinline__ int cta_rank(bool flag, int &all)
+{
+    __shared__ int warp_tot[STEP_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned ballot = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0)
+        warp_tot[warp] = __popc(ballot);
+    __syncthreads();
+    int ahead = 0;
+    all = 0;
+#pragma unroll
+    for (int w = 0; w < STEP_WARPS; ++w) {
+        ahead += w < warp ? warp_tot[w] : 0;
+        all += warp_tot[w];
+    }
+    __syncthreads();
+    return ahead + __popc(ballot & ((1u << lane) - 1u));
+}
+
+// Correct the pending block and take min (t_i + dt_i).  Thread t of CTA b
+// owns particles c0 + t, c0 + t + 256, ... of its chunk.  A member of the
+// pending block is recognised by t_i + dt_i == the block time; the select
+// kernel listed the chunk's members in index order from chunk_off[b], so a
+// member's rank among them gives its row of the force results.  Members add
+// their new end time to the minimum, the others their unchanged one.
 __global__ void __launch_bounds__(STEP_THREADS) k_step_correct(const StepArgs A)
 {
     RunState *R = A.run;
     const int par = (int)(R->steps & 1);
+    const bool any = R->pending > 0;
+    const double t_prev = R->t_last;
     int c0, c1;
     chunk_of(A.n, c0, c1);
-    if (R->pending > 0) {
-        // this CTA's members: one per warp first (an FP64 warp instruction costs
-        // the same with one active lane as with 32)
-        const int off = A.chunk_off[blockIdx.x], cnt = A.chunk_cnt[blockIdx.x];
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int m = warp + lane * STEP_WARPS; m < cnt; m += STEP_THREADS)
-            correct_one(off + m, A.ilist, R->t_last, A.eta, A.dt_min, A.dt_max, 1, A.xp, A.vp, A.acc, A.jerk, A.bx,
-                        A.bv, A.ba, A.bj, A.bt, A.bdt);
-        __syncthreads();
-    }
+    int base = any ? A.chunk_off[blockIdx.x] : 0;
     unsigned long long mn = ~0ull;
-    for (int i = c0 + threadIdx.x; i < c1; i += STEP_THREADS)
-        mn = min(mn, (unsigned long long)__double_as_longlong(__ldcg(A.bt + i) + __ldcg(A.bdt + i)));
+    for (int i0 = c0; i0 < c1; i0 += STEP_THREADS) {
+        const int i = i0 + threadIdx.x;
+        double end = 0.0;
+        bool member = false;
+        if (i < c1) {
+            end = A.bt[i] + A.bdt[i];
+            member = any && end == t_prev;
+        }
+        int all;
+        const int rank = cta_rank(member, all);
+        if (member)
+            end = correct_at((size_t)i, base + rank, t_prev, A.eta, A.dt_min, A.dt_max, 1, A.xp, A.vp, A.acc,
+                             A.jerk, A.bx, A.bv, A.ba, A.bj, A.bt, A.bdt);
+        if (i < c1)
+            mn = min(mn, (unsigned long long)__double_as_longlong(end));
+        base += all;
+    }
     mn = cta_min_u64(mn);
     if (threadIdx.x == 0) {
         atomicMin(&R->minw[par], mn);
         if (blockIdx.x == 0) {  // fresh words for the select kernel and the next step
             R->minw[par ^ 1] = ~0ull;
-            R->list_count = 0;
-            R->done = 0u;
+            R->list_done = 0ull;
         }
     }
 }
 
+// Predict every j to t_next and list the next block.  One 64-bit atomic per
+// CTA reserves its range of the list (low word) and counts finished CTAs
+// (high word); the CTA that reserves last publishes the block at once (the
+// list itself is read only by later kernels).
 __global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
 {
     RunState *R = A.run;
@@ -539,62 +589,48 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
     }
     int c0, c1;
     chunk_of(A.n, c0, c1);
-    for (int k = c0 + threadIdx.x; k < c1; k += STEP_THREADS)
+    int c = 0;
+    for (int k = c0 + threadIdx.x; k < c1; k += STEP_THREADS) {
         predict_one(k, A.n, tn, 1, A.bm, A.bx, A.bv, A.ba, A.bj, A.bt, A.xp, A.vp, A.jm, A.jd, A.err);
+        c += A.bt[k] + A.bdt[k] == tn;
+    }
     for (int k = A.n + blockIdx.x * STEP_THREADS + threadIdx.x; k < A.n_pad; k += gridDim.x * STEP_THREADS)
         predict_one(k, A.n, tn, 1, A.bm, A.bx, A.bv, A.ba, A.bj, A.bt, A.xp, A.vp, A.jm, A.jd, A.err);  // padding
-    int c = 0;
-    for (int i = c0 + threadIdx.x; i < c1; i += STEP_THREADS)
-        c += A.bt[i] + A.bdt[i] == tn;
     const int cnt = cta_sum(c);
     __shared__ int base_s;
     if (threadIdx.x == 0) {
-        base_s = cnt ? atomicAdd(&R->list_count, cnt) : 0;
-        A.chunk_off[blockIdx.x] = base_s;
-        A.chunk_cnt[blockIdx.x] = cnt;
+        const unsigned long long prev = atomicAdd(&R->list_done, (1ull << 32) | (unsigned long long)cnt);
+        const int off = (int)(prev & 0xffffffffull);
+        base_s = off;
+        A.chunk_off[blockIdx.x] = off;
+        if ((unsigned)(prev >> 32) == gridDim.x - 1) {  // the last reservation: the block is complete
+            const int count = off + cnt;
+            unsigned cls = (unsigned)A.n_classes - 1;
+            for (int q = A.n_classes - 1; q >= 0; --q)
+                if (count <= A.class_max[q])
+                    cls = (unsigned)q;
+            *A.count_out = count;
+            *A.t_next_out = tn;
+            R->steps = steps0 + 1;
+            R->pairs += (double)count * (double)A.n_j;
+            R->t_last = tn;
+            R->pending = count;
+            cudaGraphSetConditional(A.branch, cls);
+            cudaGraphSetConditional(A.loop, 1u);
+        }
     }
     __syncthreads();
     if (cnt) {
-        __shared__ int warp_tot[STEP_WARPS];
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         int base = base_s;
         for (int i0 = c0; i0 < c1; i0 += STEP_THREADS) {
             const int i = i0 + threadIdx.x;
             const bool flag = i < c1 && A.bt[i] + A.bdt[i] == tn;
-            const unsigned ballot = __ballot_sync(0xffffffffu, flag);
-            if (lane == 0)
-                warp_tot[warp] = __popc(ballot);
-            __syncthreads();
-            int ahead = 0, all = 0;
-#pragma unroll
-            for (int w = 0; w < STEP_WARPS; ++w) {
-                ahead += w < warp ? warp_tot[w] : 0;
-                all += warp_tot[w];
-            }
+            int all;
+            const int rank = cta_rank(flag, all);
             if (flag)
-                A.ilist[base + ahead + __popc(ballot & ((1u << lane) - 1u))] = i;
+                A.ilist[base + rank] = i;
             base += all;
-            __syncthreads();
         }
-    }
-    // the last CTA to finish publishes the block
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0 && atomicAdd(&R->done, 1u) == gridDim.x - 1) {
-        __threadfence();
-        const int count = atomicAdd(&R->list_count, 0);
-        unsigned cls = (unsigned)A.n_classes - 1;
-        for (int q = A.n_classes - 1; q >= 0; --q)
-            if (count <= A.class_max[q])
-                cls = (unsigned)q;
-        *A.count_out = count;
-        *A.t_next_out = tn;
-        R->steps = steps0 + 1;
-        R->pairs += (double)count * (double)A.n_j;
-        R->t_last = tn;
-        R->pending = count;
-        cudaGraphSetConditional(A.branch, cls);
-        cudaGraphSetConditional(A.loop, 1u);
     }
 }
 

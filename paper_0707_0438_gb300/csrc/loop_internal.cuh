@@ -20,8 +20,7 @@ struct RunState {
     double t_last;                  // time of the last block selected
     long long pending;              // size of the block forced but not yet corrected
     unsigned long long minw[2];     // atomic minimum of t_i + dt_i, alternating by step parity
-    int list_count;                 // block members listed so far by the select kernel
-    unsigned done;                  // CTAs of the select kernel that finished
+    unsigned long long list_done;   // select kernel: (CTAs done) << 32 | members listed so far
 };
 
 constexpr int MAX_SEL_CLASSES = 16;
@@ -38,7 +37,6 @@ struct StepArgs {
     const double *acc, *jerk;  // forces of the pending block, in list order
     int32_t *ilist;            // the pending block in, the next block out
     int32_t *chunk_off;        // per CTA: where its members start in ilist
-    int32_t *chunk_cnt;        // per CTA: how many there are
     double eta, dt_min, dt_max;
     RunState *run;
     int32_t *count_out;        // size of the next block (read by the force launches)
@@ -52,13 +50,13 @@ struct StepArgs {
 
 // One block step of a device-driven run in two kernels over `ctas` CTAs.
 // The first corrects the pending block (Hermite corrector and new steps),
-// each CTA the members in its own particles, then takes the minimum of
+// each CTA the members among its own particles, and takes the minimum of
 // t_i + dt_i over them.  The second, if t_next <= t_end and fewer than
 // max_steps blocks were taken, predicts every j to t_next and lists the
 // block: each CTA its own members in index order, at a range reserved with
 // one atomic add (so the order of the CTAs' ranges varies; each particle's
 // force and correction do not depend on its place in the list).  The CTA
-// that finishes last publishes the block and sets the graph's WHILE
+// that reserves last publishes the block and sets the graph's WHILE
 // condition (a block was selected) and SWITCH value (the first c with
 // class_max[c] >= block size; n_classes when there is none).  A block time
 // that does not advance stops the loop with ERR_STALL.

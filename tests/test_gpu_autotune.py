@@ -18,7 +18,10 @@ def test_autotuned_table_is_used_and_correct(kirin_lib, tmp_path):
         assert entries and entries[-1][0] == p.n
         assert all(a[0] < b[0] for a, b in zip(entries, entries[1:]))
         for n_i_max, g, s, _ in entries:
-            assert k.get_launch(n_i_max) == (g, min(s, (p.n + 127) // 128))
+            if n_i_max <= 8:  # blocks this small go to the tiny-block kernel whatever the table says
+                assert k.get_launch(n_i_max)[0] == 0
+            else:
+                assert k.get_launch(n_i_max) == (g, min(s, (p.n + 127) // 128))
         for n_i in (1, 37, 1000, 8192):
             il = workloads.i_subset(p.n, n_i, n_i)
             got = k.forces(il)

@@ -82,6 +82,43 @@ def test_wide_j_split_reduction(kirin_lib, precision):
         k.set_launch(0, 0)
 
 
+@pytest.mark.parametrize("n_i", [1, 2, 5, 8])
+def test_tiny_block_kernel(kirin_lib, n_i):
+    """Blocks of at most 8 i go to the tiny-block kernel (j ranges per CTA, lanes over j, Sect. 3.2's
+    j-split taken to the limit); ragged j count, the self pair inside the list, and agreement with the
+    regular kernel under a fixed launch shape."""
+    p = workloads.plummer(40000, 93, masses="lognormal", eps=1e-3)  # 313 tiles, the last one ragged
+    il = workloads.i_subset(p.n, n_i, seed=n_i)
+    il[0] = p.n - 1  # the last particle, in the ragged tile
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    with _ctx(p, "mixed") as k:
+        assert k.get_launch(n_i)[0] == 0 and k.get_launch(9)[0] != 0
+        tiny = k.forces(il)
+        k.set_launch(8, 64)
+        regular = k.forces(il)
+        k.set_launch(0, 0)
+    assert_parity(tiny, ref, "mixed", f"tiny n_i={n_i}")
+    for a, b in zip(tiny, regular):
+        assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
+
+
+def test_tiny_block_kernel_guard_and_duplicates(kirin_lib):
+    """eps = 0 with r_min through the tiny-block kernel: a coincident distinct pair contributes
+    nothing, repeated and unordered i are each evaluated."""
+    p = workloads.plummer(3001, 94, eps=0.0)
+    x = p.x.copy()
+    x[7] = x[8]
+    r_min = 1e-6
+    il = np.array([8, 3000, 7, 8, 0, 1500], dtype=np.int32)
+    with abi.Kirin(p.n, 0.0, r_min=r_min, precision="mixed") as k:
+        k.set_j_particles(p.m, x, p.v)
+        assert k.get_launch(len(il))[0] == 0
+        got = k.forces(il)
+    ref = oracle.acc_jerk_pot(p.m, x, p.v, 0.0, r_min=r_min, i_idx=il)
+    assert_parity(got, ref, "mixed", "tiny eps=0")
+    assert np.array_equal(got[0][0], got[0][3])
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_duplicate_and_unordered_i_list(kirin_lib, precision):
     p = workloads.plummer(700, 8, eps=0.01)

@@ -29,6 +29,26 @@ def test_hermite_shared_steps_small_config(kirin_lib, precision, tol):
     assert np.all(st["t"] == steps * dt)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shared_run_is_repeated_shared_steps(kirin_lib, precision):
+    """kirin_hermite_shared_run(dt, 10) enqueues the same kernels as 10 single steps: identical state."""
+    p = workloads.config_small()
+    out = []
+    for run in (True, False):
+        with abi.Kirin(p.n, p.eps, precision=precision) as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            k.hermite_init(0.0)
+            if run:
+                k.hermite_shared_run(1.0 / 1024, 10)
+            else:
+                for _ in range(10):
+                    k.hermite_shared_step(1.0 / 1024)
+            out.append(k.get_state())
+    for key in ("x", "v", "a", "j", "t", "dt"):
+        assert np.array_equal(out[0][key], out[1][key]), key
+    assert np.all(out[0]["t"] == 10.0 / 1024)
+
+
 def test_hermite_block_steps_fp64_follow_the_oracle(kirin_lib):
     """Block time-steps (Aarseth criterion, power-of-two levels): same schedule and state as the oracle."""
     p = workloads.plummer(256, 1002, eps=1e-3)
