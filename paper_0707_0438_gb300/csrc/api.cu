@@ -402,7 +402,9 @@ RunPlan plan_run(kirin_ctx *c)
     const int ntiles = (int)((std::max<int64_t>(n, 1) + TILE_J - 1) / TILE_J);
     for (int q = 0; q < k; ++q) {
         p.class_max[q] = desc[k - 1 - q];
-        const int64_t rep = std::max<int64_t>(1, (int64_t)(0.7 * p.class_max[q]));
+        // a class above the tiny-block bound needs a regular shape (its grid covers class_max)
+        const int64_t floor_rep = p.class_max[q] > TINY_MAX ? TINY_MAX + 1 : 1;
+        const int64_t rep = std::max<int64_t>(floor_rep, (int64_t)(0.7 * p.class_max[q]));
         p.shape[q] = choose_shape(c, rep, ntiles, c->prec, MODE_ACC_JERK_POT, guard_on(c));
     }
     return p;

@@ -120,3 +120,33 @@ def test_block_time_that_stops_advancing_is_an_error(kirin_lib, device_loop):
         k.set_device_loop(device_loop)
         with pytest.raises(abi.KirinError):
             k.hermite_run(2.0 ** 60 + 2.0 ** 10)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("n,eps,r_min", [(1, 1e-2, 0.0), (2, 1e-2, 0.0), (129, 0.0, 1e-6)])
+def test_device_loop_edge_sizes(kirin_lib, precision, n, eps, r_min):
+    """One particle (no force, no jerk: the step criterion is 0/0 and the step is kept), a pair, and a
+    ragged 129 with eps = 0 and the r_min guard: the device loop matches the host loop bit for bit under a
+    fixed launch shape, and keeps its schedule with the automatic shapes (tiny-block kernel included)."""
+    p = workloads.plummer(n, (1006, n), eps=eps)
+
+    def run(device_loop, launch):
+        with abi.Kirin(p.n, eps, r_min=r_min, precision=precision) as k:
+            if launch:
+                k.set_launch(*launch)
+            k.set_j_particles(p.m, p.x, p.v)
+            k.hermite_init(0.0)
+            k.set_device_loop(device_loop)
+            counts = k.hermite_run(1.0 / 8)  # = dt_max: a lone particle (dt = dt_max) steps once
+            return counts, k.get_state()
+
+    host = run(False, (1, 2))
+    dev = run(True, (1, 2))
+    assert dev[0] == host[0] and dev[0][0] > 0
+    for key in STATE_KEYS:
+        assert np.array_equal(dev[1][key], host[1][key]), key
+    auto_h, auto_d = run(False, None), run(True, None)
+    assert auto_d[0][0] == auto_h[0][0]
+    assert np.array_equal(auto_d[1]["t"], auto_h[1]["t"]) and np.array_equal(auto_d[1]["dt"], auto_h[1]["dt"])
+    assert np.allclose(auto_d[1]["x"], auto_h[1]["x"], rtol=0, atol=1e-9 * max(1.0, np.abs(p.x).max()))
+    assert np.all(np.isfinite(auto_d[1]["x"]))
