@@ -100,7 +100,10 @@ int kirin_set_launch(kirin_ctx *ctx, int32_t groups, int32_t n_split);
 int kirin_set_launch_table(kirin_ctx *ctx, int32_t n_entries, const int64_t *n_i_max,
                            const int32_t *groups, const int32_t *n_split);
 
-/* The shape that a force call for n_i i-particles would use now. */
+/* The shape that a force call for n_i i-particles would use now.  groups = 0
+ * names the tiny-block kernel, which serves automatic mixed-precision calls
+ * with n_i <= 8 (and n_j <= 512 x the SM count): n_split CTAs each stage a
+ * range of j in shared memory and give every i a warp. */
 int kirin_get_launch(kirin_ctx *ctx, int64_t n_i, int32_t *groups, int32_t *n_split);
 
 /* GPU_set_j_particle (Appendix A), in bulk: particles [first, first + n) get
