@@ -534,6 +534,8 @@ def run_adjoint(args):
     q = workloads.perturb(p, 1e-3)
     stream = torch.cuda.current_stream().cuda_stream
     k = abi.Kirin(n, p.eps, precision="mixed", stream=stream)
+    from paper_0707_0438_gb300 import autotune
+    autotune.install(k, n, torch.cuda.get_device_name(dev), "mixed")  # acc+pot and adjoint tables, if stored
     T = lambda a, g=False: torch.tensor(a, dtype=torch.float64, device=dev, requires_grad=g)
     with torch.no_grad():
         tgt, _ = kag.leapfrog(T(q.x), T(q.v), T(q.m), k, dt, steps)

@@ -100,6 +100,19 @@ int kirin_set_launch(kirin_ctx *ctx, int32_t groups, int32_t n_split);
 int kirin_set_launch_table(kirin_ctx *ctx, int32_t n_entries, const int64_t *n_i_max,
                            const int32_t *groups, const int32_t *n_split);
 
+/* The kinds of force call that each have their own launch table: the full
+ * evaluation (acc, jerk, pot), acceleration and potential only (the leapfrog
+ * and kirin_accel_dev), and the adjoint (kirin_accel_adjoint_dev and the
+ * reverse leapfrog).  Their pair costs differ (about 33, 19 and 40 FP32
+ * operations), so do their best shapes. */
+typedef enum { KIRIN_CALL_FORCES = 0, KIRIN_CALL_ACC_POT = 1, KIRIN_CALL_ADJOINT = 2 } kirin_call_kind;
+
+/* kirin_set_launch_table / kirin_get_launch for one kind of call.
+ * Errors: EINVAL (unknown kind, bad entries). */
+int kirin_set_launch_table_for(kirin_ctx *ctx, int32_t kind, int32_t n_entries, const int64_t *n_i_max,
+                               const int32_t *groups, const int32_t *n_split);
+int kirin_get_launch_for(kirin_ctx *ctx, int32_t kind, int64_t n_i, int32_t *groups, int32_t *n_split);
+
 /* The shape that a force call for n_i i-particles would use now.  groups = 0
  * names the tiny-block kernel, which serves automatic mixed-precision calls
  * with n_i <= 8 (and n_j <= 512 x the SM count): n_split CTAs each stage a

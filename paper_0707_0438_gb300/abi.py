@@ -26,6 +26,11 @@ KIRIN_ETIMEOUT = -5
 KIRIN_ESTATE = -6
 KIRIN_FP64 = 0
 KIRIN_MIXED = 1
+# kirin_call_kind: the force calls that each have their own launch table
+KIRIN_CALL_FORCES = 0
+KIRIN_CALL_ACC_POT = 1
+KIRIN_CALL_ADJOINT = 2
+CALL_KINDS = {"forces": KIRIN_CALL_FORCES, "acc_pot": KIRIN_CALL_ACC_POT, "adjoint": KIRIN_CALL_ADJOINT}
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kirin.h")
 
@@ -57,6 +62,8 @@ _SIGS = {
     "kirin_set_params": (ctypes.c_int, [_P, _D, _D, _D, _I32]),
     "kirin_set_stream": (ctypes.c_int, [_P, _P]),
     "kirin_set_launch": (ctypes.c_int, [_P, _I32, _I32]),
+    "kirin_set_launch_table_for": (ctypes.c_int, [_P, _I32, _I32, _PI64, _PI32, _PI32]),
+    "kirin_get_launch_for": (ctypes.c_int, [_P, _I32, _I64, _PI32, _PI32]),
     "kirin_get_launch": (ctypes.c_int, [_P, _I64, _PI32, _PI32]),
     "kirin_set_launch_table": (ctypes.c_int, [_P, _I32, _PI64, _PI32, _PI32]),
     "kirin_set_j_particles": (ctypes.c_int, [_P, _I64, _I64, _PD, _PD, _PD, _PD, _PD, _PD]),
@@ -220,19 +227,20 @@ class Kirin:
     def set_launch(self, groups=0, n_split=0):
         self._check(self.lib.kirin_set_launch(self.ctx, int(groups), int(n_split)), "kirin_set_launch")
 
-    def set_launch_table(self, entries):
-        """entries: [(n_i_max, groups, n_split), ...] ascending in n_i_max; [] clears the table."""
+    def set_launch_table(self, entries, kind=KIRIN_CALL_FORCES):
+        """entries: [(n_i_max, groups, n_split), ...] ascending in n_i_max; [] clears the table.
+        kind: which force calls it serves (KIRIN_CALL_FORCES, _ACC_POT or _ADJOINT)."""
         ni = np.ascontiguousarray([e[0] for e in entries], dtype=np.int64)
         gr = np.ascontiguousarray([e[1] for e in entries], dtype=np.int32)
         sp = np.ascontiguousarray([e[2] for e in entries], dtype=np.int32)
-        self._check(self.lib.kirin_set_launch_table(self.ctx, len(entries), ni.ctypes.data_as(_PI64),
-                                                    gr.ctypes.data_as(_PI32), sp.ctypes.data_as(_PI32)),
-                    "kirin_set_launch_table")
+        self._check(self.lib.kirin_set_launch_table_for(self.ctx, int(kind), len(entries), ni.ctypes.data_as(_PI64),
+                                                        gr.ctypes.data_as(_PI32), sp.ctypes.data_as(_PI32)),
+                    "kirin_set_launch_table_for")
 
-    def get_launch(self, n_i):
+    def get_launch(self, n_i, kind=KIRIN_CALL_FORCES):
         g, s = ctypes.c_int32(), ctypes.c_int32()
-        self._check(self.lib.kirin_get_launch(self.ctx, int(n_i), ctypes.byref(g), ctypes.byref(s)),
-                    "kirin_get_launch")
+        self._check(self.lib.kirin_get_launch_for(self.ctx, int(kind), int(n_i), ctypes.byref(g), ctypes.byref(s)),
+                    "kirin_get_launch_for")
         return g.value, s.value
 
     def query(self):

@@ -14,7 +14,7 @@ import os
 
 import numpy as np
 
-from .abi import Kirin
+from .abi import CALL_KINDS, KIRIN_CALL_ACC_POT, KIRIN_CALL_ADJOINT, Kirin
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "kirin_gb300", "launch_table.json")
 # Tables measured on this project's GPUs (python -m paper_0707_0438_gb300.autotune --n N --out FILE).
@@ -150,16 +150,78 @@ def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, d
     return entries
 
 
+def _key(device_name: str, precision: str, n_j: int, kind: str = "forces") -> str:
+    base = f"{device_name}|{precision}|{n_j}"
+    return base if kind == "forces" else f"{base}|{kind}"
+
+
+def tune_full(k: Kirin, m, x, kind: str, reps: int = 3, device_name: str = "", cache: str | None = DEFAULT_CACHE,
+              precision: str = "mixed"):
+    """Time launch shapes of full evaluations (every particle an i) of the acceleration-and-potential
+    call ("acc_pot", as the leapfrog makes) or of the adjoint ("adjoint") for the particles (m, x) on
+    the device, and install the best as that kind's table; returns [(n_j, groups, n_split, seconds)]."""
+    import torch
+
+    n_j = int(m.shape[0])
+    key = _key(device_name, precision, n_j, kind)
+    if cache and os.path.exists(cache):
+        try:
+            table = json.load(open(cache)).get(key)
+        except (OSError, ValueError):
+            table = None
+        if table:
+            k.set_launch_table([tuple(e[:3]) for e in table], CALL_KINDS[kind])
+            return table
+    acc = torch.empty_like(x)
+    pot = torch.empty_like(m)
+    g = torch.randn_like(x)
+    gm = torch.zeros_like(m)
+    if kind == "acc_pot":
+        call = lambda: k.accel_dev(m, x, acc, pot)
+    elif kind == "adjoint":
+        call = lambda: k.accel_adjoint_dev(m, x, g, acc, gm)
+    else:
+        raise ValueError(f"kind must be acc_pot or adjoint, not {kind!r}")
+    ntiles = (n_j + 127) // 128
+    best = None
+    for groups in (1, 2, 4, 8):
+        for n_split in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64):
+            if n_split > ntiles:
+                continue
+            k.set_launch(groups, n_split)
+            t = _seconds_per_call(k, call, reps, torch)
+            if best is None or t < best[3]:
+                best = (n_j, groups, n_split, t)
+    k.set_launch(0, 0)
+    k.sync()
+    entries = [tuple(best)]
+    k.set_launch_table([e[:3] for e in entries], CALL_KINDS[kind])
+    if cache:
+        os.makedirs(os.path.dirname(cache) or ".", exist_ok=True)
+        try:
+            data = json.load(open(cache)) if os.path.exists(cache) else {}
+        except (OSError, ValueError):
+            data = {}
+        data[key] = entries
+        with open(cache, "w") as f:
+            json.dump(data, f)
+    return entries
+
+
 def install(k: Kirin, n_j: int, device_name: str, precision: str = "mixed", path: str = PACKAGED) -> bool:
-    """Install a stored table for this GPU, precision and n_j, if there is one."""
+    """Install the stored tables for this GPU, precision and n_j, one per kind of call that has one;
+    returns whether the table of full (acc, jerk, pot) calls was among them."""
     try:
-        table = json.load(open(path)).get(f"{device_name}|{precision}|{n_j}")
+        data = json.load(open(path))
     except (OSError, ValueError):
         return False
-    if not table:
-        return False
-    k.set_launch_table([tuple(e[:3]) for e in table])
-    return True
+    found = False
+    for kind, code in CALL_KINDS.items():
+        table = data.get(_key(device_name, precision, n_j, kind))
+        if table:
+            k.set_launch_table([tuple(e[:3]) for e in table], code)
+            found = found or kind == "forces"
+    return found
 
 
 def main(argv=None):
@@ -170,20 +232,29 @@ def main(argv=None):
     from . import workloads
     ap = argparse.ArgumentParser(description="time launch shapes and store the winners")
     ap.add_argument("--n", type=int, nargs="+", default=[1 << 20, 65536])
+    ap.add_argument("--kinds", nargs="+", default=["forces"], choices=sorted(CALL_KINDS))
     ap.add_argument("--out", default=PACKAGED)
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
     name = torch.cuda.get_device_name(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     for n in args.n:
         p = workloads.config_large(n)
         k = Kirin(n, p.eps, stream=torch.cuda.current_stream().cuda_stream)
         k.set_j_particles(p.m, p.x, p.v)
-        if os.path.exists(args.out):  # re-time: drop a stored entry for this key first
-            data = json.load(open(args.out))
-            data.pop(f"{name}|mixed|{n}", None)
-            json.dump(data, open(args.out, "w"), indent=0)
-        entries = tune(k, n, reps=args.reps, device_name=name, cache=args.out)
-        print(n, [(e[0], e[1], e[2], round(n * min(e[0], n) / e[3] / 1e9, 1)) for e in entries], flush=True)
+        for kind in args.kinds:
+            if os.path.exists(args.out):  # re-time: drop a stored entry for this key first
+                data = json.load(open(args.out))
+                data.pop(_key(name, "mixed", n, kind), None)
+                json.dump(data, open(args.out, "w"), indent=0)
+            if kind == "forces":
+                entries = tune(k, n, reps=args.reps, device_name=name, cache=args.out)
+            else:
+                m = torch.tensor(p.m, dtype=torch.float64, device=dev)
+                x = torch.tensor(p.x, dtype=torch.float64, device=dev)
+                entries = tune_full(k, m, x, kind, reps=args.reps, device_name=name, cache=args.out)
+            print(n, kind, [(e[0], e[1], e[2], round(n * min(e[0], n) / e[3] / 1e9, 1)) for e in entries],
+                  flush=True)
         k.close()
 
 

@@ -80,11 +80,12 @@ struct kirin_ctx {
     // launch-shape override (0 = automatic), tuned table and occupancy cache
     int fix_groups = 0, fix_split = 0;
     static constexpr int MAX_TABLE = 64;
-    int table_n = 0;
-    int64_t table_ni[MAX_TABLE] = {};   // entry k covers n_i <= table_ni[k] (ascending)
-    int32_t table_groups[MAX_TABLE] = {};
-    int32_t table_split[MAX_TABLE] = {};
-    int table_prec = -1;                // the table applies to this precision, full force mode
+    static constexpr int N_KINDS = 3;   // kirin_call_kind: acc+jerk+pot, acc+pot, adjoint
+    int table_n[N_KINDS] = {};
+    int64_t table_ni[N_KINDS][MAX_TABLE] = {};   // entry k covers n_i <= table_ni[k] (ascending)
+    int32_t table_groups[N_KINDS][MAX_TABLE] = {};
+    int32_t table_split[N_KINDS][MAX_TABLE] = {};
+    int table_prec[N_KINDS] = {-1, -1, -1};      // each table applies to the precision it was set for
     int occ[2][N_MODES][2][4] = {};  // [prec][mode][guard][log2 groups]
 
     // nearest-neighbour search of the host-pointer path (GRAPE's neighbour list)
@@ -139,6 +140,22 @@ int ilog2(int g) { return g == 1 ? 0 : g == 2 ? 1 : g == 4 ? 2 : 3; }
 
 bool guard_on(const kirin_ctx *c) { return c->eps == 0.0 || c->r_min > 0.0; }
 
+// The launch-table kind of a force mode (kirin_call_kind), -1 for none.
+int call_kind(int mode)
+{
+    switch (mode) {
+    case MODE_ACC_JERK_POT: return KIRIN_CALL_FORCES;
+    case MODE_ACC_POT: return KIRIN_CALL_ACC_POT;
+    case MODE_ADJOINT: return KIRIN_CALL_ADJOINT;
+    default: return -1;
+    }
+}
+
+int mode_of_kind(int kind)
+{
+    return kind == KIRIN_CALL_ACC_POT ? MODE_ACC_POT : kind == KIRIN_CALL_ADJOINT ? MODE_ADJOINT : MODE_ACC_JERK_POT;
+}
+
 // The j image the context's precision reads; packs write only that one.
 JMixed *img_m(const kirin_ctx *c) { return c->prec == KIRIN_MIXED ? c->jm : nullptr; }
 JF64 *img_d(const kirin_ctx *c) { return c->prec == KIRIN_MIXED ? nullptr : c->jd; }
@@ -170,10 +187,11 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
         const int ctas = std::max(1, std::min(2 * c->nsm, ntiles * TILE_J / 64));
         return Shape{0, ctas};
     }
-    if (c->table_n > 0 && prec == c->table_prec && mode == MODE_ACC_JERK_POT) {
-        for (int k = 0; k < c->table_n; ++k)
-            if (n_i <= c->table_ni[k])
-                return Shape{c->table_groups[k], std::min<int>(c->table_split[k], std::max(1, ntiles))};
+    const int kind = call_kind(mode);
+    if (kind >= 0 && c->table_n[kind] > 0 && prec == c->table_prec[kind]) {
+        for (int k = 0; k < c->table_n[kind]; ++k)
+            if (n_i <= c->table_ni[kind][k])
+                return Shape{c->table_groups[kind][k], std::min<int>(c->table_split[kind][k], std::max(1, ntiles))};
     }
     const int per_thread = prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1;
     Shape best{1, 1};
@@ -787,10 +805,10 @@ int kirin_set_launch(kirin_ctx *ctx, int32_t groups, int32_t n_split)
     return KIRIN_OK;
 }
 
-int kirin_set_launch_table(kirin_ctx *ctx, int32_t n_entries, const int64_t *n_i_max, const int32_t *groups,
-                           const int32_t *n_split)
+int kirin_set_launch_table_for(kirin_ctx *ctx, int32_t kind, int32_t n_entries, const int64_t *n_i_max,
+                               const int32_t *groups, const int32_t *n_split)
 {
-    if (!ctx || n_entries < 0 || n_entries > kirin_ctx::MAX_TABLE)
+    if (!ctx || kind < 0 || kind >= kirin_ctx::N_KINDS || n_entries < 0 || n_entries > kirin_ctx::MAX_TABLE)
         return KIRIN_EINVAL;
     if (n_entries > 0 && (!n_i_max || !groups || !n_split))
         return KIRIN_EINVAL;
@@ -801,27 +819,38 @@ int kirin_set_launch_table(kirin_ctx *ctx, int32_t n_entries, const int64_t *n_i
             return KIRIN_EINVAL;
     }
     for (int k = 0; k < n_entries; ++k) {
-        ctx->table_ni[k] = n_i_max[k];
-        ctx->table_groups[k] = groups[k];
-        ctx->table_split[k] = n_split[k];
+        ctx->table_ni[kind][k] = n_i_max[k];
+        ctx->table_groups[kind][k] = groups[k];
+        ctx->table_split[kind][k] = n_split[k];
     }
-    ctx->table_n = n_entries;
-    ctx->table_prec = ctx->prec;
+    ctx->table_n[kind] = n_entries;
+    ctx->table_prec[kind] = ctx->prec;
     return KIRIN_OK;
 }
 
-int kirin_get_launch(kirin_ctx *ctx, int64_t n_i, int32_t *groups, int32_t *n_split)
+int kirin_set_launch_table(kirin_ctx *ctx, int32_t n_entries, const int64_t *n_i_max, const int32_t *groups,
+                           const int32_t *n_split)
 {
-    if (!ctx || n_i < 0)
+    return kirin_set_launch_table_for(ctx, KIRIN_CALL_FORCES, n_entries, n_i_max, groups, n_split);
+}
+
+int kirin_get_launch_for(kirin_ctx *ctx, int32_t kind, int64_t n_i, int32_t *groups, int32_t *n_split)
+{
+    if (!ctx || n_i < 0 || kind < 0 || kind >= kirin_ctx::N_KINDS)
         return KIRIN_EINVAL;
     DeviceGuard dg(ctx->device);
     const int ntiles = (int)((std::max<int64_t>(ctx->n_j, 1) + TILE_J - 1) / TILE_J);
-    const Shape s = choose_shape(ctx, n_i, ntiles, ctx->prec, MODE_ACC_JERK_POT, guard_on(ctx));
+    const Shape s = choose_shape(ctx, n_i, ntiles, ctx->prec, mode_of_kind(kind), guard_on(ctx));
     if (groups)
         *groups = s.groups;
     if (n_split)
         *n_split = s.n_split;
     return KIRIN_OK;
+}
+
+int kirin_get_launch(kirin_ctx *ctx, int64_t n_i, int32_t *groups, int32_t *n_split)
+{
+    return kirin_get_launch_for(ctx, KIRIN_CALL_FORCES, n_i, groups, n_split);
 }
 
 int kirin_set_j_particles(kirin_ctx *ctx, int64_t first, int64_t n, const double *m, const double *x,

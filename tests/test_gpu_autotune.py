@@ -40,3 +40,37 @@ def test_launch_table_rejects_bad_entries(kirin_lib):
             with pytest.raises(abi.KirinError) as e:
                 k.set_launch_table(bad)
             assert e.value.code == abi.KIRIN_EINVAL
+
+
+def test_tables_per_call_kind(kirin_lib, tmp_path):
+    """Acceleration-and-potential and adjoint calls follow their own tables (tuned here for a small
+    sphere), the full force calls keep theirs, and the results do not change."""
+    import torch
+    dev = torch.device("cuda:0")
+    p = workloads.plummer(3000, 17, masses="lognormal", eps=0.01)
+    m = torch.tensor(p.m, device=dev)
+    x = torch.tensor(p.x, device=dev)
+    with abi.Kirin(p.n, p.eps, stream=torch.cuda.current_stream().cuda_stream) as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        forces = k.get_launch(p.n)
+        acc = torch.empty_like(x)
+        pot = torch.empty_like(m)
+        k.accel_dev(m, x, acc, pot)
+        k.sync()
+        before = acc.cpu().numpy()
+        e = autotune.tune_full(k, m, x, "acc_pot", reps=1, cache=str(tmp_path / "t.json"), device_name="test")
+        assert len(e) == 1 and e[0][0] == p.n
+        assert k.get_launch(p.n, abi.KIRIN_CALL_ACC_POT) == (e[0][1], min(e[0][2], (p.n + 127) // 128))
+        assert k.get_launch(p.n) == forces
+        k.set_launch_table([(p.n, 8, 3)], abi.KIRIN_CALL_ADJOINT)
+        assert k.get_launch(p.n, abi.KIRIN_CALL_ADJOINT) == (8, 3)
+        k.accel_dev(m, x, acc, pot)
+        k.sync()
+        ra, rp = oracle.acc_pot(p.m, p.x, p.eps)
+        assert np.median(np.linalg.norm(acc.cpu().numpy() - ra, axis=1) / np.linalg.norm(ra, axis=1)) <= 1e-6
+        assert np.max(np.abs(acc.cpu().numpy() - before)) <= 1e-6 * np.max(np.abs(before))
+        with pytest.raises(abi.KirinError):
+            k.set_launch_table([(p.n, 4, 2)], 3)
+        # a stored table for each kind is installed together with the others
+        assert autotune.install(k, p.n, "test", "mixed", path=str(tmp_path / "t.json")) is False
+        assert k.get_launch(p.n, abi.KIRIN_CALL_ACC_POT) == (e[0][1], min(e[0][2], (p.n + 127) // 128))
