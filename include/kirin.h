@@ -217,25 +217,27 @@ int kirin_hermite_init(kirin_ctx *ctx, double t, double eta, double dt_min, doub
  * *t_now receives t_next; *n_active the block size.  Either may be NULL. */
 int kirin_hermite_block_step(kirin_ctx *ctx, double t_end, double *t_now, int64_t *n_active);
 
-/* Block steps until every particle reached t_end (a multiple of dt_max) or
- * max_steps steps were taken (max_steps <= 0: no limit); *n_steps and
- * *n_pairs receive the number of block steps and the sum of n_active * n_j
- * over them (either may be NULL).
+/* Block steps until no block is due by t_end (then every particle has
+ * t_i <= t_end < t_i + dt_i, and all sit at t_end when it is a multiple of
+ * dt_max) or max_steps steps were taken (max_steps <= 0: no limit); *n_steps
+ * and *n_pairs receive the number of block steps and the sum of
+ * n_active * n_j over them (either may be NULL).
  *
  * With the device loop on (the default, see kirin_set_device_loop) the whole
  * run is one CUDA graph launch: a conditional WHILE node repeats two step
  * kernels (correction of the previous block and the minimum of t_i + dt_i;
  * selection of the next block and prediction of all j) and the force
- * evaluation (a SWITCH node picks one of a ladder of launches by block size);
- * the step kernels decide on the device whether another step follows.  The host then waits
- * once per call instead of once per block step.  The graph is built on the
- * first call and rebuilt only when n_j, the parameters or the launch shapes
- * change.  Results are those of the same steps taken one kirin_hermite_block_step
- * at a time, bit for bit when both use the same launch shape
- * (kirin_set_launch); the automatic shapes of the two paths can differ, and
- * so can the summation order.  Errors: KIRIN_ESTATE before kirin_hermite_init,
- * or when a block time does not advance (t + dt rounds to t in FP64; the run
- * stops there); KIRIN_ECUDA if the graph cannot be built or launched. */
+ * evaluation (a SWITCH node picks one of a ladder of launches by block
+ * size); the step kernels decide on the device whether another step
+ * follows.  The host then waits once per call instead of once per block
+ * step.  The graph is built on the first call and rebuilt only when n_j, the
+ * parameters or the launch shapes change.  Results are those of the same
+ * steps taken one kirin_hermite_block_step at a time, bit for bit when both
+ * use the same launch shape (kirin_set_launch); the automatic shapes of the
+ * two paths can differ, and so can the summation order.  Errors:
+ * KIRIN_ESTATE before kirin_hermite_init, or when a block time does not
+ * advance (t + dt rounds to t in FP64; the run stops there); KIRIN_ECUDA if
+ * the graph cannot be built or launched. */
 int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *n_steps,
                       double *n_pairs);
 
