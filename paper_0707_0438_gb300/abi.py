@@ -294,12 +294,17 @@ class Kirin:
         return self.get_acc_jerk_pot()
 
     def compute_forces_dev(self, i_list, acc, jerk, pot):
-        """Device arrays (torch): i_list int32 (n_i) or None, acc/jerk (n_i, 3) and pot (n_i) float64."""
+        """Device arrays (torch): i_list int32 (n_i) or None, acc/jerk (n_i, 3) and pot (n_i) float64.
+        An empty i_list does nothing (the C call reads a NULL list, which an empty tensor has, as all j)."""
+        if i_list is not None and i_list.numel() == 0:
+            return
         n_i = self.n_j if i_list is None else i_list.shape[0]
         self._check(self.lib.kirin_compute_forces_dev(self.ctx, int(n_i), _dev(i_list), _dev(acc), _dev(jerk),
                                                       _dev(pot)), "kirin_compute_forces_dev")
 
     def compute_forces_nn_dev(self, i_list, acc, jerk, pot, nn, nn_r2):
+        if i_list is not None and i_list.numel() == 0:
+            return
         n_i = self.n_j if i_list is None else i_list.shape[0]
         self._check(self.lib.kirin_compute_forces_nn_dev(self.ctx, int(n_i), _dev(i_list), _dev(acc), _dev(jerk),
                                                          _dev(pot), _dev(nn), _dev(nn_r2)),

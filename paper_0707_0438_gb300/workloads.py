@@ -142,6 +142,15 @@ def ensemble(n_clusters: int = 512, seed: int = 1004, n_lo: int = 256,
     return out, sizes
 
 
+def gaussian_cloud(n: int, seed, eps: float) -> Particles:
+    """n equal masses (sum 1) at standard-normal positions with velocities 0.1 N(0, 1): a cheap seeded
+    set for size and indexing tests far beyond the paper's N (no equilibrium implied)."""
+    rng = _rng(seed)
+    x = rng.standard_normal((n, 3))
+    v = 0.1 * rng.standard_normal((n, 3))
+    return Particles(np.full(n, 1.0 / n), x, v, eps=eps, meta={"kind": "gaussian cloud", "seed": seed})
+
+
 def config_adjoint(n: int = 16384) -> Particles:
     """Equal-mass Plummer sphere for the differentiable leapfrog, eps = 0.01, seed 1005."""
     return plummer(n, 1005, eps=0.01)

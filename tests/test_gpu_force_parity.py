@@ -82,6 +82,36 @@ def test_wide_j_split_reduction(kirin_lib, precision):
         k.set_launch(0, 0)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_empty_i_list(kirin_lib, precision):
+    """No active i: the host call returns empty results, the device call does nothing."""
+    import torch
+    p = workloads.plummer(500, 31, eps=0.01)
+    with _ctx(p, precision) as k:
+        acc, jerk, pot = k.forces(np.zeros(0, dtype=np.int32))
+        assert acc.shape == (0, 3) and jerk.shape == (0, 3) and pot.shape == (0,)
+        dev = torch.device("cuda:0")
+        out = torch.full((4, 3), 7.0, dtype=torch.float64, device=dev)
+        k.compute_forces_dev(torch.zeros(0, dtype=torch.int32, device=dev), out, out, out[:, 0])
+        k.sync()
+        assert bool((out == 7.0).all())
+        acc, _, _ = k.forces(np.array([3], dtype=np.int32))  # the context is still usable
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=np.array([3]))
+    assert np.allclose(acc, ref[0], rtol=1e-5)
+
+
+def test_maximum_size_sampled_parity(kirin_lib):
+    """N = 2^25 (about 15 GB on the device; image offsets and tile indices far beyond 2^24): 256
+    sampled i, the last particle among them, against the oracle over all j."""
+    p = workloads.gaussian_cloud(1 << 25, 2025, eps=1e-4)
+    il = workloads.i_subset(p.n, 256, seed=25)
+    il[-1] = p.n - 1
+    with _ctx(p, "mixed") as k:
+        got = k.forces(il)
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    assert_parity(got, ref, "mixed", "N=2^25")
+
+
 @pytest.mark.parametrize("n_i", [1, 2, 5, 8])
 def test_tiny_block_kernel(kirin_lib, n_i):
     """Blocks of at most 8 i go to the tiny-block kernel (j ranges per CTA, lanes over j, Sect. 3.2's
