@@ -255,11 +255,15 @@ def run_native(args):
                 evs[s][1].record(stream)
             kk.sync()
             torch.cuda.synchronize(dev)
-        return sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        per_step.clear()
+        per_step.extend(a.elapsed_time(b) for a, b in evs)
+        return sum(per_step) / 1e3
 
     # ---- headline: mixed precision, full evaluation ----
+    per_step = []
     with ClockSampler(local) as clk:
         t_mixed = timed(k, args.steps, args.warmup)
+    step_ms = {"best": min(per_step), "median": float(np.median(per_step)), "worst": max(per_step)}
     clocks = clk.summary()
     pairs_per_step = float(n) * float(n)
     value, t_max = replica_rate(t_mixed, pairs_per_step, args.steps, world, dist, dev)
@@ -386,7 +390,8 @@ def run_native(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "step_ms_rank0": step_ms, "higher_is_better": True,
+        "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 pair math, double-single positions, f64 results", "data": "synthetic",
         "config": dict(_config(n, "mixed"), launch={"groups": groups, "n_split": n_split,
                                                      "from": "tuned table" if tuned else "cost model"}),
