@@ -150,3 +150,26 @@ def test_device_loop_edge_sizes(kirin_lib, precision, n, eps, r_min):
     assert np.array_equal(auto_d[1]["t"], auto_h[1]["t"]) and np.array_equal(auto_d[1]["dt"], auto_h[1]["dt"])
     assert np.allclose(auto_d[1]["x"], auto_h[1]["x"], rtol=0, atol=1e-9 * max(1.0, np.abs(p.x).max()))
     assert np.all(np.isfinite(auto_d[1]["x"]))
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_device_loop_with_one_level_is_the_shared_run(kirin_lib, precision):
+    """dt_min = dt_max: every block is every particle, so the device-driven block loop must reproduce
+    kirin_hermite_shared_run bit for bit under one launch shape (two independent paths: the step
+    kernels' selection, prediction and correction against the predictor/corrector kernels)."""
+    p = workloads.plummer(3000, 1007, eps=1e-3)
+    dt = 2.0 ** -8
+    out = []
+    for shared in (True, False):
+        with abi.Kirin(p.n, p.eps, precision=precision) as k:
+            k.set_launch(2, 4)
+            k.set_j_particles(p.m, p.x, p.v)
+            k.hermite_init(0.0, dt_min=dt, dt_max=dt)
+            if shared:
+                k.hermite_shared_run(dt, 16)
+            else:
+                steps, pairs = k.hermite_run(16 * dt)
+                assert steps == 16 and pairs == 16.0 * p.n * p.n
+            out.append(k.get_state())
+    for key in ("x", "v", "a", "j", "t", "dt"):
+        assert np.array_equal(out[0][key], out[1][key]), key

@@ -338,6 +338,21 @@ def test_hermite_block_steps_conserve_energy_and_sync():
     assert sum(out["blocks"]) >= p.n
 
 
+def test_block_steps_with_one_level_are_shared_steps(monkeypatch):
+    """With dt_min = dt_max the block scheduler must select every particle at every step: the block
+    integrator then reduces exactly to the shared-step one (itself pinned on the Kepler orbit)."""
+    p = workloads.plummer(64, 19, eps=0.01)
+    dt = 2.0 ** -8
+    monkeypatch.setattr(hermite, "DT_MIN", dt)
+    monkeypatch.setattr(hermite, "DT_MAX", dt)
+    out = hermite.block_steps(p.m, p.x, p.v, p.eps, t_end=16 * dt)
+    x, v, a, j, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, dt, 16)
+    assert out["blocks"] == [p.n] * 16
+    assert np.all(out["t"] == 16 * dt) and np.all(out["dt"] == dt)
+    for got, ref in ((out["x"], x), (out["v"], v)):
+        assert np.array_equal(got, ref)
+
+
 def test_nearest_neighbour_matches_kdtree():
     p = workloads.plummer(500, 41)
     idx = np.arange(0, 500, 7)
