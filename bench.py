@@ -27,6 +27,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -163,6 +164,29 @@ def _calibrated_oracle_size(p, target_s):
     return int(max(64, min(p.n, target_s / per_i)))
 
 
+def _host_cpu() -> dict:
+    """The host CPU the oracle timing ran on: model (from /proc/cpuinfo) and the cores this process may use."""
+    model = platform.machine()
+    parts = {"0xd4f": "Neoverse V2", "0xd40": "Neoverse V1", "0xd0c": "Neoverse N1"}
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":", 1)[0].strip().lower()
+            if key == "model name":
+                model = line.split(":", 1)[1].strip()
+                break
+            if key == "cpu part":
+                part = line.split(":", 1)[1].strip()
+                model = f"{platform.machine()} {parts.get(part, 'CPU part ' + part)}"
+                break
+    except OSError:
+        pass
+    try:
+        affinity = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        affinity = os.cpu_count()
+    return {"cpu": model, "affinity_cores": affinity}
+
+
 def run_reference(args):
     """The CPU oracle on the host cores (the reference arm), bounded sample per step."""
     rank, world, _ = _dist()
@@ -187,8 +211,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(n, "oracle"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{k_i} i x {n} j per step (FP64 CPU oracle, OpenMP over i)"},
+        "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                              "sample": f"{k_i} i x {n} j per step (FP64 CPU oracle, OpenMP over i)"}, **_host_cpu()),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -354,8 +378,9 @@ def run_native(args):
             ("acc", metrics.rel_err_vec, res_mixed[0], ref[0]),
             ("jerk", metrics.rel_err_vec, res_mixed[1], ref[1]),
             ("pot", metrics.rel_err_scalar, res_mixed[2], ref[2]))}
-        cpu = {"value": k_i * float(n) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{k_i} random i x all {n} j, FP64 CPU oracle (OpenMP over i), {dt:.1f} s"}
+        cpu = dict({"value": k_i * float(n) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                    "sample": f"{k_i} random i x all {n} j, FP64 CPU oracle (OpenMP over i), {dt:.1f} s"},
+                   **_host_cpu())
         extra["mixed_vs_oracle_rel_err"] = errs
 
     # ---- roofline of the force kernel (FP32 CUDA-core pipe) ----
