@@ -90,6 +90,14 @@ def _seconds_per_call(k: Kirin, call, reps: int, torch) -> float:
     return ev[0].elapsed_time(ev[1]) / 1e3 / r
 
 
+def _pick(timed, tie: float = 0.005):
+    """The fastest (n_i, groups, n_split, seconds); among shapes within `tie` of it, the fewest splits
+    (each split adds a partial sum per i to write and reduce), then the fewest groups."""
+    t_best = min(e[3] for e in timed)
+    close = [e for e in timed if e[3] <= t_best * (1.0 + tie)]
+    return min(close, key=lambda e: (e[2], e[1], e[3]))
+
+
 def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, device_name: str = "",
          cache: str | None = DEFAULT_CACHE, precision: str = "mixed"):
     """Time launch shapes for the particles already set in `k` (n_j of them) and install
@@ -123,13 +131,12 @@ def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, d
         cands = _candidates(auto, ntiles, big=n_i >= 16 * nsm * 512)
         if quick:  # prune: the groups the cost model chose and its neighbours
             cands = [c for c in cands if c == auto or abs(np.log2(c[0]) - np.log2(auto[0])) <= 1]
-        best = None
+        timed = []
         for g, s in cands:
             k.set_launch(g, s)
-            t = _seconds_per_call(k, lambda: k.compute_forces_dev(il, acc, jerk, pot), reps, torch)
-            if best is None or t < best[3]:
-                best = (n_i, g, s, t)
-        table.append(best)
+            timed.append((n_i, g, s, _seconds_per_call(k, lambda: k.compute_forces_dev(il, acc, jerk, pot), reps,
+                                                       torch)))
+        table.append(_pick(timed))
     k.set_launch(0, 0)
     k.sync()
     # each timed size covers the sizes up to the geometric mean with the next one
@@ -183,15 +190,14 @@ def tune_full(k: Kirin, m, x, kind: str, reps: int = 3, device_name: str = "", c
     else:
         raise ValueError(f"kind must be acc_pot or adjoint, not {kind!r}")
     ntiles = (n_j + 127) // 128
-    best = None
+    timed = []
     for groups in (1, 2, 4, 8):
         for n_split in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64):
             if n_split > ntiles:
                 continue
             k.set_launch(groups, n_split)
-            t = _seconds_per_call(k, call, reps, torch)
-            if best is None or t < best[3]:
-                best = (n_j, groups, n_split, t)
+            timed.append((n_j, groups, n_split, _seconds_per_call(k, call, reps, torch)))
+    best = _pick(timed)
     k.set_launch(0, 0)
     k.sync()
     entries = [tuple(best)]
