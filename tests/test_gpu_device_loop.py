@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import hermite
-from paper_0707_0438_gb300 import abi, workloads
+from paper_0707_0438_gb300 import abi, metrics, workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -173,3 +173,26 @@ def test_device_loop_with_one_level_is_the_shared_run(kirin_lib, precision):
             out.append(k.get_state())
     for key in ("x", "v", "a", "j", "t", "dt"):
         assert np.array_equal(out[0][key], out[1][key]), key
+
+
+def test_device_loop_long_run(kirin_lib):
+    """Thousands of block steps in one graph launch (N = 2048 to t = 1/2, four dt_max periods): energy
+    conserved, every particle synchronised at t_end, the host loop's step count, and a second call
+    that continues from there."""
+    p = workloads.plummer(2048, 1008, eps=1e-3)
+    counts = {}
+    for device_loop in (True, False):
+        with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            e0 = sum(k.energy())
+            k.hermite_init(0.0)
+            k.set_device_loop(device_loop)
+            steps, _ = k.hermite_run(0.5)
+            st = k.get_state()
+            e1 = sum(k.energy())
+            more, _ = k.hermite_run(0.625)
+            counts[device_loop] = (steps, more)
+        assert np.all(st["t"] == 0.5)
+        assert abs(metrics.energy_error(e0, e1)) < 1e-5
+    assert counts[True][0] > 1000 and counts[True][1] > 0
+    assert abs(counts[True][0] - counts[False][0]) <= 0.01 * counts[False][0]
