@@ -23,6 +23,18 @@
 
 using namespace kirin;
 
+// Everything the instantiated graph bakes in: sizes, parameters, shapes and
+// the addresses of buffers that can be re-allocated.  Compared byte for byte
+// (the struct is zero-filled first, padding included).
+struct RunKey {
+    double par[6];
+    int64_t n_j, prec;
+    const void *partial;
+    int32_t n_classes;
+    int32_t class_max[MAX_SEL_CLASSES];
+    Shape shape[MAX_SEL_CLASSES];
+};
+
 struct kirin_ctx {
     int device = 0;
     int nsm = 0;
@@ -71,7 +83,7 @@ struct kirin_ctx {
     // run to t_end is one graph launch and one read-back.
     bool device_loop = true;
     cudaGraphExec_t run_exec = nullptr;
-    uint64_t run_key = 0;
+    RunKey run_key = {};          // what the graph was built for
     RunState *d_run = nullptr;      // run parameters, counters and barrier words (device)
     RunState *h_run = nullptr;      // pinned mirror
     int32_t *d_step_counts = nullptr;  // per-CTA list offsets and counts of the step kernels
@@ -428,29 +440,21 @@ RunPlan plan_run(kirin_ctx *c)
     return p;
 }
 
-uint64_t fnv1a(uint64_t h, const void *data, size_t bytes)
+RunKey run_key(const kirin_ctx *c, const RunPlan &p)
 {
-    const unsigned char *b = static_cast<const unsigned char *>(data);
-    for (size_t k = 0; k < bytes; ++k) {
-        h ^= b[k];
-        h *= 1099511628211ull;
-    }
-    return h;
-}
-
-// Everything the instantiated graph bakes in: sizes, parameters, shapes and
-// the addresses of buffers that can be re-allocated.
-uint64_t run_key(const kirin_ctx *c, const RunPlan &p)
-{
-    uint64_t h = 1469598103934665603ull;
+    RunKey k;
+    memset(&k, 0, sizeof(k));
     const double par[6] = {c->eps, c->G, c->r_min, c->eta, c->dt_min, c->dt_max};
-    h = fnv1a(h, par, sizeof(par));
-    const int64_t sizes[2] = {c->n_j, c->prec};
-    h = fnv1a(h, sizes, sizeof(sizes));
-    h = fnv1a(h, &c->d_partial, sizeof(c->d_partial));
-    h = fnv1a(h, p.class_max, sizeof(int32_t) * p.n_classes);
-    h = fnv1a(h, p.shape, sizeof(Shape) * p.n_classes);
-    return h | 1;  // never 0, the "no graph" key
+    memcpy(k.par, par, sizeof(par));
+    k.n_j = c->n_j;
+    k.prec = c->prec;
+    k.partial = c->d_partial;
+    k.n_classes = p.n_classes;
+    for (int q = 0; q < p.n_classes; ++q) {
+        k.class_max[q] = p.class_max[q];
+        k.shape[q] = p.shape[q];
+    }
+    return k;
 }
 
 // Capture onto the body graph with stream cs.
@@ -579,20 +583,19 @@ int hermite_run_device(kirin_ctx *c, double t_end, int64_t max_steps, int64_t *n
     int rc = ensure_partial(c, need);
     if (rc)
         return rc;
-    const uint64_t key = run_key(c, p);
-    if (!c->run_exec || key != c->run_key) {
+    const RunKey key = run_key(c, p);
+    if (!c->run_exec || memcmp(&key, &c->run_key, sizeof(key)) != 0) {
         if (c->run_exec) {
             CK(c, cudaStreamSynchronize(c->stream));
             cudaGraphExecDestroy(c->run_exec);
             c->run_exec = nullptr;
-            c->run_key = 0;
         }
         rc = build_run_graph(c, p, &c->run_exec);
         if (rc) {
             c->run_exec = nullptr;
             return rc;
         }
-        c->run_key = key;
+        memcpy(&c->run_key, &key, sizeof(key));
     }
     // the pinned mirror may still be the source or target of the last run's copies
     CK(c, cudaStreamSynchronize(c->stream));
