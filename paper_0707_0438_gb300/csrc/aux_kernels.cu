@@ -261,11 +261,31 @@ __global__ void k_hermite_init(int n, double t, const double *acc, const double 
     bdt[k] = quantise_down(0.01 * norm3(a) / norm3(j), dt_min, dt_max);
 }
 
+// Order-preserving map of doubles to unsigned keys (the sign bit set for
+// non-negative values, every bit flipped for negative ones; NaN the largest
+// key), so an unsigned atomic minimum finds the smallest end time whatever
+// its sign.  ~0 (the start value of a minimum) maps back to NaN: no block.
+__device__ __forceinline__ unsigned long long time_key(double d)
+{
+    if (d != d)
+        return ~0ull;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double key_time(unsigned long long k)
+{
+    if (k == ~0ull)
+        return __longlong_as_double(0x7ff8000000000000ll);
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
 // Block selection: t_next = min_i (t_i + dt_i) and the ordered list of the
 // i with t_i + dt_i == t_next (Sect. 3.1 block time-steps).  Three passes
-// over the particles, each fully parallel: an atomic minimum over the bit
-// patterns of the (non-negative) end times, per-CTA counts, then ordered
-// writes at offsets summed from the counts, so the list is in index order.
+// over the particles, each fully parallel: an atomic minimum over the keys
+// (time_key) of the end times, per-CTA counts, then ordered writes at
+// offsets summed from the counts, so the list is in index order.
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_ITEMS = 4;  // particles per thread, SEL_THREADS apart
 constexpr int SEL_PER_CTA = SEL_THREADS * SEL_ITEMS;
@@ -276,7 +296,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_min(int n, const double *__
 {
     unsigned long long mn = ~0ull;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        mn = min(mn, (unsigned long long)__double_as_longlong(bt[i] + bdt[i]));
+        mn = min(mn, time_key(bt[i] + bdt[i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -288,7 +308,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_count(int n, const double *
                                                            const double *__restrict__ bdt,
                                                            const unsigned long long *minw, int32_t *counts)
 {
-    const double tn = __longlong_as_double((long long)*minw);
+    const double tn = key_time(*minw);
     int total = 0;
 #pragma unroll
     for (int j = 0; j < SEL_ITEMS; ++j) {
@@ -308,7 +328,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *
 {
     __shared__ int warp_tot[SEL_THREADS / 32];
     __shared__ int red[SEL_THREADS];
-    const double tn = __longlong_as_double((long long)*minw);
+    const double tn = key_time(*minw);
     const bool due = tn <= t_end;
     // offset of this CTA: sum of the counts of the CTAs before it
     int part = 0;
@@ -549,7 +569,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_correct(const StepArgs A)
             end = correct_at((size_t)i, base + rank, t_prev, A.eta, A.dt_min, A.dt_max, 1, A.xp, A.vp, A.acc,
                              A.jerk, A.bx, A.bv, A.ba, A.bj, A.bt, A.bdt);
         if (i < c1)
-            mn = min(mn, (unsigned long long)__double_as_longlong(end));
+            mn = min(mn, time_key(end));
         base += all;
     }
     mn = cta_min_u64(mn);
@@ -570,7 +590,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
 {
     RunState *R = A.run;
     const long long steps0 = R->steps;
-    const double tn = __longlong_as_double((long long)R->minw[steps0 & 1]);
+    const double tn = key_time(R->minw[steps0 & 1]);
     const long long lim = R->max_steps;
     bool due = tn <= R->t_end && (lim <= 0 || steps0 < lim);
     const bool stall = due && steps0 > 0 && !(tn > R->t_last);

@@ -19,7 +19,7 @@ struct RunState {
     double pairs;                   // sum over those blocks of n_active * n_j
     double t_last;                  // time of the last block selected
     long long pending;              // size of the block forced but not yet corrected
-    unsigned long long minw[2];     // atomic minimum of t_i + dt_i, alternating by step parity
+    unsigned long long minw[2];     // atomic minimum of the keys of t_i + dt_i, alternating by step parity
     unsigned long long list_done;   // select kernel: (CTAs done) << 32 | members listed so far
 };
 

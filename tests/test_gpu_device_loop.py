@@ -196,3 +196,24 @@ def test_device_loop_long_run(kirin_lib):
         assert abs(metrics.energy_error(e0, e1)) < 1e-5
     assert counts[True][0] > 1000 and counts[True][1] > 0
     assert abs(counts[True][0] - counts[False][0]) <= 0.01 * counts[False][0]
+
+
+@pytest.mark.parametrize("device_loop", [True, False])
+def test_block_steps_from_a_negative_time(kirin_lib, device_loop):
+    """Block times are ordered as numbers, not as bit patterns: a run that starts at t = -1/8 reaches
+    t = 0 exactly as a run shifted to start at 0 reaches 1/8 (same schedule, same state)."""
+    p = workloads.plummer(1024, 1009, eps=1e-3)
+    results = []
+    for t0 in (-0.125, 0.0):
+        with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+            k.set_launch(2, 4)
+            k.set_j_particles(p.m, p.x, p.v)
+            k.hermite_init(t0)
+            k.set_device_loop(device_loop)
+            steps, pairs = k.hermite_run(t0 + 0.125)
+            st = k.get_state()
+        assert np.all(st["t"] == t0 + 0.125)
+        results.append((steps, st))
+    assert results[0][0] == results[1][0] > 0
+    for key in ("x", "v", "a", "j", "dt"):
+        assert np.array_equal(results[0][1][key], results[1][1][key]), key
