@@ -217,3 +217,40 @@ def test_block_steps_from_a_negative_time(kirin_lib, device_loop):
     assert results[0][0] == results[1][0] > 0
     for key in ("x", "v", "a", "j", "dt"):
         assert np.array_equal(results[0][1][key], results[1][1][key]), key
+
+
+def test_host_and_device_steps_interleave(kirin_lib):
+    """Host-driven block steps, then a device-driven run limited by max_steps, then host steps to the end
+    reproduce a pure host-driven run bit for bit (one launch shape): each driver leaves a state the other
+    continues from."""
+    p = workloads.plummer(2048, 1010, eps=1e-3)
+    t_end = 1.0 / 16
+
+    def ctx():
+        k = abi.Kirin(p.n, p.eps, precision="mixed")
+        k.set_launch(4, 4)
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        return k
+
+    with ctx() as k:
+        k.set_device_loop(False)
+        total, _ = k.hermite_run(t_end)
+        ref = k.get_state()
+    with ctx() as k:
+        done = 0
+        for _ in range(7):
+            _, n_act = k.hermite_block_step(t_end)
+            done += n_act > 0
+        k.set_device_loop(True)
+        steps, _ = k.hermite_run(t_end, 50)
+        done += steps
+        while True:
+            _, n_act = k.hermite_block_step(t_end)
+            if n_act == 0:
+                break
+            done += 1
+        st = k.get_state()
+    assert done == total and steps == 50
+    for key in STATE_KEYS:
+        assert np.array_equal(st[key], ref[key]), key
