@@ -100,6 +100,23 @@ def test_empty_i_list(kirin_lib, precision):
     assert np.allclose(acc, ref[0], rtol=1e-5)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_far_from_the_origin(kirin_lib, precision):
+    """A cluster at |x| ~ 1e4 with separations down to ~1e-3: the FP32 high parts of the positions are
+    2^-10 apart there, so only the double-single separation (high parts subtracted exactly, low parts
+    added) keeps the mixed forces within the stated tolerance."""
+    p = workloads.plummer(2000, 33, eps=1e-3)
+    x = p.x + np.array([1.0e4, -0.7e4, 0.3e4])
+    ref = oracle.acc_jerk_pot(p.m, x, p.v, p.eps)
+    with abi.Kirin(p.n, p.eps, precision=precision) as k:
+        k.set_j_particles(p.m, x, p.v)
+        got = k.forces()
+    assert_parity(got, ref, precision, "offset 1e4")
+    # and the forces are those of the cluster at the origin (translation invariance)
+    at0 = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps)
+    assert np.median(metrics.rel_err_vec(got[0], at0[0])) <= (1e-6 if precision == "mixed" else 1e-10)
+
+
 def test_maximum_size_sampled_parity(kirin_lib):
     """N = 2^25 (about 15 GB on the device; image offsets and tile indices far beyond 2^24): 256
     sampled i, the last particle among them, against the oracle over all j."""
