@@ -89,6 +89,29 @@ def test_hermite_block_run_energy_drift_mixed_vs_fp64(kirin_lib):
     assert abs(out["mixed"]) < 1e-5
 
 
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-7), ("fp64", 1e-11)])
+def test_device_leapfrog_is_time_reversible(kirin_lib, precision, tol):
+    """kirin_leapfrog_dev at N = 16384: 32 steps forward, velocities negated, 32 steps forward again
+    return the initial positions and velocities; the mixed forces differ only by rounding between the
+    two passes, the FP64 ones hardly at all."""
+    import torch
+    dev = torch.device("cuda:0")
+    p = workloads.config_adjoint(16384)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    with abi.Kirin(p.n, p.eps, precision=precision, stream=torch.cuda.current_stream().cuda_stream) as k:
+        m, x, v = T(p.m), T(p.x), T(p.v)
+        acc = torch.empty_like(x)
+        k.leapfrog_dev(m, x, v, acc, 1.0 / 128, 32)
+        moved = float((x - T(p.x)).abs().max())
+        v.neg_()
+        k.leapfrog_dev(m, x, v, acc, 1.0 / 128, 32, acc_valid=True)
+        k.sync()
+        dx = float((x - T(p.x)).abs().max())
+        dv = float((-v - T(p.v)).abs().max())
+    assert moved > 1e-3
+    assert dx <= tol * np.abs(p.x).max() and dv <= tol * 10 * np.abs(p.v).max(), (dx, dv)
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_accel_and_adjoint_dev(kirin_lib, precision):
     import torch

@@ -353,6 +353,18 @@ def test_block_steps_with_one_level_are_shared_steps(monkeypatch):
         assert np.array_equal(got, ref)
 
 
+def test_leapfrog_is_time_reversible():
+    """Kick-drift-kick is symmetric in time: n steps forward, velocities negated, n steps forward again
+    return the initial state up to rounding.  A wrong kick/drift order or half-kick weight breaks it."""
+    p = workloads.plummer(64, 23, eps=0.05)
+    xs, vs = leapfrog.trajectory(p.m, p.x, p.v, p.eps, 1.0 / 64, 32)
+    xb, vb = leapfrog.trajectory(p.m, xs[-1], -vs[-1], p.eps, 1.0 / 64, 32)
+    assert np.abs(xb[-1] - p.x).max() <= 1e-12 * np.abs(p.x).max()
+    assert np.abs(-vb[-1] - p.v).max() <= 1e-12 * np.abs(p.v).max()
+    # and the motion in between is real
+    assert np.abs(xs[-1] - p.x).max() > 1e-3
+
+
 def test_nearest_neighbour_matches_kdtree():
     p = workloads.plummer(500, 41)
     idx = np.arange(0, 500, 7)
