@@ -342,6 +342,22 @@ int kirin_batch_sync(kirin_batch *b);
 /* Accelerations of every particle of every cluster into a host array (n_total x 3). */
 int kirin_batch_accel(kirin_batch *b, double *acc);
 
+/* Work decomposition of the batched force launch (the batching is this
+ * library's; the paper evaluates one system at a time).  A work item is one
+ * cluster's block of 2 * 256 / groups i-particles (groups = 1, 2 or 4 j-groups
+ * per CTA: 512, 256 or 128 i) against a range of at most j_tiles tiles of 128
+ * j-particles of the same cluster (j_tiles = 0: the whole cluster).  A
+ * cluster whose j range is split gets its sums added in split order by the
+ * item that finishes last, so results are deterministic for a given
+ * decomposition; different decompositions differ by rounding only.  Default:
+ * groups 1, j_tiles 0.  Waits for the context's stream, rebuilds the work
+ * list and drops the captured leapfrog graph.  Errors: EINVAL (groups not 1,
+ * 2 or 4, j_tiles < 0, or the partial sums of the split clusters would exceed
+ * 1 GiB), ENOMEM, ECUDA; on error the previous decomposition stays. */
+int kirin_batch_set_launch(kirin_batch *b, int32_t groups, int32_t j_tiles);
+/* The current decomposition and its number of work items; any pointer may be NULL. */
+int kirin_batch_get_launch(const kirin_batch *b, int32_t *groups, int32_t *j_tiles, int32_t *n_items);
+
 /* ---- allocation-free evaluation ----
  * No counterpart in the paper.  For callers that cannot allocate device
  * memory when they need forces (inside another framework's memory pool that

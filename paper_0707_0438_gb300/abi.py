@@ -98,6 +98,8 @@ _SIGS = {
     "kirin_batch_leapfrog": (ctypes.c_int, [_P, _D, _I32, _I32]),
     "kirin_batch_sync": (ctypes.c_int, [_P]),
     "kirin_batch_accel": (ctypes.c_int, [_P, _PD]),
+    "kirin_batch_set_launch": (ctypes.c_int, [_P, _I32, _I32]),
+    "kirin_batch_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "kirin_forces_noalloc": (ctypes.c_int, [_I64, _P, _P, _P, _I64, _P, _D, _D, _D, _P, _P, _P, _P, _P]),
     "kirin_measure_fma_rate": (ctypes.c_int, [_I32, _I32, _PD]),
     "kirin_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -439,6 +441,17 @@ class KirinBatch:
         acc = np.empty((self.n_total, 3))
         self._check(self.lib.kirin_batch_accel(self.b, _dp(acc)), "kirin_batch_accel")
         return acc
+
+    def set_launch(self, groups, j_tiles):
+        """Work items: blocks of 512 / groups i against at most j_tiles tiles of 128 j (0: whole clusters)."""
+        self._check(self.lib.kirin_batch_set_launch(self.b, int(groups), int(j_tiles)), "kirin_batch_set_launch")
+
+    def get_launch(self):
+        """(groups, j_tiles, number of work items)."""
+        g, jt, ni = _I32(), _I32(), _I32()
+        self._check(self.lib.kirin_batch_get_launch(self.b, ctypes.byref(g), ctypes.byref(jt), ctypes.byref(ni)),
+                    "kirin_batch_get_launch")
+        return g.value, jt.value, ni.value
 
     def close(self):
         if getattr(self, "b", None):

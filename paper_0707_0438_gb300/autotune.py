@@ -6,6 +6,10 @@ the active block is small.  Here the candidates are timed on the device,
 through the C ABI, for a ladder of active-block sizes, and the winners become
 the context's launch table (kirin_set_launch_table).  Results are cached in a
 JSON file keyed by GPU name, SM count, precision and n_j.
+
+For batched ensembles, tune_batch times the work decompositions (i-block size
+through the j-groups per CTA, and the longest j range of a work item) on the
+ensemble itself and installs the fastest (kirin_batch_set_launch).
 """
 from __future__ import annotations
 
@@ -14,7 +18,7 @@ import os
 
 import numpy as np
 
-from .abi import CALL_KINDS, KIRIN_CALL_ACC_POT, KIRIN_CALL_ADJOINT, Kirin
+from .abi import CALL_KINDS, KIRIN_CALL_ACC_POT, KIRIN_CALL_ADJOINT, Kirin, KirinBatch, KirinError
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "kirin_gb300", "launch_table.json")
 # Tables measured on this project's GPUs (python -m paper_0707_0438_gb300.autotune --n N --out FILE).
@@ -228,6 +232,48 @@ def install(k: Kirin, n_j: int, device_name: str, precision: str = "mixed", path
             k.set_launch_table([tuple(e[:3]) for e in table], code)
             found = found or kind == "forces"
     return found
+
+
+# Batched ensembles: (j-groups per CTA, longest j range of a work item in tiles of 128; 0 = whole clusters).
+BATCH_CANDIDATES = tuple((g, jt) for g in (1, 2, 4) for jt in (0, 64, 32, 16))
+
+
+def _pick_batch(timed, tie: float = 0.005):
+    """The fastest (groups, j_tiles, seconds); among those within `tie` of it, whole clusters first (no
+    partial sums), then the longest j ranges, then the fewest groups."""
+    t_best = min(e[2] for e in timed)
+    close = [e for e in timed if e[2] <= t_best * (1.0 + tie)]
+    return min(close, key=lambda e: (e[1] != 0, -e[1], e[0], e[2]))
+
+
+def tune_batch(b: KirinBatch, m, x, v, dt: float = 1.0 / 256, steps: int = 2, reps: int = 2,
+               candidates=BATCH_CANDIDATES, tie: float = 0.005):
+    """Time the work decompositions of a batched ensemble by replaying a captured `steps`-step leapfrog
+    of it (the kick and drift kernels are the same for every candidate), install the fastest and put
+    the state (m, x, v) back.  Returns (groups, j_tiles, [(groups, j_tiles, seconds per step)]);
+    candidates whose partial sums would exceed the library's cap are skipped."""
+    import time
+
+    timed = []
+    for g, jt in candidates:
+        try:
+            b.set_launch(g, jt)
+        except KirinError:
+            continue
+        b.set_state(m, x, v)
+        b.leapfrog(dt, steps)  # first evaluation and graph capture
+        b.sync()
+        best = float("inf")
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            b.leapfrog(dt, steps)
+            b.sync()
+            best = min(best, time.perf_counter() - t0)
+        timed.append((g, jt, best / steps))
+    g, jt, _ = _pick_batch(timed, tie)
+    b.set_launch(g, jt)
+    b.set_state(m, x, v)
+    return g, jt, timed
 
 
 def main(argv=None):

@@ -3,10 +3,15 @@
 // for its treecode client, Sect. 4.3), with every force evaluation of every
 // cluster done by one persistent launch.
 //
-//  * Work items are (cluster, block of 512 i-particles); they are sorted by
-//    cost (cluster size) so that the largest go first, and CTAs (one or two
+//  * Work items are (cluster, block of i-particles, range of j tiles); they
+//    are sorted by cost so that the largest go first, and CTAs (one or two
 //    per SM) take them from an atomic counter until none are left; no CTA
-//    ever waits for another.
+//    ever waits for another.  The i-block size (512, 256 or 128: one, two or
+//    four j-groups per CTA) and the longest j range (whole clusters by
+//    default) are set per context; the autotuner times the choices.  When a
+//    cluster's j range is split, each item leaves its sums in a partial
+//    buffer and the item that completes the group adds the splits in order,
+//    so results do not depend on scheduling.
 //  * Each cluster's j image is padded to whole tiles with zero-mass records,
 //    so a work item streams exactly its own cluster through the same
 //    bulk-copy ring and the same pair arithmetic (acceleration and
@@ -33,12 +38,25 @@ using namespace kirin;
 
 namespace {
 
-constexpr int BATCH_I = 2 * FORCE_THREADS;  // i-particles per work item
 constexpr int BATCH_FLUSH_J = 256;
+constexpr int BATCH_NQ = 4;  // sums per i: acceleration (3) and potential
 
+// One unit of the work queue: j tiles [jt0, jt1) of a cluster against one
+// block of its i-particles.  group >= 0 when the cluster's j range is split
+// over several items: their sums meet in the partial buffer and the item
+// that finishes last adds them up (in split order, so the result does not
+// depend on which CTA comes last).
 struct Item {
     int32_t cluster;
     int32_t iblock;
+    int32_t jt0, jt1;
+    int32_t group;
+    int32_t split;
+};
+
+struct Group {
+    int32_t nsplit;
+    int32_t slot0;  // first partial slot (one per split)
 };
 
 struct BatchArgs {
@@ -51,20 +69,45 @@ struct BatchArgs {
     double G;
     double *acc;          // n_total x 3
     double *pot;          // n_total or null
+    const Group *groups;
+    unsigned *gcount;     // per group: items finished (set back to 0 by the last)
+    double *partial;      // [slot][BATCH_NQ][i per item]
     unsigned *counter;
     unsigned *err;
 };
 
-template <bool GUARD>
+// Final value of sum q (0-2: acceleration, 3: potential) of particle p.
+__device__ __forceinline__ void batch_store(const BatchArgs &A, size_t p, int q, double sum)
+{
+    if (q < 3)
+        A.acc[3 * p + q] = A.G * sum;
+    else if (A.pot)
+        A.pot[p] = -A.G * sum;
+}
+
+// GROUPS j-groups per CTA: an item holds 2 * 256 / GROUPS i-particles (two
+// per thread, as in the single-system kernel) and each tile of TILE_J j is
+// shared out among the groups, whose sums meet in shared memory at the end of
+// the item.
+template <int GROUPS, bool GUARD>
 __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArgs A)
 {
+    constexpr int GT = FORCE_THREADS / GROUPS;  // threads per j-group
+    constexpr int I_ITEM = 2 * GT;              // i-particles per item
+    constexpr int JG = TILE_J / GROUPS;         // j per group and tile
     constexpr uint32_t TILE_BYTES = TILE_J * sizeof(JMixed);
+    static_assert(GT >= 32, "a warp must read one j at a time (broadcast loads)");
+    static_assert((size_t)GROUPS * BATCH_NQ * I_ITEM * sizeof(float2) <= (size_t)STAGES * TILE_J * sizeof(JMixed),
+                  "cross-group reduction space");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     JMixed *tiles = reinterpret_cast<JMixed *>(smem_raw);
     __shared__ __align__(8) uint64_t bars[STAGES];
     __shared__ int item_s;
+    __shared__ int last_s;
 
     const int tid = threadIdx.x;
+    const int g = tid / GT;
+    const int s = tid - g * GT;
     if (tid == 0) {
 #pragma unroll
         for (int st = 0; st < STAGES; ++st)
@@ -80,16 +123,14 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
         const int it = item_s;
         if (it >= A.n_items)
             return;
-        const int c = A.items[it].cluster;
-        const int b = A.items[it].iblock;
-        const int off = A.off[c];
-        const int n_c = A.off[c + 1] - off;
-        const int poff = A.poff[c];
-        const int nt = (n_c + TILE_J - 1) / TILE_J;
-        const JMixed *__restrict__ J = A.jimg + poff;
-        const float eps2f = A.eps2[c];
+        const Item W = A.items[it];
+        const int off = A.off[W.cluster];
+        const int n_c = A.off[W.cluster + 1] - off;
+        const int nt = W.jt1 - W.jt0;
+        const JMixed *__restrict__ J = A.jimg + A.poff[W.cluster];
+        const float eps2f = A.eps2[W.cluster];
 
-        const int k0 = b * BATCH_I + tid, k1 = k0 + FORCE_THREADS;
+        const int k0 = W.iblock * I_ITEM + s, k1 = k0 + GT;
         const bool v0 = k0 < n_c, v1 = k1 < n_c;
         const IPair I = load_ipair(J + (v0 ? k0 : 0), J + (v1 ? k1 : 0), eps2f, 0.0f);
 
@@ -97,7 +138,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
             for (int st = 0; st < STAGES && st < nt; ++st) {
                 const int slot = (kt + st) % STAGES;
                 mbar_arrive_expect_tx(&bars[slot], TILE_BYTES);
-                bulk_g2s_hint(tiles + slot * TILE_J, J + (size_t)st * TILE_J, TILE_BYTES, &bars[slot], pol);
+                bulk_g2s_hint(tiles + slot * TILE_J, J + (size_t)(W.jt0 + st) * TILE_J, TILE_BYTES, &bars[slot],
+                              pol);
             }
         }
         Tile7 t;
@@ -113,20 +155,20 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
             const uint32_t par = (uint32_t)((kt + k) / STAGES) & 1u;
             const bool ok = mbar_wait_bounded(&bars[slot], par);
             if (ok) {
-                const JMixed *__restrict__ T = tiles + slot * TILE_J;
-                const int j0 = k * TILE_J;  // cluster-local index of T[0]
-                const bool mine = (v0 && (unsigned)(k0 - j0) < (unsigned)TILE_J) ||
-                                  (v1 && (unsigned)(k1 - j0) < (unsigned)TILE_J);
+                const JMixed *__restrict__ T = tiles + slot * TILE_J + g * JG;
+                const int j0 = (W.jt0 + k) * TILE_J + g * JG;  // cluster-local index of T[0]
+                const bool mine = (v0 && (unsigned)(k0 - j0) < (unsigned)JG) ||
+                                  (v1 && (unsigned)(k1 - j0) < (unsigned)JG);
                 if (eps2f != 0.f && __any_sync(0xffffffffu, mine)) {
 #pragma unroll 2
-                    for (int jj = 0; jj < TILE_J; ++jj)
+                    for (int jj = 0; jj < JG; ++jj)
                         pair<GUARD, MODE_ACC_POT, true>(T[jj], I, t, j0 + jj, v0 ? k0 : -1, v1 ? k1 : -1);
                 } else {
 #pragma unroll 4
-                    for (int jj = 0; jj < TILE_J; ++jj)
+                    for (int jj = 0; jj < JG; ++jj)
                         pair<GUARD, MODE_ACC_POT>(T[jj], I, t);
                 }
-                since += TILE_J;
+                since += JG;
                 if (since >= BATCH_FLUSH_J) {
                     fold<MODE_ACC_POT>(t, acc0, acc1);
                     since = 0;
@@ -138,7 +180,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
             }
             if (tid == 0 && k + STAGES < nt) {
                 mbar_arrive_expect_tx(&bars[slot], TILE_BYTES);
-                bulk_g2s_hint(tiles + slot * TILE_J, J + (size_t)(k + STAGES) * TILE_J, TILE_BYTES, &bars[slot], pol);
+                bulk_g2s_hint(tiles + slot * TILE_J, J + (size_t)(W.jt0 + k + STAGES) * TILE_J, TILE_BYTES,
+                              &bars[slot], pol);
             }
         }
         if (aborted) {
@@ -156,23 +199,80 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
         }
         kt += nt;
         fold<MODE_ACC_POT>(t, acc0, acc1);
-        if (v0) {
-            const size_t p = (size_t)off + k0;
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                A.acc[3 * p + q] = A.G * ((double)acc0.h[q] + (double)acc0.l[q]);
-            if (A.pot)
-                A.pot[p] = -A.G * ((double)acc0.h[6] + (double)acc0.l[6]);
+
+        // this item's sums: final values, or the partial slot of its split
+        double *part = nullptr;
+        Group grp{1, 0};
+        if (W.group >= 0) {
+            grp = A.groups[W.group];
+            part = A.partial + (size_t)(grp.slot0 + W.split) * BATCH_NQ * I_ITEM;
         }
-        if (v1) {
-            const size_t p = (size_t)off + k1;
+        auto emit = [&](int slot, int q, double sum) {
+            const int kk = W.iblock * I_ITEM + slot;
+            if (part)
+                part[q * I_ITEM + slot] = sum;
+            else if (kk < n_c)
+                batch_store(A, (size_t)off + kk, q, sum);
+        };
+        if (GROUPS == 1) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-                A.acc[3 * p + q] = A.G * ((double)acc1.h[q] + (double)acc1.l[q]);
-            if (A.pot)
-                A.pot[p] = -A.G * ((double)acc1.h[6] + (double)acc1.l[6]);
+            for (int q = 0; q < BATCH_NQ; ++q) {
+                const int c = q < 3 ? q : 6;
+                emit(s, q, (double)acc0.h[c] + (double)acc0.l[c]);
+                emit(s + GT, q, (double)acc1.h[c] + (double)acc1.l[c]);
+            }
+        } else {
+            // every tile is consumed and no copy is in flight: the ring is free
+            float2 *red = reinterpret_cast<float2 *>(smem_raw);  // [GROUPS][BATCH_NQ][I_ITEM] of (hi, lo)
+#pragma unroll
+            for (int q = 0; q < BATCH_NQ; ++q) {
+                const int c = q < 3 ? q : 6;
+                red[(g * BATCH_NQ + q) * I_ITEM + s] = make_float2(acc0.h[c], acc0.l[c]);
+                red[(g * BATCH_NQ + q) * I_ITEM + s + GT] = make_float2(acc1.h[c], acc1.l[c]);
+            }
+            __syncthreads();
+            for (int o = tid; o < BATCH_NQ * I_ITEM; o += FORCE_THREADS) {
+                const int q = o / I_ITEM;
+                const int slot = o - q * I_ITEM;
+                float2 v = red[q * I_ITEM + slot];
+                float hi = v.x, lo = v.y;
+#pragma unroll
+                for (int gg = 1; gg < GROUPS; ++gg) {
+                    v = red[(gg * BATCH_NQ + q) * I_ITEM + slot];
+                    two_sum(hi, lo, v.x);
+                    lo = __fadd_rn(lo, v.y);
+                }
+                emit(slot, q, (double)hi + (double)lo);
+            }
+            // the next item's copies refill this space after the barrier below
+            fence_proxy_async_smem();
         }
-        // item_s is rewritten only after every thread passed this barrier
+        if (part) {
+            // publish this split's sums; the last split of the group adds them all up
+            __threadfence();
+            __syncthreads();
+            if (tid == 0)
+                last_s = atomicAdd(&A.gcount[W.group], 1u) + 1u == (unsigned)grp.nsplit;
+            __syncthreads();
+            if (last_s) {
+                __threadfence();
+                const double *base = A.partial + (size_t)grp.slot0 * BATCH_NQ * I_ITEM;
+                for (int o = tid; o < BATCH_NQ * I_ITEM; o += FORCE_THREADS) {
+                    const int q = o / I_ITEM;
+                    const int slot = o - q * I_ITEM;
+                    const int kk = W.iblock * I_ITEM + slot;
+                    if (kk >= n_c)
+                        continue;
+                    double sum = 0.0;
+                    for (int sp = 0; sp < grp.nsplit; ++sp)
+                        sum += __ldcg(base + ((size_t)sp * BATCH_NQ + q) * I_ITEM + slot);
+                    batch_store(A, (size_t)off + kk, q, sum);
+                }
+                if (tid == 0)
+                    A.gcount[W.group] = 0u;
+            }
+        }
+        // item_s, last_s and the reduction space are rewritten only after every thread passed this barrier
         __syncthreads();
     }
 }
@@ -246,8 +346,17 @@ struct kirin_batch {
     float *d_eps2 = nullptr;
     double *m = nullptr, *x = nullptr, *v = nullptr, *a = nullptr;
     JMixed *jm = nullptr;
+    std::vector<int64_t> sizes;  // particles per cluster
+    // work decomposition (kirin_batch_set_launch): j-groups per CTA and the
+    // longest j range of an item in tiles (0: whole clusters)
+    int groups = 1;
+    int j_tiles = 0;
     Item *d_items = nullptr;
     int n_items = 0;
+    Group *d_groups = nullptr;
+    unsigned *d_gcount = nullptr;
+    double *d_partial = nullptr;
+    int n_groups = 0;
     unsigned *d_counter = nullptr, *d_err = nullptr, *h_err = nullptr;
     bool a_valid = false;
     bool have_state = false;
@@ -279,7 +388,7 @@ void batch_free(kirin_batch *b)
     if (b->gexec)
         cudaGraphExecDestroy(b->gexec);
     void *ptrs[] = {b->d_off, b->d_poff, b->d_img_idx, b->d_eps2, b->m, b->x, b->v, b->a, b->jm,
-                    b->d_items, b->d_counter, b->d_err};
+                    b->d_items, b->d_groups, b->d_gcount, b->d_partial, b->d_counter, b->d_err};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -287,6 +396,33 @@ void batch_free(kirin_batch *b)
         cudaFreeHost(b->h_err);
     if (b->own_stream && b->stream)
         cudaStreamDestroy(b->stream);
+}
+
+template <int GROUPS, bool GUARD>
+void launch_batch(const kirin_batch *b, const BatchArgs &A)
+{
+    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
+    k_batch_accel<GROUPS, GUARD><<<b->ctas, FORCE_THREADS, smem, b->stream>>>(A);
+}
+
+// The kernel instance of a decomposition, and its resident CTAs per SM.
+template <bool GUARD>
+int batch_occupancy(int groups)
+{
+    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
+    int occ = 0;
+    auto occ_of = [&](auto kern) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, FORCE_THREADS, smem);
+    };
+    if (groups == 4)
+        occ_of(k_batch_accel<4, GUARD>);
+    else if (groups == 2)
+        occ_of(k_batch_accel<2, GUARD>);
+    else
+        occ_of(k_batch_accel<1, GUARD>);
+    return occ;
 }
 
 cudaError_t enqueue_force(kirin_batch *b)
@@ -304,14 +440,113 @@ cudaError_t enqueue_force(kirin_batch *b)
     A.G = b->G;
     A.acc = b->a;
     A.pot = nullptr;
+    A.groups = b->d_groups;
+    A.gcount = b->d_gcount;
+    A.partial = b->d_partial;
     A.counter = b->d_counter;
     A.err = b->d_err;
-    const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
-    if (b->guard)
-        k_batch_accel<true><<<b->ctas, FORCE_THREADS, smem, b->stream>>>(A);
-    else
-        k_batch_accel<false><<<b->ctas, FORCE_THREADS, smem, b->stream>>>(A);
+    switch (b->groups * 2 + (b->guard ? 1 : 0)) {
+    case 2: launch_batch<1, false>(b, A); break;
+    case 3: launch_batch<1, true>(b, A); break;
+    case 4: launch_batch<2, false>(b, A); break;
+    case 5: launch_batch<2, true>(b, A); break;
+    case 8: launch_batch<4, false>(b, A); break;
+    case 9: launch_batch<4, true>(b, A); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
+}
+
+// Work items of a decomposition: i-blocks of 2 * 256 / groups particles
+// against j ranges of at most j_tiles tiles (0: the whole cluster), the
+// costliest first (longest j range, then largest cluster) so that the atomic
+// queue ends on short items.
+struct Plan {
+    std::vector<Item> items;
+    std::vector<Group> groups;
+    int64_t slots = 0;
+};
+
+Plan make_plan(const std::vector<int64_t> &nc, int groups, int j_tiles)
+{
+    Plan P;
+    const int i_item = 2 * FORCE_THREADS / groups;
+    for (int c = 0; c < (int)nc.size(); ++c) {
+        const int64_t nt = (nc[c] + TILE_J - 1) / TILE_J;
+        const int64_t S = (j_tiles > 0 && nt > j_tiles) ? (nt + j_tiles - 1) / j_tiles : 1;
+        for (int64_t ib = 0; ib * i_item < nc[c]; ++ib) {
+            int32_t grp = -1;
+            if (S > 1) {
+                grp = (int32_t)P.groups.size();
+                P.groups.push_back(Group{(int32_t)S, (int32_t)P.slots});
+                P.slots += S;
+            }
+            for (int64_t sp = 0; sp < S; ++sp)
+                P.items.push_back(Item{c, (int32_t)ib, (int32_t)(nt * sp / S), (int32_t)(nt * (sp + 1) / S), grp,
+                                       (int32_t)sp});
+        }
+    }
+    std::stable_sort(P.items.begin(), P.items.end(), [&](const Item &p, const Item &q) {
+        const int lp = p.jt1 - p.jt0, lq = q.jt1 - q.jt0;
+        if (lp != lq)
+            return lp > lq;
+        return nc[p.cluster] > nc[q.cluster];
+    });
+    return P;
+}
+
+// Partial sums of split clusters are capped at this many bytes.
+constexpr size_t BATCH_PARTIAL_MAX = (size_t)1 << 30;
+
+// Build and upload the work items of (groups, j_tiles); on failure the
+// context keeps its previous decomposition.
+int install_plan(kirin_batch *b, int groups, int j_tiles)
+{
+    const Plan P = make_plan(b->sizes, groups, j_tiles);
+    const int i_item = 2 * FORCE_THREADS / groups;
+    const size_t partial_bytes = (size_t)P.slots * BATCH_NQ * i_item * sizeof(double);
+    if (P.items.size() > (size_t)INT32_MAX || partial_bytes > BATCH_PARTIAL_MAX)
+        return KIRIN_EINVAL;
+    Item *items = nullptr;
+    Group *grps = nullptr;
+    unsigned *gcount = nullptr;
+    double *partial = nullptr;
+    bool ok = cudaMalloc((void **)&items, std::max<size_t>(P.items.size() * sizeof(Item), 16)) == cudaSuccess &&
+              cudaMalloc((void **)&grps, std::max<size_t>(P.groups.size() * sizeof(Group), 16)) == cudaSuccess &&
+              cudaMalloc((void **)&gcount, std::max<size_t>(P.groups.size() * sizeof(unsigned), 16)) == cudaSuccess &&
+              cudaMalloc((void **)&partial, std::max<size_t>(partial_bytes, 16)) == cudaSuccess;
+    if (ok && !P.items.empty())
+        ok = cudaMemcpy(items, P.items.data(), P.items.size() * sizeof(Item), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && !P.groups.empty())
+        ok = cudaMemcpy(grps, P.groups.data(), P.groups.size() * sizeof(Group), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(gcount, 0, std::max<size_t>(P.groups.size() * sizeof(unsigned), 16)) == cudaSuccess;
+    const int occ = b->guard ? batch_occupancy<true>(groups) : batch_occupancy<false>(groups);
+    if (!ok || occ < 1) {
+        cudaFree(items);
+        cudaFree(grps);
+        cudaFree(gcount);
+        cudaFree(partial);
+        cudaGetLastError();
+        return ok ? KIRIN_ECUDA : KIRIN_ENOMEM;
+    }
+    cudaFree(b->d_items);
+    cudaFree(b->d_groups);
+    cudaFree(b->d_gcount);
+    cudaFree(b->d_partial);
+    b->d_items = items;
+    b->d_groups = grps;
+    b->d_gcount = gcount;
+    b->d_partial = partial;
+    b->n_items = (int)P.items.size();
+    b->n_groups = (int)P.groups.size();
+    b->groups = groups;
+    b->j_tiles = j_tiles;
+    b->ctas = occ * b->nsm;
+    if (b->gexec) {  // the captured launches carry the old items
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    return KIRIN_OK;
 }
 
 cudaError_t enqueue_pack(kirin_batch *b)
@@ -353,6 +588,8 @@ int batch_errors(kirin_batch *b)
     if (!e)
         return KIRIN_OK;
     cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
+    if (b->n_groups)  // an aborted item never counted itself in
+        cudaMemsetAsync(b->d_gcount, 0, b->n_groups * sizeof(unsigned), b->stream);
     if (e & (ERR_TIMEOUT | ERR_DRAIN))
         return KIRIN_ETIMEOUT;
     if (e & ERR_NONFINITE)
@@ -396,7 +633,7 @@ int kirin_batch_create(kirin_batch **out, int32_t n_clusters, const int64_t *off
 
     std::vector<int32_t> off(n_clusters + 1), poff(n_clusters + 1), img_idx((size_t)n_total);
     std::vector<float> eps2(n_clusters);
-    std::vector<Item> items;
+    b->sizes.resize(n_clusters);
     poff[0] = 0;
     for (int c = 0; c < n_clusters; ++c) {
         off[c] = (int32_t)offsets[c];
@@ -407,16 +644,10 @@ int kirin_batch_create(kirin_batch **out, int32_t n_clusters, const int64_t *off
             b->guard = true;
         for (int64_t k = 0; k < nc; ++k)
             img_idx[(size_t)(offsets[c] + k)] = poff[c] + (int32_t)k;
-        for (int64_t ib = 0; ib * BATCH_I < nc; ++ib)
-            items.push_back(Item{c, (int32_t)ib});
+        b->sizes[c] = nc;
     }
     off[n_clusters] = (int32_t)n_total;
     b->n_img = std::max<int32_t>(poff[n_clusters], TILE_J);
-    // largest clusters first: their items cost the most (n_c pairs per i)
-    std::stable_sort(items.begin(), items.end(), [&](const Item &p, const Item &q) {
-        return offsets[p.cluster + 1] - offsets[p.cluster] > offsets[q.cluster + 1] - offsets[q.cluster];
-    });
-    b->n_items = (int)items.size();
 
     bool ok = true;
     auto dalloc = [&](void **p, size_t bytes) {
@@ -433,7 +664,6 @@ int kirin_batch_create(kirin_batch **out, int32_t n_clusters, const int64_t *off
     dalloc((void **)&b->v, 3 * n * sizeof(double));
     dalloc((void **)&b->a, 3 * n * sizeof(double));
     dalloc((void **)&b->jm, (size_t)b->n_img * sizeof(JMixed));
-    dalloc((void **)&b->d_items, items.size() * sizeof(Item));
     dalloc((void **)&b->d_counter, sizeof(unsigned));
     dalloc((void **)&b->d_err, sizeof(unsigned));
     if (ok && cudaMallocHost((void **)&b->h_err, sizeof(unsigned)) != cudaSuccess)
@@ -452,26 +682,14 @@ int kirin_batch_create(kirin_batch **out, int32_t n_clusters, const int64_t *off
              cudaMemcpy(b->d_poff, poff.data(), poff.size() * sizeof(int32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(b->d_img_idx, img_idx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(b->d_eps2, eps2.data(), eps2.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemset(b->d_err, 0, sizeof(unsigned)) == cudaSuccess;
     }
     if (ok) {
         k_fill_pad<<<(int)((b->n_img + 255) / 256), 256, 0, b->stream>>>((int)b->n_img, b->jm);
         ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(b->stream) == cudaSuccess;
     }
-    if (ok) {
-        int occ = 0;
-        const size_t smem = (size_t)STAGES * TILE_J * sizeof(JMixed);
-        if (smem > 48 * 1024) {
-            cudaFuncSetAttribute(k_batch_accel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(k_batch_accel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        }
-        if (b->guard)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_accel<true>, FORCE_THREADS, smem);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_accel<false>, FORCE_THREADS, smem);
-        b->ctas = std::max(1, occ) * b->nsm;
-    }
+    if (ok)  // default decomposition: blocks of 512 i against whole clusters
+        ok = install_plan(b, 1, 0) == KIRIN_OK;
     if (!ok) {
         cudaGetLastError();
         batch_free(b);
@@ -594,6 +812,29 @@ int kirin_batch_sync(kirin_batch *b)
         return KIRIN_EINVAL;
     DevGuard dg(b->device);
     return batch_errors(b);
+}
+
+int kirin_batch_set_launch(kirin_batch *b, int32_t groups, int32_t j_tiles)
+{
+    if (!b || (groups != 1 && groups != 2 && groups != 4) || j_tiles < 0)
+        return KIRIN_EINVAL;
+    DevGuard dg(b->device);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return KIRIN_ECUDA;
+    return install_plan(b, groups, j_tiles);
+}
+
+int kirin_batch_get_launch(const kirin_batch *b, int32_t *groups, int32_t *j_tiles, int32_t *n_items)
+{
+    if (!b)
+        return KIRIN_EINVAL;
+    if (groups)
+        *groups = b->groups;
+    if (j_tiles)
+        *j_tiles = b->j_tiles;
+    if (n_items)
+        *n_items = b->n_items;
+    return KIRIN_OK;
 }
 
 }  // extern "C"

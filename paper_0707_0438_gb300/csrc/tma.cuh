@@ -24,6 +24,14 @@ __device__ __forceinline__ void mbar_fence_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Order this thread's earlier direct (generic-proxy) accesses to shared
+// memory before later bulk-copy (async-proxy) writes to the same bytes: a
+// buffer that threads wrote or read must be fenced so before a copy refills it.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),

@@ -59,6 +59,8 @@ def test_null_context_is_rejected(lib):
     assert lib.kirin_predict(None, 0.0) == abi.KIRIN_EINVAL
     assert lib.kirin_sync(None) == abi.KIRIN_EINVAL
     assert lib.kirin_batch_leapfrog(None, 0.1, 1, 0) == abi.KIRIN_EINVAL
+    assert lib.kirin_batch_set_launch(None, 1, 0) == abi.KIRIN_EINVAL
+    assert lib.kirin_batch_get_launch(None, None, None, None) == abi.KIRIN_EINVAL
     assert lib.kirin_last_error(None).decode() == "no context"
 
 

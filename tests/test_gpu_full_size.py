@@ -12,13 +12,14 @@ pytestmark = pytest.mark.gpu
 
 
 def test_ensemble_full_size_sampled_parity(kirin_lib):
-    """512 clusters (N_c log-uniform in [256, 16384), eps = 1/N_c) in one batched launch: the largest,
-    the smallest and two random clusters against the oracle, every particle."""
+    """512 clusters (N_c log-uniform in [256, 16384), eps = 1/N_c) in one batched launch, in the
+    decomposition the tuner picks (as the benchmark does): the largest, the smallest and two random
+    clusters against the oracle, every particle."""
     clusters, sizes = workloads.ensemble()
     off = np.concatenate([[0], np.cumsum(sizes)])
+    m, x, v = (np.concatenate([getattr(c, a) for c in clusters]) for a in ("m", "x", "v"))
     b = abi.KirinBatch(off, [c.eps for c in clusters])
-    b.set_state(np.concatenate([c.m for c in clusters]), np.concatenate([c.x for c in clusters]),
-                np.concatenate([c.v for c in clusters]))
+    autotune.tune_batch(b, m, x, v)
     acc = b.accel()
     b.close()
     rng = np.random.default_rng(11)

@@ -192,3 +192,75 @@ def test_batched_leapfrog_matches_oracle_and_graph_is_identical(kirin_lib):
         a0, _ = oracle.acc_pot(cl.m, cl.x, cl.eps)
         bound = 10 * 0.5 * (steps * dt) ** 2 * 1e-5 * np.abs(a0).max()
         assert np.abs(xg[off[c]:off[c + 1]] - xs[-1]).max() <= bound
+
+
+def _ragged_ensemble(zero_eps: bool):
+    """Clusters of 1 ... 5000 particles: single particles, exact tiles, tiles plus one, several i-blocks,
+    several j tiles; with zero_eps one cluster has eps = 0 (the guarded pair arithmetic for the batch)."""
+    sizes = [1, 2, 127, 128, 129, 300, 513, 1000, 2049, 5000]
+    clusters = [workloads.plummer(n, (321, c), eps=1.0 / 128 if n > 1 else 0.01) for c, n in enumerate(sizes)]
+    if zero_eps:
+        clusters[6].eps = 0.0
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    m = np.concatenate([c.m for c in clusters])
+    x = np.concatenate([c.x for c in clusters])
+    v = np.concatenate([c.v for c in clusters])
+    return clusters, off, m, x, v
+
+
+@pytest.mark.parametrize("zero_eps", [False, True])
+def test_batched_decompositions_match_oracle(kirin_lib, zero_eps):
+    """Every work decomposition (512, 256 or 128 i per item; whole clusters or j ranges of 1, 2, 3 or
+    16 tiles, which splits every cluster with more than that many tiles) against the oracle, and the
+    same decomposition twice bit for bit (the split sums are added in a fixed order)."""
+    clusters, off, m, x, v = _ragged_ensemble(zero_eps)
+    refs = [oracle.acc_pot(cl.m, cl.x, cl.eps)[0] for cl in clusters]  # eps = 0: no coincident pairs here
+    b = abi.KirinBatch(off, [c.eps for c in clusters])
+    assert b.get_launch()[:2] == (1, 0)
+    for bad in ((3, 0), (8, 0), (1, -1)):
+        with pytest.raises(abi.KirinError):
+            b.set_launch(*bad)
+    assert b.get_launch()[:2] == (1, 0)
+    for groups, j_tiles in ((1, 0), (2, 0), (4, 0), (1, 1), (2, 2), (4, 3), (1, 16), (4, 1)):
+        b.set_launch(groups, j_tiles)
+        assert b.get_launch()[:2] == (groups, j_tiles)
+        b.set_state(m, x, v)
+        acc = b.accel()
+        again = b.accel()
+        assert np.array_equal(acc, again), (groups, j_tiles)
+        for c, cl in enumerate(clusters):
+            if cl.n == 1:
+                assert np.all(acc[off[c]:off[c + 1]] == 0.0)
+                continue
+            e = metrics.rel_err_vec(acc[off[c]:off[c + 1]], refs[c])
+            assert np.median(e) <= 1e-6 and e.max() <= 1e-5, (groups, j_tiles, c, np.median(e), e.max())
+    b.close()
+
+
+def test_batched_split_leapfrog_graph_is_identical(kirin_lib):
+    """With split j ranges the captured graph replays the eager launches bit for bit."""
+    clusters, off, m, x, v = _ragged_ensemble(False)
+    finals = []
+    for use_graph in (False, True):
+        b = abi.KirinBatch(off, [c.eps for c in clusters])
+        b.set_launch(2, 2)
+        b.set_state(m, x, v)
+        b.leapfrog(1.0 / 256, 6, use_graph=use_graph)
+        b.leapfrog(1.0 / 256, 6, use_graph=use_graph)  # a replay of the captured graph
+        b.sync()
+        finals.append(b.get_state())
+        b.close()
+    assert np.array_equal(finals[0][0], finals[1][0]) and np.array_equal(finals[0][1], finals[1][1])
+
+
+def test_batch_tuner_installs_a_timed_decomposition(kirin_lib):
+    from paper_0707_0438_gb300 import autotune
+    clusters, off, m, x, v = _ragged_ensemble(False)
+    b = abi.KirinBatch(off, [c.eps for c in clusters])
+    g, jt, timed = autotune.tune_batch(b, m, x, v, candidates=((1, 0), (2, 0), (4, 4)))
+    assert {(e[0], e[1]) for e in timed} == {(1, 0), (2, 0), (4, 4)} and all(e[2] > 0 for e in timed)
+    assert (g, jt) in {(e[0], e[1]) for e in timed} and b.get_launch()[:2] == (g, jt)
+    acc = b.accel()  # the state was put back
+    b.close()
+    ra, _ = oracle.acc_pot(clusters[-1].m, clusters[-1].x, clusters[-1].eps)
+    assert metrics.rel_err_vec(acc[off[-2]:off[-1]], ra).max() <= 1e-5

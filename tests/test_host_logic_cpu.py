@@ -16,6 +16,17 @@ def test_pick_prefers_fewer_splits_within_the_tie():
     assert autotune._pick([(8, 8, 4, 1.0), (8, 2, 4, 1.001)])[1:3] == (2, 4)
 
 
+def test_pick_batch_prefers_whole_clusters_within_the_tie():
+    timed = [(1, 0, 1.004), (2, 0, 1.010), (1, 32, 1.000), (4, 16, 0.990), (2, 64, 0.994)]
+    # 4 x 16 is the fastest; 2 x 64 is within 0.5% and splits less; whole clusters are 1.4% slower
+    assert autotune._pick_batch(timed)[:2] == (2, 64)
+    assert autotune._pick_batch(timed, tie=0.0)[:2] == (4, 16)
+    # whole clusters win whenever they are within the tie, then fewer groups
+    assert autotune._pick_batch(timed, tie=0.02)[:2] == (1, 0)
+    assert autotune._pick_batch([(4, 0, 1.0), (1, 0, 1.001)])[:2] == (1, 0)
+    assert set(autotune.BATCH_CANDIDATES) >= {(1, 0), (2, 0), (4, 0)}
+
+
 def test_table_keys_per_call_kind():
     assert autotune._key("NVIDIA GB300", "mixed", 65536) == "NVIDIA GB300|mixed|65536"
     assert autotune._key("NVIDIA GB300", "mixed", 16384, "acc_pot") == "NVIDIA GB300|mixed|16384|acc_pot"
