@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
         I[p] = load_ipair(J + (idx[2 * p] >= 0 ? idx[2 * p] : 0), J + (idx[2 * p + 1] >= 0 ? idx[2 * p + 1] : 0),
                           eps2f, rmin2f);
     // the self pair is masked unless eps = 0 zeroes it anyway (in the adjoint,
-    // w = m_k g_j - m_j g_k would vanish only if the compiler kept both
-    // products rounded; a contracted multiply-add leaves ~u m g, times 1/eps^3)
+    // w = m_k g_j - m_j g_k is formed with a multiply-add, which leaves ~u m g
+    // for j = k instead of zero, times 1/eps^3)
     // (the neighbour search always excludes j = i by index)
     const bool need_mask = eps2f != 0.f || NN;
 

@@ -204,10 +204,11 @@ __device__ __forceinline__ void pair(const JMixed &J, const IPair &I, Tile7 &t, 
         const float2 mj = f2(q1.z, q1.w);
         const float2 gjx = f2(q3.z, q3.w), gjy = f2(q4.x, q4.y), gjz = f2(q4.z, q4.w);
         const float2 ri3 = __fmul2_rn(ri, ri2);
-        // w = m_k g_j - m_j g_k (the self pair is masked by the caller)
-        const float2 wx = __fadd2_rn(__fmul2_rn(I.mk, gjx), __fmul2_rn(mj, I.nvx));
-        const float2 wy = __fadd2_rn(__fmul2_rn(I.mk, gjy), __fmul2_rn(mj, I.nvy));
-        const float2 wz = __fadd2_rn(__fmul2_rn(I.mk, gjz), __fmul2_rn(mj, I.nvz));
+        // w = m_k g_j - m_j g_k, one rounding fewer with the multiply-add (the self pair, where the
+        // two products are equal, is masked by the caller or has r = 0 under the eps = 0 guard)
+        const float2 wx = __ffma2_rn(I.mk, gjx, __fmul2_rn(mj, I.nvx));
+        const float2 wy = __ffma2_rn(I.mk, gjy, __fmul2_rn(mj, I.nvy));
+        const float2 wz = __ffma2_rn(I.mk, gjz, __fmul2_rn(mj, I.nvz));
         float2 dw = __fmul2_rn(dx, wx);
         dw = __ffma2_rn(dy, wy, dw);
         dw = __ffma2_rn(dz, wz, dw);
