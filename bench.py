@@ -609,7 +609,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    # --particles: the same, for use under torchrun, whose own parser takes "--n" for a prefix of its options
+    ap.add_argument("--n", "--particles", dest="n", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", choices=["large", "small", "block", "ensemble", "adjoint"], default="large")
