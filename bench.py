@@ -393,7 +393,9 @@ def run_native(args):
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             tr = json.load(f).get("k_force_mixed", {})
-        if tr.get("source_sha") == _kernel_source_sha():
+        # the counters hold for the captured source, size and launch shape only
+        if (tr.get("source_sha") == _kernel_source_sha() and tr.get("n") == n
+                and tr.get("launch") == [groups, n_split]):
             traffic = tr.get("bytes_per_launch")
     except (OSError, ValueError):
         pass

@@ -1,0 +1,55 @@
+"""bench.py's native lines on the GPU at reduced sizes: every key of the output contract, the roofline,
+the host-buffer (end-to-end) figures with their byte counts, and the CPU oracle baseline."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(args):
+    r = subprocess.run([sys.executable, "bench.py"] + args, cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    return lines[0]
+
+
+def test_native_line_contract(kirin_lib):
+    n, steps = 65536, 3
+    line = _run(["--n", str(n), "--steps", str(steps), "--warmup", "3", "--cpu-seconds", "1"])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "clocks", "roofline",
+                "cpu_baseline"):
+        assert key in line, key
+    assert line["n_gpus"] == 1 and line["steps"] == steps and line["warmup"] == 3
+    assert line["value"] > 1e11 and line["ms_per_step"] > 0 and line["higher_is_better"] is True
+    assert line["scaling"] == "weak" and line["vs_baseline"] is None and line["data"] == "synthetic"
+    assert f"N={n}" in line["config"]["workload"]
+    assert line["gpu_launches"] >= 2 * steps
+    e2e = line["e2e"]
+    assert e2e["value"] > 0 and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == n * 7 * 8  # m, x, v in FP64
+    assert e2e["d2h_bytes_per_step"] == n * 7 * 8  # acc, jerk, pot in FP64
+    clk = line["clocks"]
+    assert clk["sm_max_mhz"] > 0 and isinstance(clk["reasons"], list)
+    roof = line["roofline"]
+    assert roof["bound"] == "alu" and roof["unit"] == "TFLOP/s" and roof["peak"] > 0
+    assert 0.1 < roof["frac"] < 1.2 and roof["achieved"] == pytest.approx(roof["frac"] * roof["peak"])
+    assert roof["traffic"] is None  # the stored counters are for the N = 2^20 launch only
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0 and cb["sample"]
+    err = line["mixed_vs_oracle_rel_err"]
+    assert err["acc"]["median"] <= 1e-6 and err["acc"]["max"] <= 1e-5 and err["pot"]["median"] <= 1e-6
+    assert line["fp64"]["mixed_speedup"] > 1.0
+
+
+def test_small_workload_line(kirin_lib):
+    line = _run(["--workload", "small", "--steps", "2", "--warmup", "3"])
+    assert line["value"] > 0 and line["steps"] == 2 and "N=1024" in line["config"]["workload"]
+    assert line["fp64"]["value"] > 0
