@@ -264,3 +264,22 @@ def test_batch_tuner_installs_a_timed_decomposition(kirin_lib):
     b.close()
     ra, _ = oracle.acc_pot(clusters[-1].m, clusters[-1].x, clusters[-1].eps)
     assert metrics.rel_err_vec(acc[off[-2]:off[-1]], ra).max() <= 1e-5
+
+
+def test_batch_with_empty_clusters(kirin_lib):
+    """Clusters of zero particles (repeated offsets) own no work items and leave their neighbours intact."""
+    a = workloads.plummer(5, (55, 1), eps=0.05)
+    b_ = workloads.plummer(300, (55, 2), eps=0.01)
+    off = np.array([0, 0, 5, 5, 305, 305])
+    eps = [0.1, a.eps, 0.1, b_.eps, 0.1]
+    m, x, v = (np.concatenate([getattr(a, k), getattr(b_, k)]) for k in ("m", "x", "v"))
+    b = abi.KirinBatch(off, eps)
+    for groups, j_tiles in ((1, 0), (4, 1)):
+        b.set_launch(groups, j_tiles)
+        b.set_state(m, x, v)
+        acc = b.accel()
+        for cl, lo, hi in ((a, 0, 5), (b_, 5, 305)):
+            ra, _ = oracle.acc_pot(cl.m, cl.x, cl.eps)
+            e = metrics.rel_err_vec(acc[lo:hi], ra)
+            assert np.median(e) <= 1e-6 and e.max() <= 1e-5, (groups, j_tiles, e.max())
+    b.close()
