@@ -21,6 +21,9 @@
  *    kirin_sync / kirin_get_* call on that context.
  *  - Units: any consistent set; G is a parameter (1 in the Henon units of
  *    Sect. 4).
+ *  - A context (or a batch) is used by one host thread at a time: calls on
+ *    the same context from several threads must be serialised by the caller.
+ *    Different contexts share nothing and may be driven concurrently.
  */
 #ifndef KIRIN_H
 #define KIRIN_H
