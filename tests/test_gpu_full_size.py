@@ -104,3 +104,32 @@ def test_adjoint_full_size_directional_derivative(kirin_lib):
     fd = (lp - lm) / (2 * h)
     assert np.isfinite(g_dir) and g_dir != 0.0
     assert abs(fd - g_dir) <= 1e-4 * abs(g_dir), (fd, g_dir)
+
+
+def test_adjoint_workload_calls_full_size_match_oracle(kirin_lib):
+    """The two force calls of the differentiable leapfrog at N = 16384 in the packaged launch shapes
+    (acc + pot: 1 j-group x 32 splits; adjoint: 4 x 8, as the benchmark runs them), mixed precision,
+    against the FP64 oracle for every particle."""
+    import torch
+    dev = torch.device("cuda:0")
+    p = workloads.config_adjoint(16384)
+    g = np.random.default_rng(21).standard_normal((p.n, 3))
+    m, x, gt = (torch.tensor(a, device=dev) for a in (p.m, p.x, g))
+    acc, gx = torch.empty_like(x), torch.empty_like(x)
+    pot, gm = torch.empty_like(m), torch.empty_like(m)
+    with abi.Kirin(p.n, p.eps, precision="mixed", stream=torch.cuda.current_stream().cuda_stream) as k:
+        autotune.install(k, p.n, torch.cuda.get_device_name(0), "mixed")
+        k.accel_dev(m, x, acc, pot)
+        k.accel_adjoint_dev(m, x, gt, gx, gm)
+        k.sync()
+    ra, rp = oracle.acc_pot(p.m, p.x, p.eps)
+    rgx, rgm = oracle.force_adjoint(p.m, p.x, g, p.eps)
+    e = metrics.rel_err_vec(acc.cpu().numpy(), ra)
+    assert np.median(e) <= 1e-6 and e.max() <= 1e-5, ("acc", np.median(e), e.max())
+    e = metrics.rel_err_scalar(pot.cpu().numpy(), rp)
+    assert np.median(e) <= 1e-6 and e.max() <= 1e-5, ("pot", np.median(e), e.max())
+    # random-sign sums over j: the median per particle, the worst against the gradient's RMS size
+    for name, got, ref in (("dL/dx", gx.cpu().numpy(), rgx), ("dL/dm", gm.cpu().numpy()[:, None], rgm[:, None])):
+        err = np.linalg.norm(got - ref, axis=1)
+        rms = np.sqrt(np.mean(np.sum(ref * ref, axis=1)))
+        assert np.median(err / np.linalg.norm(ref, axis=1)) <= 1e-6 and err.max() / rms <= 1e-5, name
