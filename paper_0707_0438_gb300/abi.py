@@ -458,6 +458,12 @@ class KirinBatch:
             self.lib.kirin_batch_destroy(self.b)
             self.b = None
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def __del__(self):
         try:
             self.close()

@@ -273,13 +273,13 @@ def test_batch_with_empty_clusters(kirin_lib):
     off = np.array([0, 0, 5, 5, 305, 305])
     eps = [0.1, a.eps, 0.1, b_.eps, 0.1]
     m, x, v = (np.concatenate([getattr(a, k), getattr(b_, k)]) for k in ("m", "x", "v"))
-    b = abi.KirinBatch(off, eps)
-    for groups, j_tiles in ((1, 0), (4, 1)):
-        b.set_launch(groups, j_tiles)
-        b.set_state(m, x, v)
-        acc = b.accel()
-        for cl, lo, hi in ((a, 0, 5), (b_, 5, 305)):
-            ra, _ = oracle.acc_pot(cl.m, cl.x, cl.eps)
-            e = metrics.rel_err_vec(acc[lo:hi], ra)
-            assert np.median(e) <= 1e-6 and e.max() <= 1e-5, (groups, j_tiles, e.max())
-    b.close()
+    with abi.KirinBatch(off, eps) as b:
+        for groups, j_tiles in ((1, 0), (4, 1)):
+            b.set_launch(groups, j_tiles)
+            b.set_state(m, x, v)
+            acc = b.accel()
+            for cl, lo, hi in ((a, 0, 5), (b_, 5, 305)):
+                ra, _ = oracle.acc_pot(cl.m, cl.x, cl.eps)
+                e = metrics.rel_err_vec(acc[lo:hi], ra)
+                assert np.median(e) <= 1e-6 and e.max() <= 1e-5, (groups, j_tiles, e.max())
+    assert b.b is None
