@@ -40,3 +40,40 @@ def test_bounded_wait_times_out_and_context_survives(kirin_lib):
         got = k.forces()
         assert_parity(got, oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps), "mixed")
         k.sync()  # the error flag was cleared when it was reported
+
+
+def test_contexts_and_batches_release_device_memory(kirin_lib):
+    """Create, use and destroy contexts and batches repeatedly (device-loop graphs, launch tables,
+    split partials, the neighbour buffers, batch work lists re-planned): the free device memory
+    returns to where it started."""
+    import torch
+    p = workloads.plummer(20000, 31, eps=1e-3)
+    sizes = np.array([300, 1000, 4000])
+    cl = [workloads.plummer(int(n), (31, c), eps=1.0 / n) for c, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    bm, bx, bv = (np.concatenate([getattr(c, a) for c in cl]) for a in ("m", "x", "v"))
+
+    def cycle():
+        with abi.Kirin(p.n, p.eps) as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            k.forces(workloads.i_subset(p.n, 100, seed=1))
+            k.set_nn(True)
+            k.forces(workloads.i_subset(p.n, 37, seed=2))
+            k.hermite_init(0.0)
+            k.hermite_run(1.0 / 512)
+        with abi.KirinBatch(off, [c.eps for c in cl]) as b:
+            b.set_state(bm, bx, bv)
+            for g, jt in ((2, 2), (4, 1), (1, 0)):
+                b.set_launch(g, jt)
+                b.accel()
+            b.leapfrog(1.0 / 256, 4)
+            b.sync()
+
+    cycle()  # first use: lazily loaded modules and the runtime's own pools
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(10):
+        cycle()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 <= 8 << 20, (free0 - free1) / 2**20  # MiB lost over ten cycles
