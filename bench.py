@@ -31,7 +31,6 @@ import platform
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np

@@ -18,7 +18,7 @@ import os
 
 import numpy as np
 
-from .abi import CALL_KINDS, KIRIN_CALL_ACC_POT, KIRIN_CALL_ADJOINT, Kirin, KirinBatch, KirinError
+from .abi import CALL_KINDS, Kirin, KirinBatch, KirinError
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "kirin_gb300", "launch_table.json")
 # Tables measured on this project's GPUs (python -m paper_0707_0438_gb300.autotune --n N --out FILE).
