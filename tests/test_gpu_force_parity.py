@@ -350,3 +350,25 @@ def test_large_workload_sampled_parity(kirin_lib):
         assert_parity(tuple(q[il] for q in full0), ref0, "mixed", "N=2^20 eps=0")
         k.set_params(p.eps, 1.0, 0.0, "fp64")
         assert_parity(k.forces(il), ref, "fp64", "N=2^20 fp64")
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_scaling_by_powers_of_two(kirin_lib, precision):
+    """x -> lam x, eps -> lam eps, m -> mu m, v -> nu v with powers of two scale every step of the
+    double-single and FP64 arithmetic exactly (lam^2 an even power of two for the reciprocal square
+    root): a -> mu a / lam^2, jerk -> mu nu jerk / lam^3, phi -> mu phi / lam, bit for bit, through
+    the split reduction of a small block and a full evaluation."""
+    p = workloads.plummer(3000, 4242, masses="lognormal", eps=1.0 / 256)
+    il = workloads.i_subset(p.n, 77, seed=8)
+    lam, mu, nu = 2.0 ** -3, 2.0 ** 5, 2.0 ** 2
+    out = []
+    for scale in (False, True):
+        m, x, v, eps = (mu * p.m, lam * p.x, nu * p.v, lam * p.eps) if scale else (p.m, p.x, p.v, p.eps)
+        with abi.Kirin(p.n, eps, precision=precision) as k:
+            k.set_j_particles(m, x, v)
+            out.append((k.forces(), k.forces(il)))
+    for got, ref in zip(out[1], out[0]):
+        a, j, f = ref
+        assert np.array_equal(got[0], mu / lam ** 2 * a)
+        assert np.array_equal(got[1], mu * nu / lam ** 3 * j)
+        assert np.array_equal(got[2], mu / lam * f)

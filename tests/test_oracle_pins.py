@@ -229,6 +229,26 @@ def test_translation_rotation_permutation_invariance():
     assert np.allclose(pot4, pot[perm], rtol=1e-14)
 
 
+def test_homogeneity_under_scaling():
+    """Dimensional homogeneity of Eq. 1 and its time derivative: x -> lam x, eps -> lam eps, m -> mu m,
+    v -> nu v, G -> g G give a -> g mu a / lam^2, phi -> g mu phi / lam, jerk -> g mu nu jerk / lam^3.
+    With powers of two every floating-point step scales exactly, so the oracle must reproduce the
+    scaling bit for bit; a wrong power of s, of the separation or of the mass anywhere breaks it."""
+    p = workloads.plummer(60, 808, masses="lognormal", eps=0.02)
+    a, j, f = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps)
+    for lam, mu, nu, g in ((2.0 ** -3, 2.0 ** 5, 2.0 ** 2, 1.0), (2.0 ** 4, 2.0 ** -7, 2.0 ** -3, 0.5)):
+        a2, j2, f2 = oracle.acc_jerk_pot(mu * p.m, lam * p.x, nu * p.v, lam * p.eps, G=g)
+        assert np.array_equal(a2, g * mu / lam ** 2 * a)
+        assert np.array_equal(f2, g * mu / lam * f)
+        assert np.array_equal(j2, g * mu * nu / lam ** 3 * j)
+    # a factor that is not a power of two: equal to rounding
+    lam, mu, nu = 1.7, 0.3, 2.9
+    a2, j2, f2 = oracle.acc_jerk_pot(mu * p.m, lam * p.x, nu * p.v, lam * p.eps)
+    assert np.allclose(a2, mu / lam ** 2 * a, rtol=1e-13, atol=0)
+    assert np.allclose(f2, mu / lam * f, rtol=1e-13, atol=0)
+    assert np.allclose(j2, mu * nu / lam ** 3 * j, rtol=1e-12, atol=1e-12 * np.abs(j).max())
+
+
 def test_i_subset_equals_full_rows():
     p = workloads.plummer(300, 8)
     acc, jerk, pot = oracle.acc_jerk_pot(p.m, p.x, p.v, 0.01)
