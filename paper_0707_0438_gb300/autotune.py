@@ -270,6 +270,8 @@ def tune_batch(b: KirinBatch, m, x, v, dt: float = 1.0 / 256, steps: int = 2, re
             b.sync()
             best = min(best, time.perf_counter() - t0)
         timed.append((g, jt, best / steps))
+    if not timed:
+        raise ValueError("tune_batch: no candidate decomposition could be installed")
     g, jt, _ = _pick_batch(timed, tie)
     b.set_launch(g, jt)
     b.set_state(m, x, v)
