@@ -345,6 +345,16 @@ int kirin_batch_sync(kirin_batch *b);
 /* Accelerations of every particle of every cluster into a host array (n_total x 3). */
 int kirin_batch_accel(kirin_batch *b, double *acc);
 
+/* Device-pointer twins of kirin_batch_set_state / _get_state / _accel: the
+ * same layouts as CUDA device arrays (FP64), enqueued on the batch's stream
+ * without synchronising.  Non-finite uploaded values and device errors are
+ * reported by the next kirin_batch_sync (ENONFINITE, ETIMEOUT).
+ * Errors here: EINVAL (NULL batch or array), ESTATE (accel before any
+ * state), ECUDA (a launch or copy failed to enqueue). */
+int kirin_batch_set_state_dev(kirin_batch *b, const double *m, const double *x, const double *v);
+int kirin_batch_get_state_dev(kirin_batch *b, double *x, double *v);
+int kirin_batch_accel_dev(kirin_batch *b, double *acc);
+
 /* Work decomposition of the batched force launch (the batching is this
  * library's; the paper evaluates one system at a time).  A work item is one
  * cluster's block of 2 * 256 / groups i-particles (groups = 1, 2 or 4 j-groups

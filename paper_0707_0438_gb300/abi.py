@@ -99,6 +99,9 @@ _SIGS = {
     "kirin_batch_sync": (ctypes.c_int, [_P]),
     "kirin_batch_accel": (ctypes.c_int, [_P, _PD]),
     "kirin_batch_set_launch": (ctypes.c_int, [_P, _I32, _I32]),
+    "kirin_batch_set_state_dev": (ctypes.c_int, [_P, _P, _P, _P]),
+    "kirin_batch_get_state_dev": (ctypes.c_int, [_P, _P, _P]),
+    "kirin_batch_accel_dev": (ctypes.c_int, [_P, _P]),
     "kirin_batch_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "kirin_forces_noalloc": (ctypes.c_int, [_I64, _P, _P, _P, _I64, _P, _D, _D, _D, _P, _P, _P, _P, _P]),
     "kirin_measure_fma_rate": (ctypes.c_int, [_I32, _I32, _PD]),
@@ -441,6 +444,29 @@ class KirinBatch:
         acc = np.empty((self.n_total, 3))
         self._check(self.lib.kirin_batch_accel(self.b, _dp(acc)), "kirin_batch_accel")
         return acc
+
+    def _dev_state(self, t, cols):
+        """Device pointer of a contiguous CUDA float64 tensor of n_total (x cols) entries."""
+        import torch
+        shape = (self.n_total,) if cols == 1 else (self.n_total, cols)
+        if t.dtype != torch.float64 or tuple(t.shape) != shape:
+            raise ValueError(f"expected a float64 CUDA tensor of shape {shape}")
+        return _dev(t)
+
+    def set_state_dev(self, m, x, v):
+        """State from CUDA tensors m (n_total,), x, v (n_total, 3); asynchronous on the batch's stream."""
+        self._check(self.lib.kirin_batch_set_state_dev(self.b, self._dev_state(m, 1), self._dev_state(x, 3),
+                                                       self._dev_state(v, 3)), "kirin_batch_set_state_dev")
+
+    def get_state_dev(self, x=None, v=None):
+        """Copy the positions and/or velocities into CUDA tensors (n_total, 3); asynchronous."""
+        self._check(self.lib.kirin_batch_get_state_dev(self.b, None if x is None else self._dev_state(x, 3),
+                                                       None if v is None else self._dev_state(v, 3)),
+                    "kirin_batch_get_state_dev")
+
+    def accel_dev(self, acc):
+        """Accelerations into a CUDA tensor (n_total, 3); asynchronous."""
+        self._check(self.lib.kirin_batch_accel_dev(self.b, self._dev_state(acc, 3)), "kirin_batch_accel_dev")
 
     def set_launch(self, groups, j_tiles):
         """Work items: blocks of 512 / groups i against at most j_tiles tiles of 128 j (0: whole clusters)."""

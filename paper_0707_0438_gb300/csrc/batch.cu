@@ -322,6 +322,26 @@ __global__ void k_kick(int n, double h, const double *__restrict__ a, double *v)
     v[p] += h * a[p];
 }
 
+// Device-to-device state upload with the finiteness check of the host path.
+__global__ void k_batch_scatter(int n, const double *__restrict__ m, const double *__restrict__ x,
+                                const double *__restrict__ v, double *bm, double *bx, double *bv, unsigned *err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n)
+        return;
+    bool fin = isfinite(m[k]);
+    bm[k] = m[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double xc = x[3 * (size_t)k + c], vc = v[3 * (size_t)k + c];
+        fin = fin && isfinite(xc) && isfinite(vc);
+        bx[3 * (size_t)k + c] = xc;
+        bv[3 * (size_t)k + c] = vc;
+    }
+    if (!fin)
+        atomicOr(err, ERR_NONFINITE);
+}
+
 __global__ void k_fill_pad(int n_img, JMixed *jm)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -760,6 +780,49 @@ int kirin_batch_accel(kirin_batch *b, double *acc)
         cudaSuccess)
         return KIRIN_ECUDA;
     return batch_errors(b);
+}
+
+int kirin_batch_set_state_dev(kirin_batch *b, const double *m, const double *x, const double *v)
+{
+    if (!b || !m || !x || !v)
+        return KIRIN_EINVAL;
+    DevGuard dg(b->device);
+    const int n = (int)b->n_total;
+    k_batch_scatter<<<(n + 255) / 256, 256, 0, b->stream>>>(n, m, x, v, b->m, b->x, b->v, b->d_err);
+    if (cudaGetLastError() != cudaSuccess)
+        return KIRIN_ECUDA;
+    b->a_valid = false;
+    b->have_state = true;
+    return KIRIN_OK;
+}
+
+int kirin_batch_get_state_dev(kirin_batch *b, double *x, double *v)
+{
+    if (!b)
+        return KIRIN_EINVAL;
+    DevGuard dg(b->device);
+    const size_t bytes = 3 * (size_t)b->n_total * sizeof(double);
+    if (x && cudaMemcpyAsync(x, b->x, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+        return KIRIN_ECUDA;
+    if (v && cudaMemcpyAsync(v, b->v, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+        return KIRIN_ECUDA;
+    return KIRIN_OK;
+}
+
+int kirin_batch_accel_dev(kirin_batch *b, double *acc)
+{
+    if (!b || !acc)
+        return KIRIN_EINVAL;
+    if (!b->have_state)
+        return KIRIN_ESTATE;
+    DevGuard dg(b->device);
+    if (enqueue_pack(b) != cudaSuccess || enqueue_force(b) != cudaSuccess)
+        return KIRIN_ECUDA;
+    b->a_valid = true;
+    if (cudaMemcpyAsync(acc, b->a, 3 * (size_t)b->n_total * sizeof(double), cudaMemcpyDeviceToDevice,
+                        b->stream) != cudaSuccess)
+        return KIRIN_ECUDA;
+    return KIRIN_OK;
 }
 
 int kirin_batch_leapfrog(kirin_batch *b, double dt, int32_t n_steps, int32_t use_graph)

@@ -60,6 +60,9 @@ def test_null_context_is_rejected(lib):
     assert lib.kirin_sync(None) == abi.KIRIN_EINVAL
     assert lib.kirin_batch_leapfrog(None, 0.1, 1, 0) == abi.KIRIN_EINVAL
     assert lib.kirin_batch_set_launch(None, 1, 0) == abi.KIRIN_EINVAL
+    assert lib.kirin_batch_set_state_dev(None, None, None, None) == abi.KIRIN_EINVAL
+    assert lib.kirin_batch_get_state_dev(None, None, None) == abi.KIRIN_EINVAL
+    assert lib.kirin_batch_accel_dev(None, None) == abi.KIRIN_EINVAL
     assert lib.kirin_batch_get_launch(None, None, None, None) == abi.KIRIN_EINVAL
     assert lib.kirin_last_error(None).decode() == "no context"
 

@@ -283,3 +283,43 @@ def test_batch_with_empty_clusters(kirin_lib):
                 e = metrics.rel_err_vec(acc[lo:hi], ra)
                 assert np.median(e) <= 1e-6 and e.max() <= 1e-5, (groups, j_tiles, e.max())
     assert b.b is None
+
+
+def test_batch_device_pointer_twins(kirin_lib):
+    """set_state_dev / accel_dev / get_state_dev give the host path's results bit for bit; accel before
+    any state is ESTATE; a non-finite upload is reported by the next sync."""
+    import torch
+    clusters, off, m, x, v = _ragged_ensemble(False)
+    dev = torch.device("cuda:0")
+    md, xd, vd = (torch.tensor(a, device=dev) for a in (m, x, v))
+    torch.cuda.synchronize()  # the batch enqueues on a stream of its own
+    with abi.KirinBatch(off, [c.eps for c in clusters]) as b:
+        b.set_launch(2, 2)
+        b.set_state(m, x, v)
+        acc_host = b.accel()
+        b.leapfrog(1.0 / 256, 3, use_graph=False)
+        b.sync()
+        x_host, v_host = b.get_state()
+    with abi.KirinBatch(off, [c.eps for c in clusters]) as b:
+        acc = torch.empty_like(xd)
+        with pytest.raises(abi.KirinError) as e:
+            b.accel_dev(acc)
+        assert e.value.code == abi.KIRIN_ESTATE
+        with pytest.raises(ValueError):
+            b.accel_dev(torch.empty((b.n_total, 3), dtype=torch.float32, device=dev))
+        b.set_launch(2, 2)
+        b.set_state_dev(md, xd, vd)
+        b.accel_dev(acc)
+        b.leapfrog(1.0 / 256, 3, use_graph=False)
+        xo, vo = torch.empty_like(xd), torch.empty_like(vd)
+        b.get_state_dev(xo, vo)
+        b.sync()
+        assert np.array_equal(acc.cpu().numpy(), acc_host)
+        assert np.array_equal(xo.cpu().numpy(), x_host) and np.array_equal(vo.cpu().numpy(), v_host)
+        bad = vd.clone()
+        bad[5, 1] = float("nan")
+        torch.cuda.synchronize()
+        b.set_state_dev(md, xd, bad)
+        with pytest.raises(abi.KirinError) as e:
+            b.sync()
+        assert e.value.code == abi.KIRIN_ENONFINITE
