@@ -372,3 +372,23 @@ def test_scaling_by_powers_of_two(kirin_lib, precision):
         assert np.array_equal(got[0], mu / lam ** 2 * a)
         assert np.array_equal(got[1], mu * nu / lam ** 3 * j)
         assert np.array_equal(got[2], mu / lam * f)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_set_nj_shrinks_and_grows_the_j_set(kirin_lib, precision):
+    """kirin_set_nj: the force runs over the first n_j particles only (a ragged 3001 of 5000), the full
+    set again after growing back, and n_j beyond the highest index ever set is EINVAL."""
+    p = workloads.plummer(5000, 515, eps=1.0 / 256)
+    nj = 3001
+    il = workloads.i_subset(nj, 200, seed=3)
+    ref_small = oracle.acc_jerk_pot(p.m[:nj], p.x[:nj], p.v[:nj], p.eps, i_idx=il)
+    ref_full = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    with abi.Kirin(6000, p.eps, precision=precision) as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        k.set_nj(nj)
+        assert_parity(k.forces(il), ref_small, precision, "n_j = 3001")
+        k.set_nj(p.n)
+        assert_parity(k.forces(il), ref_full, precision, "n_j = 5000 again")
+        with pytest.raises(abi.KirinError) as e:
+            k.set_nj(p.n + 1)
+        assert e.value.code == abi.KIRIN_EINVAL
