@@ -241,9 +241,13 @@ def test_energy(kirin_lib, precision):
     p = workloads.config_small()
     with _ctx(p, precision) as k:
         kin, pot = k.energy()
+        kin2, pot2 = k.energy(2.0 * p.v)  # velocities given by the caller: K scales by 4, W unchanged
+        n_max, tile_i, tile_j = k.query()
     rk, rw = oracle.energy(p.m, p.x, p.v, p.eps)
     assert kin == pytest.approx(rk, rel=1e-13)
     assert pot == pytest.approx(rw, rel=1e-12 if precision == "fp64" else 1e-6)
+    assert kin2 == pytest.approx(4.0 * kin, rel=1e-15) and pot2 == pot
+    assert n_max >= p.n and tile_i > 0 and tile_j == 128
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
