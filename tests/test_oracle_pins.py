@@ -392,3 +392,120 @@ def test_nearest_neighbour_matches_kdtree():
     d, k = spatial.cKDTree(p.x).query(p.x[idx], k=2)
     assert np.array_equal(nn, k[:, 1])
     assert np.allclose(np.sqrt(r2), d[:, 1], rtol=1e-14)
+
+
+# ---- acceleration + potential without jerk (the leapfrog clients of Sect. 4.3) ----
+
+@pytest.mark.parametrize("eps", [0.0, 0.01])
+def test_acc_pot_equals_acc_jerk_pot_bit_for_bit(eps):
+    """oracle.acc_pot forms the same separations, s^3 and 1/s terms in the same j order as
+    acc_jerk_pot (itself pinned above), so its acceleration and potential must be identical
+    bits.  A sign slip, a dropped G or mass, or a wrong power of s in either potential or
+    acceleration of acc_pot breaks the equality."""
+    p = workloads.plummer(300, 61, masses="lognormal")
+    idx = np.array([0, 299, 17, 150, 17, 3])
+    for G in (1.0, 0.7):
+        a_ref, _, p_ref = oracle.acc_jerk_pot(p.m, p.x, p.v, eps, G, i_idx=idx)
+        a, ph = oracle.acc_pot(p.m, p.x, eps, G, i_idx=idx)
+        assert np.array_equal(a, a_ref) and np.array_equal(ph, p_ref)
+    a_all, p_all = oracle.acc_pot(p.m, p.x, eps)
+    a_ref, _, p_ref = oracle.acc_jerk_pot(p.m, p.x, p.v, eps)
+    assert np.array_equal(a_all, a_ref) and np.array_equal(p_all, p_ref)
+
+
+def test_acc_pot_skips_a_coincident_pair_at_zero_softening():
+    """eps = 0 and a distinct particle at the same place: that pair contributes nothing (Sect. 3.3.1),
+    the others their point-mass terms, written out by hand."""
+    m = np.array([1.0, 2.0, 0.5])
+    x = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, -4.0, 0.0]])
+    a, ph = oracle.acc_pot(m, x, 0.0, G=3.0, i_idx=[0])
+    assert np.array_equal(a[0], np.array([0.0, -3.0 * 0.5 * 4.0 / 64.0, 0.0]))
+    assert ph[0] == -3.0 * 0.5 / 4.0
+
+
+@pytest.mark.parametrize("r_frac", [0.05, 0.2])
+def test_acc_pot_shell_theorem(r_frac):
+    """The shell theorem through acc_pot: inside, a = 0 and phi = -G M / R up to O((r/R)^5); outside,
+    a point mass at the centre.  Pins the potential's sign, G and mass factor independently of the
+    jerk-carrying routine."""
+    R, M, G = 2.0, 3.0, 1.7
+    shell = icosahedron(R)
+    d = np.array([0.6, -0.3, 0.74])
+    probe = r_frac * R * d / np.linalg.norm(d)
+    m = np.concatenate([[0.123], np.full(12, M / 12.0)])
+    acc, pot = oracle.acc_pot(m, np.vstack([probe, shell]), 0.0, G, i_idx=[0])
+    assert np.linalg.norm(acc[0]) < 20 * r_frac ** 5 * G * M / R ** 2
+    assert abs(pot[0] + G * M / R) < 5 * r_frac ** 6 * G * M / R
+    far = probe / r_frac * 5.0 / 1.0  # at 5 R
+    acc, pot = oracle.acc_pot(m, np.vstack([far, shell]), 0.0, G, i_idx=[0])
+    r = np.linalg.norm(far)
+    expect = -G * M * far / r ** 3
+    assert np.linalg.norm(acc[0] - expect) < 20 * 0.2 ** 6 * np.linalg.norm(expect)
+    assert abs(pot[0] + G * M / r) < 5 * 0.2 ** 7 * G * M / r
+
+
+# ---- Aarseth's time-step criterion (Sect. 3: the Makino & Aarseth Hermite scheme) ----
+
+def _circular_binary(G=1.3, m1=0.25, m2=0.75, d=2.0):
+    """Two bodies on a circular orbit of separation d about their centre of mass: angular rate
+    omega = sqrt(G (m1 + m2) / d^3), radii d m2 / M and d m1 / M."""
+    M = m1 + m2
+    w = math.sqrt(G * M / d ** 3)
+    r1, r2 = d * m2 / M, d * m1 / M
+    m = np.array([m1, m2])
+    x = np.array([[r1, 0.0, 0.0], [-r2, 0.0, 0.0]])
+    v = np.array([[0.0, w * r1, 0.0], [0.0, -w * r2, 0.0]])
+    return m, x, v, G, w
+
+
+def test_aarseth_step_on_exact_circular_derivatives():
+    """On a circular orbit of rate omega, |a| = omega^2 r, |jerk| = omega^3 r, |a2| = omega^4 r and
+    |a3| = omega^5 r, so both products in the numerator and in the denominator are equal and the
+    criterion gives exactly sqrt(eta) / omega.  Catches a missing square root, eta inside the root
+    twice or not at all, and a wrong power of any derivative."""
+    for w, r, eta in ((1.0, 0.5, 0.01), (0.37, 3.0, 0.02), (5.0, 1e-3, 0.003)):
+        ph = 0.8
+        x = r * np.array([math.cos(ph), math.sin(ph), 0.0])
+        u = r * w * np.array([-math.sin(ph), math.cos(ph), 0.0])   # velocity
+        a1, j1 = -w * w * x, -w * w * u
+        a2, a3 = w ** 4 * x, w ** 4 * u
+        got = hermite.aarseth_step(a1[None], j1[None], a2[None], a3[None], np.array([0.0]), eta)
+        assert got[0] == pytest.approx(math.sqrt(eta) / w, rel=1e-14)
+
+
+def test_aarseth_step_after_one_hermite_step_on_a_circular_orbit():
+    """One shared Hermite step of the oracle on a circular binary, then the derivatives the corrector
+    interpolates: the criterion returns sqrt(eta) / omega up to O((omega dt)^2), and the error falls
+    by about 4 when dt halves."""
+    m, x, v, G, w = _circular_binary()
+    eta = 0.01
+    errs = []
+    for wdt in (0.02, 0.01):
+        dt = wdt / w
+        _, _, _, _, ev = hermite.shared_steps(m, x, v, 0.0, dt, 1, G=G)
+        (a0, j0, _), (a1, j1, _) = ev
+        a2, a3 = hermite.hermite_derivatives(a0, j0, a1, j1, dt)
+        got = hermite.aarseth_step(a1, j1, a2, a3, dt, eta)
+        e = np.abs(got * w / math.sqrt(eta) - 1.0)
+        assert np.all(e < wdt ** 2)
+        errs.append(e.max())
+    assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_aarseth_step_hand_computed_non_parallel_vectors():
+    """Hand-worked rows with derivatives in different directions, where the terms of the criterion
+    differ.  Row 1: |a1| = 5, |jerk| = 2, a2 carried to the end of the step a2 + dt a3 = (2, 0, 1)
+    with |.| = sqrt(5), |a3| = 2 sqrt(2):  dt = sqrt(eta (5 sqrt 5 + 4) / (4 sqrt 2 + 5)).
+    Row 2 (its own dt = 0.25): a2 + dt a3 = (0, 3, 0) + (0, 1, 0) = (0, 4, 0), |a1| = 13 from
+    (5, 12, 0), |jerk| = 1, |a3| = 4:  dt = sqrt(eta (13 * 4 + 1) / (1 * 4 + 16)).
+    Not carrying a2 to the end of the step, carrying it with the wrong sign, or exchanging any two
+    of the four terms changes both rows."""
+    eta = 0.01
+    a1 = np.array([[3.0, 0.0, 4.0], [5.0, 12.0, 0.0]])
+    j1 = np.array([[0.0, 2.0, 0.0], [0.0, 0.0, -1.0]])
+    a2 = np.array([[1.0, 0.0, 0.0], [0.0, 3.0, 0.0]])
+    a3 = np.array([[2.0, 0.0, 2.0], [0.0, 4.0, 0.0]])
+    dt = np.array([0.5, 0.25])
+    got = hermite.aarseth_step(a1, j1, a2, a3, dt, eta)
+    assert got[0] == pytest.approx(math.sqrt(eta * (5 * math.sqrt(5) + 4) / (4 * math.sqrt(2) + 5)), rel=1e-15)
+    assert got[1] == pytest.approx(math.sqrt(eta * 53.0 / 20.0), rel=1e-15)
