@@ -180,8 +180,10 @@ int kirin_compute_forces_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list,
  * force loop).  Device twin of compute + get with, in addition, the index of
  * the nearest j != i (nn, int32, n_i; -1 if there is no other particle) and
  * its squared distance |x_j - x_i|^2 (nn_r2, FP64, n_i), either may be NULL.
- * "Nearest" is decided on s^2 = |d|^2 + eps^2 in the precision of the pair
- * arithmetic (FP32 for KIRIN_MIXED), the smallest index on ties. */
+ * "Nearest" compares the squared separation |x_j - x_i|^2 itself (softening
+ * plays no part) in the precision of the pair arithmetic (FP32 from the
+ * double-single separation for KIRIN_MIXED, FP64 for KIRIN_FP64); ties go to
+ * the smallest j. */
 int kirin_compute_forces_nn_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list, double *acc,
                                 double *jerk, double *pot, int32_t *nn, double *nn_r2);
 
@@ -389,7 +391,8 @@ int kirin_batch_get_launch(const kirin_batch *b, int32_t *groups, int32_t *j_til
  *   stream: cudaStream_t (NULL or cudaStreamLegacy: the legacy default stream).
  * Asynchronous.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) and must come before any stream capture on
- * that device.  Every call on a device shares the one array, which keeps the
+ * that device; if that set-up fails the call returns ECUDA, nothing of it is
+ * kept, and the next call on the device tries again.  Every call on a device shares the one array, which keeps the
  * last call's contents: calls whose work overlaps on the GPU (other streams,
  * other host threads) race and must be ordered by the caller. */
 #define KIRIN_NOALLOC_MAX_N 32768

@@ -18,7 +18,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <functional>
 #include <mutex>
 
 #include "kirin_internal.cuh"
@@ -42,8 +41,8 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 constexpr int MAX_DEVICES = 64;
 
 struct DeviceSetup {
-    std::once_flag once;
-    cudaError_t rc = cudaErrorNotReady;
+    std::mutex mu;
+    bool done = false;  // set only once the set-up has succeeded
     unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch on this device
     int nsm = 0;
     int occ[4] = {0, 0, 0, 0};  // CTAs per SM for 1, 2, 4, 8 j-groups (no guard)
@@ -52,19 +51,29 @@ struct DeviceSetup {
 DeviceSetup g_setup[MAX_DEVICES];
 
 // Once per device, with that device current: the scratch address and the
-// numbers the launch shape depends on.
-void setup_device(DeviceSetup &s, int dev)
+// numbers the launch shape depends on.  A set-up that fails (for example one
+// attempted while the stream is being captured) is not remembered: the next
+// call on that device tries again.
+cudaError_t setup_device(DeviceSetup &s, int dev)
 {
+    std::lock_guard<std::mutex> lock(s.mu);
+    if (s.done)
+        return cudaSuccess;
     void *p = nullptr;
-    s.rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (s.rc != cudaSuccess)
-        return;
-    s.scratch = static_cast<unsigned char *>(p);
-    s.rc = cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (rc == cudaSuccess)
+        rc = cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (rc != cudaSuccess) {
+        cudaGetLastError();  // clear the error the failed attempt left behind
+        return rc;
+    }
     for (int k = 0; k < 4; ++k) {
         s.occ[k] = std::max(1, force_mixed_ctas_per_sm(1 << k, false, MODE_ACC_JERK_POT));
         s.occ_guard[k] = std::max(1, force_mixed_ctas_per_sm(1 << k, true, MODE_ACC_JERK_POT));
     }
+    s.scratch = static_cast<unsigned char *>(p);
+    s.done = true;
+    return cudaSuccess;
 }
 
 // Same trade-off as the context path (waves of CTAs against per-CTA work and
@@ -114,8 +123,7 @@ extern "C" int kirin_forces_noalloc(int64_t n, const double *m, const double *x,
         return KIRIN_ECUDA;
     }
     DeviceSetup &s = g_setup[dev];
-    std::call_once(s.once, setup_device, std::ref(s), dev);
-    if (s.rc != cudaSuccess)
+    if (setup_device(s, dev) != cudaSuccess)
         return KIRIN_ECUDA;
 
     cudaStream_t st = (cudaStream_t)stream;

@@ -4,9 +4,10 @@ Tolerances (per particle, against the FP64 oracle on the same inputs):
 * mixed path, acceleration: median relative error <= 1e-6 and max <= 1e-5
   (the stated target of the mixed-precision path);
 * mixed path, potential: same bounds (all terms have one sign, no cancellation);
-* mixed path, jerk: median <= 1e-5, max <= 1e-3.  The jerk sums terms of both
-  signs built from FP32 velocity differences, and near-cancelling particles
-  amplify their rounding;
+* mixed path, jerk: median <= 1e-6, max <= 1e-4.  The jerk sums terms of both
+  signs built from FP32 velocity differences, so a particle whose jerk nearly
+  cancels carries a larger relative error than its acceleration does; measured
+  at N = 2^20 the median is ~3e-7 and the worst of ~17000 sampled i ~1e-5;
 * FP64 path: median <= 1e-12 and max <= 1e-10 for every quantity (the order
   of summation differs from the oracle's, so results agree to the rounding of
   a sum of N terms, amplified where the sum cancels).
@@ -16,7 +17,7 @@ import numpy as np
 from paper_0707_0438_gb300 import metrics
 
 TOL = {
-    "mixed": {"acc": (1e-6, 1e-5), "pot": (1e-6, 1e-5), "jerk": (1e-5, 1e-3)},
+    "mixed": {"acc": (1e-6, 1e-5), "pot": (1e-6, 1e-5), "jerk": (1e-6, 1e-4)},
     "fp64": {"acc": (1e-12, 1e-10), "pot": (1e-12, 1e-10), "jerk": (1e-12, 1e-10)},
 }
 

@@ -396,3 +396,20 @@ def test_set_nj_shrinks_and_grows_the_j_set(kirin_lib, precision):
         with pytest.raises(abi.KirinError) as e:
             k.set_nj(p.n + 1)
         assert e.value.code == abi.KIRIN_EINVAL
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("n", [4096, 65536])
+def test_newton_third_law(kirin_lib, precision, n):
+    """Sect. 2, Eq. 1: pair forces are equal and opposite, so sum_i m_i a_i = 0 and, differentiating,
+    sum_i m_i jerk_i = 0.  The GPU sums each i separately, so the totals vanish only to rounding:
+    <= 1e-7 (mixed) and 1e-14 (FP64) of sum_i m_i |a_i| (of sum_i m_i |jerk_i| for the jerk).  A pair
+    term whose rounding depends on which particle of the pair is i, or a one-sided bias of the
+    reciprocal square root, shows up here."""
+    p = workloads.plummer(n, (3003, n), masses="lognormal", eps=1e-3)
+    with _ctx(p, precision) as k:
+        acc, jerk, _ = k.forces()
+    bound = {"mixed": 1e-7, "fp64": 1e-14}[precision]
+    for q in (acc, jerk):
+        mq = p.m[:, None] * q
+        assert np.linalg.norm(mq.sum(axis=0)) <= bound * np.linalg.norm(mq, axis=1).sum()
