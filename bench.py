@@ -14,7 +14,11 @@ and result downloads inside the timed region), the FP64 CPU oracle on a
 bounded i-subset (which also gives the per-particle error of the mixed
 results), SM clocks sampled during the timed region, and the roofline entry.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+The default line also carries the other workloads as sub-records ("small",
+"block", "ensemble", "adjoint"), each with its own clock sample and a parity
+summary against the oracle; --no-sub leaves them out.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--no-sub]
   python bench.py --workload small|block|ensemble|adjoint   (the other workloads, one JSON line each)
 
 Multi-GPU runs (torchrun, one rank per GPU) are replicas: every rank
@@ -426,10 +430,31 @@ def run_native(args):
         "roofline": roof, "cpu_baseline": cpu,
     }
     line.update(extra)
+    if world == 1 and not args.no_sub:
+        line.update(secondary_workloads(local))
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def secondary_workloads(device=0):
+    """The other workloads, each with its own clock sample and oracle parity summary, as sub-records of
+    the default line: small (1 + 10 shared Hermite steps, N = 1024), block (block-step Hermite, N = 65536,
+    to t = 1/8, mixed and FP64), ensemble (512 clusters, 64 leapfrog steps) and adjoint (forward +
+    backward of the 64-step differentiable leapfrog).  A workload that fails records its error."""
+    out = {}
+    for name, fn in (("small", lambda: measure_small(20, 3, device)),
+                     ("block", lambda: measure_block(65536, 0.125, 0.125, True, 0.125, device)),
+                     ("ensemble", lambda: measure_ensemble(3, True, device)),
+                     ("adjoint", lambda: measure_adjoint(3, 1, device))):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:  # keep the headline line; say what failed
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def _line(metric, value, unit, steps, warmup, seconds, workload, extra, higher=True, dtype="f32 pair math"):
@@ -440,90 +465,175 @@ def _line(metric, value, unit, steps, warmup, seconds, workload, extra, higher=T
     print(json.dumps(line), flush=True)
 
 
-def run_small(args):
-    """N = 1024, eps = 1/256: one full evaluation and 10 shared Hermite steps dt = 1/1024, mixed and FP64."""
+def _errs(got, ref):
+    """Per-particle relative errors (median, max) of (acc, jerk, pot) or (acc, pot) against the oracle."""
+    from paper_0707_0438_gb300 import metrics
+    names = ("acc", "jerk", "pot") if len(got) == 3 else ("acc", "pot")
+    out = {}
+    for name, g, r in zip(names, got, ref):
+        f = metrics.rel_err_scalar if name == "pot" else metrics.rel_err_vec
+        e = metrics.summary(f(g, r))
+        out[name] = {"median": float(f"{e['median']:.3g}"), "max": float(f"{e['max']:.3g}")}
+    return out
+
+
+def _rel_diff(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+SMALL_WORKLOAD = "plummer N=1024 eps=1/256 seed 1001: 1 + 10 shared Hermite steps dt=1/1024 (11 acc+jerk+pot evaluations)"
+
+
+def measure_small(steps, warmup, device=0):
+    """N = 1024, eps = 1/256: one full evaluation and 10 shared Hermite steps dt = 1/1024, mixed and FP64.
+    Parity: the first evaluation (all i) and the state after the 10 steps against the oracle's."""
     import torch
 
+    import oracle
+    from oracle import hermite
     from paper_0707_0438_gb300 import abi, workloads
     p = workloads.config_small(1024)
+    ref0 = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps)
+    x_ref, v_ref, _, _, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, 1.0 / 1024, 10)
     res = {}
     for precision in ("mixed", "fp64"):
-        with abi.Kirin(p.n, p.eps, precision=precision) as k:
+        with abi.Kirin(p.n, p.eps, precision=precision, device=device) as k:
             k.set_j_particles(p.m, p.x, p.v)
-            for _ in range(args.warmup):
-                k.forces()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
+            first = k.forces()
+            for _ in range(warmup):
                 k.hermite_init(0.0)
-                k.hermite_shared_run(1.0 / 1024, 10)  # enqueued back to back, one synchronisation
-            dt = time.perf_counter() - t0
-            res[precision] = {"value": 11 * p.n * p.n * args.steps / dt, "ms_per_run": 1e3 * dt / args.steps}
-    _line("pair interactions/s, 1 evaluation + 10 shared Hermite steps", res["mixed"]["value"], UNIT, args.steps,
-          args.warmup, res["mixed"]["ms_per_run"] * args.steps / 1e3,
-          "plummer N=1024 eps=1/256: 11 acc+jerk+pot evaluations (kirin_hermite_init + kirin_hermite_shared_run)", {"fp64": res["fp64"]})
+                k.hermite_shared_run(1.0 / 1024, 10)
+            torch.cuda.synchronize()
+            with ClockSampler(device) as clk:
+                t0 = time.perf_counter()
+                for _ in range(steps):
+                    k.hermite_init(0.0)
+                    k.hermite_shared_run(1.0 / 1024, 10)  # enqueued back to back, one synchronisation
+                dt = time.perf_counter() - t0
+            # every timed run went on from where the last one ended: the parity run starts afresh
+            k.set_j_particles(p.m, p.x, p.v)
+            k.hermite_init(0.0)
+            k.hermite_shared_run(1.0 / 1024, 10)
+            st = k.get_state()
+        res[precision] = {"value": 11 * p.n * p.n * steps / dt, "ms_per_run": 1e3 * dt / steps,
+                          "clocks": clk.summary(),
+                          "parity": {"first_evaluation_vs_oracle": _errs(first, ref0),
+                                     "x_after_10_steps_rel_diff": _rel_diff(st["x"], x_ref),
+                                     "v_after_10_steps_rel_diff": _rel_diff(st["v"], v_ref)}}
+    m = res["mixed"]
+    return dict(m, unit=UNIT, workload=SMALL_WORKLOAD, runs=steps, fp64=res["fp64"])
 
 
-def run_block(args):
-    """N = 65536, eps = 1e-3, block-step Hermite (eta 0.01, levels 2^-20..2^-3) to t = 1/8."""
+def run_small(args):
+    r = measure_small(args.steps, args.warmup)
+    _line("pair interactions/s, 1 evaluation + 10 shared Hermite steps", r["value"], UNIT, args.steps,
+          args.warmup, r["ms_per_run"] * args.steps / 1e3, SMALL_WORKLOAD,
+          {k: v for k, v in r.items() if k not in ("value", "unit", "workload")})
+
+
+def _block_workload(n, t_end):
+    return f"plummer N={n} eps=1e-3 seed 1002, Hermite block steps eta=0.01, levels 2^-20..2^-3, to t={t_end:g}"
+
+
+def measure_block(n=65536, t_end=0.125, fp64_t_end=0.125, host_loop=True, histogram_t_end=0.125, device=0):
+    """N = 65536, eps = 1e-3, block-step Hermite (eta 0.01, levels 2^-20..2^-3) to t = 1/8, mixed (the
+    device-driven loop, and the host-driven one for comparison) and FP64.  Value: (initial N^2 +
+    every block's n_i N) / wall time of hermite_init + hermite_run.  Parity: the start evaluation of
+    256 sampled i against the oracle, mixed against FP64 final positions, ΔE/E of each run, and
+    how far the device- and host-driven loops end apart."""
     import torch
 
-    from paper_0707_0438_gb300 import abi, metrics, workloads
-    n = 65536 if args.n == N_DEFAULT else args.n
+    import oracle
+    from paper_0707_0438_gb300 import abi, autotune, metrics, workloads
     p = workloads.config_block(n)
-    out = {}
-    from paper_0707_0438_gb300 import autotune
-    gpu = torch.cuda.get_device_name(0)
-    # the device-driven loop (one graph launch per run) and, for comparison, one host round trip per step
-    for name, precision, t_end, device_loop in (("mixed", "mixed", 0.125, True),
-                                                ("mixed_host_loop", "mixed", 0.125, False),
-                                                ("fp64", "fp64", args.fp64_t_end, True)):
-        with abi.Kirin(n, p.eps, precision=precision) as k:
+    gpu = torch.cuda.get_device_name(device)
+    il = workloads.i_subset(n, 256, seed=9)
+    out, final, start = {}, {}, None
+    runs = [("mixed", "mixed", t_end, True)]
+    if host_loop:
+        runs.append(("mixed_host_loop", "mixed", t_end, False))
+    if fp64_t_end:
+        runs.append(("fp64", "fp64", fp64_t_end, True))
+    for name, precision, te, device_loop in runs:
+        with abi.Kirin(n, p.eps, precision=precision, device=device) as k:
             k.set_j_particles(p.m, p.x, p.v)
             if precision == "mixed":
                 autotune.install(k, n, gpu, "mixed")
+                if start is None:
+                    start = k.forces(il)
             k.set_device_loop(device_loop)
             kin0, pot0 = k.energy()
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            k.hermite_init(0.0)
-            steps, pairs = k.hermite_run(t_end)
-            dt = time.perf_counter() - t0
+            with ClockSampler(device) as clk:
+                t0 = time.perf_counter()
+                k.hermite_init(0.0)
+                steps, pairs = k.hermite_run(te)
+                dt = time.perf_counter() - t0
             kin1, pot1 = k.energy()
-            out[name] = {"t_end": t_end, "block_steps": steps, "pairs": pairs + float(n) * n,
-                         "seconds": dt, "value": (pairs + float(n) * n) / dt, "device_loop": device_loop,
-                         "dE_E": metrics.energy_error(kin0 + pot0, kin1 + pot1)}
-    # active-block histogram and per-bucket rate (each step synchronised), mixed, to t = 1/32
-    hist = {}
-    with abi.Kirin(n, p.eps, precision="mixed") as k:
-        k.set_j_particles(p.m, p.x, p.v)
-        k.hermite_init(0.0)
-        k.sync()
-        while True:
-            t0 = time.perf_counter()
-            _, n_act = k.hermite_block_step(1.0 / 32)
-            k.sync()
-            dt = time.perf_counter() - t0
-            if n_act == 0:
-                break
-            b = 1 << int(math.log2(n_act))
-            h = hist.setdefault(b, [0, 0.0, 0.0])
-            h[0] += 1
-            h[1] += n_act * float(n)
-            h[2] += dt
-    buckets = {str(b): {"steps": h[0], "pairs_per_s": h[1] / h[2]} for b, h in sorted(hist.items())}
-    m = out["mixed"]
+            final[name] = k.get_state()
+        out[name] = {"t_end": te, "block_steps": steps, "pairs": pairs + float(n) * n, "seconds": dt,
+                     "value": (pairs + float(n) * n) / dt, "unit": UNIT, "device_loop": device_loop,
+                     "dE_E": metrics.energy_error(kin0 + pot0, kin1 + pot1), "clocks": clk.summary()}
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
+    parity = {"start_evaluation_256_i_vs_oracle": _errs(start, ref)}
+    if "fp64" in final and fp64_t_end == t_end:
+        parity["x_final_mixed_vs_fp64_rel_diff"] = _rel_diff(final["mixed"]["x"], final["fp64"]["x"])
+    if "mixed_host_loop" in final:
+        # the two loops give the same bits under one fixed launch shape (the GPU tests check that); here
+        # each takes its shapes from the launch table, the device loop per block-size class and the host
+        # loop per block, so they sum in different orders and agree to rounding
+        parity["x_final_device_vs_host_loop_rel_diff"] = _rel_diff(final["mixed"]["x"], final["mixed_host_loop"]["x"])
+        parity["same_block_steps_device_and_host_loop"] = bool(out["mixed"]["block_steps"] ==
+                                                              out["mixed_host_loop"]["block_steps"])
+    res = dict(out["mixed"], workload=_block_workload(n, t_end), parity=parity)
+    for name in ("mixed_host_loop", "fp64"):
+        if name in out:
+            res[name] = out[name]
+    if "fp64" in out:
+        res["mixed_vs_fp64_speedup"] = out["mixed"]["value"] / out["fp64"]["value"]
+    if histogram_t_end:
+        # active-block sizes of the mixed run, stepped from the host (the same launch table as the
+        # host-driven timed run): blocks per power-of-two size bucket and their share of the pairs
+        hist = {}
+        with abi.Kirin(n, p.eps, precision="mixed", device=device) as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            autotune.install(k, n, gpu, "mixed")
+            k.hermite_init(0.0)
+            while True:
+                _, n_act = k.hermite_block_step(histogram_t_end)
+                if n_act == 0:
+                    break
+                h = hist.setdefault(1 << int(math.log2(n_act)), [0, 0.0])
+                h[0] += 1
+                h[1] += n_act * float(n)
+        total = sum(h[1] for h in hist.values())
+        res["n_active_histogram"] = {str(b): {"steps": h[0], "pair_share": round(h[1] / total, 4)}
+                                     for b, h in sorted(hist.items())}
+    return res
+
+
+def run_block(args):
+    n = 65536 if args.n == N_DEFAULT else args.n
+    r = measure_block(n, 0.125, args.fp64_t_end)
     _line("pair interactions/s over a block-step Hermite run (acc+jerk+pot, incl. predictor/corrector/scheduler)",
-          m["value"], UNIT, m["block_steps"], 0, m["seconds"],
-          f"plummer N={n} eps=1e-3 seed 1002, Hermite block steps eta=0.01 to t=1/8",
-          {"mixed": m, "mixed_host_loop": out["mixed_host_loop"], "fp64": out["fp64"],
-           "n_active_histogram": buckets,
-           "note": "fp64 run integrates to the shorter t_end shown; rates are comparable, ΔE/E is per run"})
+          r["value"], UNIT, r["block_steps"], 0, r["seconds"], r["workload"],
+          {k: v for k, v in r.items() if k not in ("value", "unit", "workload")})
 
 
-def run_ensemble(args):
-    """512 clusters, N_c log-uniform in [256, 16384), eps = 1/N_c, leapfrog dt = 1/256, 64 steps."""
-    from paper_0707_0438_gb300 import abi, workloads
+ENSEMBLE_WORKLOAD = ("512 Plummer clusters N_c=floor(256*64^U) seed 1004, eps=1/N_c, leapfrog dt=1/256 x 64 steps, "
+                     "one persistent launch per force, CUDA graph")
+
+
+def measure_ensemble(runs=3, no_graph=True, device=0):
+    """512 clusters, N_c log-uniform in [256, 16384), eps = 1/N_c, leapfrog dt = 1/256, 64 steps.  Value:
+    sum_c N_c^2 x 64 / t.  Parity: the accelerations of the largest, the smallest and a middle cluster
+    against the oracle, and the smallest cluster's positions after the 64 steps against the oracle's
+    leapfrog."""
+    import torch
+
+    import oracle
+    from oracle import leapfrog as olf
+    from paper_0707_0438_gb300 import abi, autotune, metrics, workloads
     clusters, sizes = workloads.ensemble()
     off = np.concatenate([[0], np.cumsum(sizes)])
     m = np.concatenate([c.m for c in clusters])
@@ -531,77 +641,132 @@ def run_ensemble(args):
     v = np.concatenate([c.v for c in clusters])
     pairs_per_step = float(np.sum(sizes.astype(np.float64) ** 2))
     res = {}
-    from paper_0707_0438_gb300 import autotune
-    b = abi.KirinBatch(off, [c.eps for c in clusters])
+    b = abi.KirinBatch(off, [c.eps for c in clusters], device=device)
     tuned = autotune.tune_batch(b, m, x, v)  # before and outside the timed runs
     b.close()
-    for use_graph in (True, False):
-        b = abi.KirinBatch(off, [c.eps for c in clusters])
+    parity = {}
+    for use_graph in ((True, False) if no_graph else (True,)):
+        b = abi.KirinBatch(off, [c.eps for c in clusters], device=device)
         b.set_launch(tuned[0], tuned[1])
+        if use_graph:
+            b.set_state(m, x, v)
+            acc = b.accel()
+            order = np.argsort(sizes)
+            for c in (int(order[-1]), int(order[0]), int(order[len(order) // 2])):
+                ra, _ = oracle.acc_pot(clusters[c].m, clusters[c].x, clusters[c].eps)
+                e = metrics.summary(metrics.rel_err_vec(acc[off[c]:off[c + 1]], ra))
+                parity[f"acc_cluster_{c}_N{int(sizes[c])}_vs_oracle"] = {q: float(f"{e[q]:.3g}") for q in e}
         b.set_state(m, x, v)
         b.leapfrog(1.0 / 256, 64, use_graph=use_graph)  # warm-up (and graph build)
         b.sync()
+        if use_graph:
+            xg, _ = b.get_state()
+            c = int(np.argmin(sizes))
+            xs, _ = olf.trajectory(clusters[c].m, clusters[c].x, clusters[c].v, clusters[c].eps, 1.0 / 256, 64)
+            parity[f"x_after_64_steps_cluster_{c}_N{int(sizes[c])}_rel_diff"] = _rel_diff(xg[off[c]:off[c + 1]],
+                                                                                         xs[-1])
         times = []
-        for _ in range(max(1, args.steps)):
-            b.set_state(m, x, v)
-            t0 = time.perf_counter()
-            b.leapfrog(1.0 / 256, 64, use_graph=use_graph)
-            b.sync()
-            times.append(time.perf_counter() - t0)
+        with ClockSampler(device) as clk:
+            for _ in range(max(1, runs)):
+                b.set_state(m, x, v)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                b.leapfrog(1.0 / 256, 64, use_graph=use_graph)
+                b.sync()
+                times.append(time.perf_counter() - t0)
         b.close()
         t = float(np.median(times))
-        res["graph" if use_graph else "no_graph"] = {"seconds_per_64_steps": t, "value": pairs_per_step * 64 / t}
+        res["graph" if use_graph else "no_graph"] = {"seconds_per_64_steps": t, "value": pairs_per_step * 64 / t,
+                                                     "clocks": clk.summary()}
     g = res["graph"]
-    _line("pair interactions/s, batched leapfrog (sum_c N_c^2 x 64 / t)", g["value"], UNIT, 64, 1,
-          g["seconds_per_64_steps"], f"512 Plummer clusters N_c=floor(256*64^U) seed 1004, sum N_c^2={pairs_per_step:.4g},"
-          " eps=1/N_c, leapfrog dt=1/256 x 64 steps, one persistent launch per force, CUDA graph",
-          {"no_graph": res["no_graph"], "gflops_k38": 38 * g["value"] / 1e9, "n_total": int(off[-1]),
+    out = {"value": g["value"], "unit": UNIT, "seconds_per_64_steps": g["seconds_per_64_steps"],
+           "clocks": g["clocks"], "workload": ENSEMBLE_WORKLOAD, "sum_Nc2": pairs_per_step,
+           "gflops_k38": 38 * g["value"] / 1e9, "n_total": int(off[-1]), "parity": parity,
            "launch": {"groups": tuned[0], "i_per_item": 512 // tuned[0], "j_tiles": tuned[1],
                       "from": "tune_batch (timed before the runs)",
-                      "timed_ms_per_step": {f"{e[0]}x{e[1]}": round(1e3 * e[2], 3) for e in tuned[2]}}})
+                      "timed_ms_per_step": {f"{e[0]}x{e[1]}": round(1e3 * e[2], 3) for e in tuned[2]}}}
+    if "no_graph" in res:
+        out["no_graph"] = res["no_graph"]
+    return out
 
 
-def run_adjoint(args):
-    """N = 16384, eps = 0.01, 64 leapfrog steps dt = 1/128, checkpoint every 8; forward + backward."""
+def run_ensemble(args):
+    r = measure_ensemble(max(1, args.steps))
+    _line("pair interactions/s, batched leapfrog (sum_c N_c^2 x 64 / t)", r["value"], UNIT, 64, 1,
+          r["seconds_per_64_steps"], r["workload"] + f", sum N_c^2={r['sum_Nc2']:.4g}",
+          {k: v for k, v in r.items() if k not in ("value", "unit", "workload", "seconds_per_64_steps")})
+
+
+ADJOINT_WORKLOAD = "plummer N=16384 eps=0.01 seed 1005, 64 KDK steps dt=1/128, checkpoints every 8 steps"
+
+
+def measure_adjoint(steps, warmup, device=0):
+    """N = 16384, eps = 0.01, 64 leapfrog steps dt = 1/128, checkpoint every 8; forward + backward, timed
+    with CUDA events.  Parity: the two force calls of the run (acc + pot and the adjoint) at the initial
+    state against the oracle, every particle."""
     import torch
 
-    from paper_0707_0438_gb300 import abi, workloads
+    import oracle
+    from paper_0707_0438_gb300 import abi, autotune, metrics, workloads
     from paper_0707_0438_gb300 import autograd as kag
-    dev = torch.device("cuda:0")
-    n, steps, dt = 16384, 64, 1.0 / 128
+    dev = torch.device("cuda", device)
+    n, n_steps, dt = 16384, 64, 1.0 / 128
     p = workloads.config_adjoint(n)
     q = workloads.perturb(p, 1e-3)
-    stream = torch.cuda.current_stream().cuda_stream
-    k = abi.Kirin(n, p.eps, precision="mixed", stream=stream)
-    from paper_0707_0438_gb300 import autotune
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    k = abi.Kirin(n, p.eps, precision="mixed", device=device, stream=stream)
     autotune.install(k, n, torch.cuda.get_device_name(dev), "mixed")  # acc+pot and adjoint tables, if stored
     T = lambda a, g=False: torch.tensor(a, dtype=torch.float64, device=dev, requires_grad=g)
     with torch.no_grad():
-        tgt, _ = kag.leapfrog(T(q.x), T(q.v), T(q.m), k, dt, steps)
+        tgt, _ = kag.leapfrog(T(q.x), T(q.v), T(q.m), k, dt, n_steps)
 
     def run():
         x, v, mm = T(p.x, True), T(p.v, True), T(p.m, True)
-        xf, _ = kag.leapfrog(x, v, mm, k, dt, steps, every=8)
+        xf, _ = kag.leapfrog(x, v, mm, k, dt, n_steps, every=8)
         loss = ((xf - tgt) ** 2).sum(dim=1).mean()
         loss.backward()
         return loss
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        loss = run()
-    e1.record()
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    with ClockSampler(device) as clk:
+        e0.record()
+        for _ in range(steps):
+            loss = run()
+        e1.record()
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    # parity of the run's two force calls at the initial state
+    g = np.random.default_rng(21).standard_normal((n, 3))
+    m_d, x_d, g_d = T(p.m), T(p.x), T(g)
+    acc, gx = torch.empty_like(x_d), torch.empty_like(x_d)
+    pot, gm = torch.empty_like(m_d), torch.empty_like(m_d)
+    k.accel_dev(m_d, x_d, acc, pot)
+    k.accel_adjoint_dev(m_d, x_d, g_d, gx, gm)
+    k.sync()
+    k.close()
+    ra, rp = oracle.acc_pot(p.m, p.x, p.eps)
+    rgx, rgm = oracle.force_adjoint(p.m, p.x, g, p.eps)
+    parity = {"acc_pot_vs_oracle": _errs((acc.cpu().numpy(), pot.cpu().numpy()), (ra, rp))}
+    for name, got, ref in (("dL_dx", gx.cpu().numpy(), rgx), ("dL_dm", gm.cpu().numpy()[:, None], rgm[:, None])):
+        err = np.linalg.norm(got - ref, axis=1)
+        parity[f"adjoint_{name}_vs_oracle"] = {
+            "median_rel": float(f"{np.median(err / np.linalg.norm(ref, axis=1)):.3g}"),
+            "max_over_rms": float(f"{err.max() / np.sqrt(np.mean(np.sum(ref * ref, axis=1))):.3g}")}
     # force evaluations: 65 forward, 64 recomputed, 65 adjoint (one per distinct position)
     evals = 65 + 64 + 65
-    k.close()
-    _line("seconds per forward+backward of a 64-step differentiable leapfrog", t, "s", args.steps, args.warmup,
-          t * args.steps, f"plummer N={n} eps=0.01 seed 1005, 64 KDK steps dt=1/128, checkpoints every 8 steps",
-          {"pair_evaluations_per_s": evals * float(n) * n / t, "loss": float(loss.item())}, higher=False)
+    return {"value": t, "unit": "s", "ms_per_forward_backward": 1e3 * t, "runs": steps,
+            "pair_evaluations_per_s": evals * float(n) * n / t, "loss": float(loss.item()),
+            "clocks": clk.summary(), "workload": ADJOINT_WORKLOAD, "parity": parity}
+
+
+def run_adjoint(args):
+    r = measure_adjoint(args.steps, args.warmup)
+    _line("seconds per forward+backward of a 64-step differentiable leapfrog", r["value"], "s", args.steps,
+          args.warmup, r["value"] * args.steps, r["workload"],
+          {k: v for k, v in r.items() if k not in ("value", "unit", "workload")}, higher=False)
 
 
 def main():
@@ -615,7 +780,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", choices=["large", "small", "block", "ensemble", "adjoint"], default="large")
-    ap.add_argument("--fp64-t-end", type=float, default=1.0 / 64)
+    ap.add_argument("--fp64-t-end", type=float, default=1.0 / 8)
+    ap.add_argument("--no-sub", action="store_true", help="skip the secondary workloads on the default line")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

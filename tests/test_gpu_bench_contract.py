@@ -47,6 +47,22 @@ def test_native_line_contract(kirin_lib):
     err = line["mixed_vs_oracle_rel_err"]
     assert err["acc"]["median"] <= 1e-6 and err["acc"]["max"] <= 1e-5 and err["pot"]["median"] <= 1e-6
     assert line["fp64"]["mixed_speedup"] > 1.0
+    # the other workloads ride on the same line, each with its clocks and an oracle parity summary
+    for name in ("small", "block", "ensemble", "adjoint"):
+        sub = line[name]
+        assert "error" not in sub, (name, sub)
+        assert sub["value"] > 0 and sub["clocks"]["sm_max_mhz"] > 0 and sub["parity"], name
+    blk = line["block"]
+    assert blk["t_end"] == 0.125 and blk["fp64"]["t_end"] == 0.125 and blk["block_steps"] > 1000
+    assert blk["parity"]["x_final_device_vs_host_loop_rel_diff"] < 1e-6
+    assert blk["parity"]["x_final_mixed_vs_fp64_rel_diff"] < 1e-6
+    assert line["small"]["parity"]["x_after_10_steps_rel_diff"] < 1e-9
+    assert blk["parity"]["start_evaluation_256_i_vs_oracle"]["acc"]["max"] <= 1e-5
+    assert abs(blk["dE_E"]) < 1e-6 and abs(blk["fp64"]["dE_E"]) < 1e-6
+    assert abs(sum(h["steps"] for h in blk["n_active_histogram"].values()) - blk["block_steps"]) <= 2
+    assert line["small"]["parity"]["first_evaluation_vs_oracle"]["acc"]["max"] <= 1e-5
+    assert all(e["max"] <= 1e-5 for q, e in line["ensemble"]["parity"].items() if q.startswith("acc"))
+    assert line["adjoint"]["parity"]["acc_pot_vs_oracle"]["acc"]["max"] <= 1e-5
 
 
 def test_small_workload_line(kirin_lib):
