@@ -21,8 +21,11 @@ summary against the oracle; --no-sub leaves them out.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--no-sub]
   python bench.py --workload small|block|ensemble|adjoint   (the other workloads, one JSON line each)
 
-Multi-GPU runs (torchrun, one rank per GPU) are replicas: every rank
-evaluates its own copy of the workload; value = all ranks' pairs / max time.
+Multi-GPU runs (torchrun, one rank per GPU) are replicas by default: every
+rank evaluates its own copy of the workload; value = all ranks' pairs / max
+time.  --parallel jsplit shares one evaluation among the ranks instead (each
+sums its part of the j tiles; the partial sums are all-gathered over NCCL and
+added in part order): value = N^2 per step / max time, strong scaling.
 """
 from __future__ import annotations
 
@@ -259,6 +262,12 @@ def run_native(args):
     k.sync()
     from paper_0707_0438_gb300 import autotune
     tuned = autotune.install(k, n, torch.cuda.get_device_name(dev), "mixed")
+    # --parallel jsplit: the ranks share one evaluation, each summing its part of the j tiles; the partial
+    # sums are all-gathered over NCCL and added in part order (every rank holds the result)
+    jsplit_mode = world > 1 and args.parallel == "jsplit"
+    if jsplit_mode:
+        from paper_0707_0438_gb300 import jsplit
+        k.set_j_partition(rank, world, jsplit.TorchAllGather(device=dev))
     groups, n_split = k.get_launch(n)
     launches_per_step = 2 + (1 if n_split > 1 else 0)  # predictor/pack, force, split reduction
 
@@ -294,10 +303,12 @@ def run_native(args):
     clocks = clk.summary()
     pairs_per_step = float(n) * float(n)
     value, t_max = replica_rate(t_mixed, pairs_per_step, args.steps, world, dist, dev)
+    if jsplit_mode:  # one shared evaluation per step, not one per rank
+        value /= world
     ms_per_step = 1e3 * t_max / args.steps
-    res_mixed = (acc.cpu().numpy(), jerk.cpu().numpy(), pot.cpu().numpy()) if rank == 0 else None
+    res_mixed = (acc.cpu().numpy(), jerk.cpu().numpy(), pot.cpu().numpy())
 
-    if rank != 0:
+    if rank != 0 and not jsplit_mode:
         k.close()
         if dist is not None:
             dist.barrier()
@@ -371,6 +382,10 @@ def run_native(args):
            "d2h_bytes_per_step": int(ha.nbytes + hj.nbytes + hp.nbytes),
            "ms_per_step": 1e3 * t_e2e / e_steps}
     k.close()
+    if rank != 0:  # jsplit: the other ranks took part in every exchanging call above
+        dist.barrier()
+        dist.destroy_process_group()
+        return
 
     # ---- CPU oracle on a bounded sample; also the error of the mixed results ----
     cpu = None
@@ -421,10 +436,12 @@ def run_native(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "step_ms_rank0": step_ms, "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if jsplit_mode else "weak",
         "vs_baseline": None, "dtype": "f32 pair math, double-single positions, f64 results", "data": "synthetic",
         "config": dict(_config(n, "mixed"), launch={"groups": groups, "n_split": n_split,
-                                                     "from": "tuned table" if tuned else "cost model"}),
+                                                     "from": "tuned table" if tuned else "cost model"},
+                       parallelism=f"j partition over {world} GPUs (NCCL all-gather of the partial sums)"
+                       if jsplit_mode else "replicas"),
         "gflops_k60": 60.0 * value / 1e9, "gflops_k38_equiv": 38.0 * value / 1e9,
         "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
         "roofline": roof, "cpu_baseline": cpu,
@@ -782,6 +799,8 @@ def main():
     ap.add_argument("--workload", choices=["large", "small", "block", "ensemble", "adjoint"], default="large")
     ap.add_argument("--fp64-t-end", type=float, default=1.0 / 8)
     ap.add_argument("--no-sub", action="store_true", help="skip the secondary workloads on the default line")
+    ap.add_argument("--parallel", choices=["replicas", "jsplit"], default="replicas",
+                    help="N > 1: independent replicas (weak scaling) or one evaluation over a j partition (strong)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

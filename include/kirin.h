@@ -41,6 +41,7 @@ extern "C" {
 #define KIRIN_ENONFINITE (-4) /* NaN or Inf in uploaded particle data */
 #define KIRIN_ETIMEOUT (-5)   /* a bounded wait inside a kernel gave up */
 #define KIRIN_ESTATE (-6)     /* call out of order (e.g. forces before particles) */
+#define KIRIN_EEXCHANGE (-7)  /* the j-partition all-gather callback reported a failure */
 
 typedef struct kirin_ctx kirin_ctx;
 
@@ -372,6 +373,48 @@ int kirin_batch_accel_dev(kirin_batch *b, double *acc);
 int kirin_batch_set_launch(kirin_batch *b, int32_t groups, int32_t j_tiles);
 /* The current decomposition and its number of work items; any pointer may be NULL. */
 int kirin_batch_get_launch(const kirin_batch *b, int32_t *groups, int32_t *j_tiles, int32_t *n_items);
+
+/* ---- j partition over several GPUs ----
+ * The j-split of Sect. 3.2 (several thread blocks each sum a range of j for
+ * the same i, and the host adds their partial sums) lifted across GPUs: each
+ * rank keeps the whole particle set (every particle is an i-particle
+ * somewhere, and the predictor of every step runs on each rank's own copy),
+ * but its force calls sum only its part of the j tiles.  The seven partial
+ * sums per i of every part are then gathered and added in part order, so
+ * every rank holds the same bits.
+ *
+ * kirin_j_partition_range: the j-particles [*j_begin, *j_end) that part
+ *   `part` of `n_parts` sums for a set of n_j: whole tiles of 128, the
+ *   tiles shared out as evenly as they go (a part may be empty when there
+ *   are more parts than tiles).  Host-only arithmetic.  Errors: EINVAL.
+ *
+ * kirin_set_j_partition: from now on the context's force calls sum only
+ *   that part's j (n_parts = 1 restores the whole sum).
+ *   With allgather == NULL every result is this part's partial sum, for the
+ *   caller to add up.  Otherwise the library calls, once per force call,
+ *     allgather(user, send, recv, count, stream)
+ *   with count = 7 n_i: `send` holds this part's partial sums (device
+ *   memory, [acc 3 n_i | jerk 3 n_i | pot n_i], G applied) and the callback
+ *   must leave part r's send buffer in recv[r * count ...] for every r
+ *   (device memory of n_parts * count doubles), ordered on `stream` (the
+ *   context's cudaStream_t): the send buffer is complete once work enqueued
+ *   on `stream` before the call has run, and the library's next work on
+ *   `stream` may read recv.  It returns 0 on success; anything else makes
+ *   the force call return KIRIN_EEXCHANGE.  The callback runs on the calling
+ *   host thread, inside the force call.  With a callback every entry point
+ *   that evaluates acc + jerk + pot or acc + pot returns whole sums:
+ *   compute_forces(_dev), energy, the Hermite and leapfrog integrators (the
+ *   block steps of kirin_hermite_run are then driven from the host, one
+ *   exchange per step).  The adjoint calls and the neighbour search return
+ *   ESTATE on a partitioned context.
+ *   The context allocates 7 n_max (send) and 7 n_max n_parts (recv) doubles
+ *   here.  Errors: EINVAL (part outside [0, n_parts), n_parts outside
+ *   [1, KIRIN_MAX_PARTS]), ENOMEM, ECUDA; on error the context is left
+ *   unpartitioned. */
+#define KIRIN_MAX_PARTS 4096
+typedef int (*kirin_allgather_fn)(void *user, const double *send, double *recv, int64_t count, void *stream);
+int kirin_j_partition_range(int64_t n_j, int32_t part, int32_t n_parts, int64_t *j_begin, int64_t *j_end);
+int kirin_set_j_partition(kirin_ctx *ctx, int32_t part, int32_t n_parts, kirin_allgather_fn allgather, void *user);
 
 /* ---- allocation-free evaluation ----
  * No counterpart in the paper.  For callers that cannot allocate device

@@ -24,6 +24,7 @@ KIRIN_ECUDA = -3
 KIRIN_ENONFINITE = -4
 KIRIN_ETIMEOUT = -5
 KIRIN_ESTATE = -6
+KIRIN_EEXCHANGE = -7
 KIRIN_FP64 = 0
 KIRIN_MIXED = 1
 # kirin_call_kind: the force calls that each have their own launch table
@@ -103,6 +104,8 @@ _SIGS = {
     "kirin_batch_get_state_dev": (ctypes.c_int, [_P, _P, _P]),
     "kirin_batch_accel_dev": (ctypes.c_int, [_P, _P]),
     "kirin_batch_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "kirin_j_partition_range": (ctypes.c_int, [_I64, _I32, _I32, _PI64, _PI64]),
+    "kirin_set_j_partition": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
     "kirin_forces_noalloc": (ctypes.c_int, [_I64, _P, _P, _P, _I64, _P, _D, _D, _D, _P, _P, _P, _P, _P]),
     "kirin_measure_fma_rate": (ctypes.c_int, [_I32, _I32, _PD]),
     "kirin_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -138,6 +141,20 @@ def lib():
             f.argtypes = args
         _lib = cdll
     return _lib
+
+
+# kirin_allgather_fn: int (*)(void *user, const double *send, double *recv, int64_t count, void *stream)
+ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_void_p)
+
+
+def j_partition_range(n_j: int, part: int, n_parts: int):
+    """(j_begin, j_end): the j-particles part `part` of `n_parts` sums (kirin_j_partition_range)."""
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().kirin_j_partition_range(int(n_j), int(part), int(n_parts), ctypes.byref(b), ctypes.byref(e))
+    if rc != KIRIN_OK:
+        raise KirinError(rc, "kirin_j_partition_range")
+    return b.value, e.value
 
 
 def _strerror(code: int) -> str:
@@ -201,6 +218,10 @@ class Kirin:
             detail = ""
             if ctx and getattr(self, "ctx", None):
                 detail = self.lib.kirin_last_error(self.ctx).decode()
+            exc = getattr(self, "_exchange_error", None)
+            if rc == KIRIN_EEXCHANGE and exc is not None:
+                self._exchange_error = None
+                raise KirinError(rc, what, detail) from exc
             raise KirinError(rc, what, detail)
 
     def close(self):
@@ -314,6 +335,25 @@ class Kirin:
         self._check(self.lib.kirin_compute_forces_nn_dev(self.ctx, int(n_i), _dev(i_list), _dev(acc), _dev(jerk),
                                                          _dev(pot), _dev(nn), _dev(nn_r2)),
                     "kirin_compute_forces_nn_dev")
+
+    def set_j_partition(self, part, n_parts, allgather=None):
+        """Sum only part `part` of `n_parts` of the j tiles (kirin_set_j_partition).  allgather: None (results
+        are this part's partial sums) or a callable (send, recv, count, stream) -> int over device pointers
+        (ints), e.g. a jsplit.TorchAllGather; the context keeps it alive."""
+        cb = None
+        if allgather is not None:
+            def trampoline(user, send, recv, count, stream, _f=allgather):
+                try:
+                    return int(_f(send, recv, count, stream))
+                except BaseException as exc:  # never let ctypes swallow a failed exchange
+                    self._exchange_error = exc
+                    return 1
+            cb = ALLGATHER_FN(trampoline)
+        self._exchange_error = None
+        rc = self.lib.kirin_set_j_partition(self.ctx, int(part), int(n_parts),
+                                            ctypes.cast(cb, ctypes.c_void_p) if cb is not None else None, None)
+        self._check(rc, "kirin_set_j_partition")
+        self._allgather_cb = cb  # the library holds the pointer: keep the thunk alive
 
     def set_nn(self, enable=True):
         self._check(self.lib.kirin_set_nn(self.ctx, 1 if enable else 0), "kirin_set_nn")

@@ -100,6 +100,16 @@ struct kirin_ctx {
     int table_prec[N_KINDS] = {-1, -1, -1};      // each table applies to the precision it was set for
     int occ[2][N_MODES][2][4] = {};  // [prec][mode][guard][log2 groups]
 
+    // j partition over several contexts (usually one per GPU): this context sums
+    // tiles [part T / n_parts, (part + 1) T / n_parts) of the T j tiles, and the
+    // exchange callback gathers every part's 7 n_i partial sums, which
+    // k_sum_parts adds in part order
+    int part = 0, n_parts = 1;
+    kirin_allgather_fn allgather = nullptr;
+    void *allgather_user = nullptr;
+    double *d_send = nullptr, *d_recv = nullptr;
+    size_t send_cap = 0, recv_cap = 0;  // doubles
+
     // nearest-neighbour search of the host-pointer path (GRAPE's neighbour list)
     bool want_nn = false;
     bool nn_valid = false;
@@ -147,6 +157,17 @@ int set_msg(kirin_ctx *c, int code, const char *fmt, ...)
     } while (0)
 
 int64_t round_up(int64_t n, int64_t m) { return (n + m - 1) / m * m; }
+
+// Tiles [*tile0, *tile0 + return) of a j partition's part among the
+// ceil(n_j / TILE_J) tiles of the padded image (every tile when n_parts = 1).
+int part_tiles(int64_t n_j, int part, int n_parts, int *tile0)
+{
+    const int64_t total = (std::max<int64_t>(n_j, 1) + TILE_J - 1) / TILE_J;
+    const int64_t b = total * part / n_parts, e = total * (part + 1) / n_parts;
+    if (tile0)
+        *tile0 = (int)b;
+    return (int)(e - b);
+}
 
 int ilog2(int g) { return g == 1 ? 0 : g == 2 ? 1 : g == 4 ? 2 : 3; }
 
@@ -271,7 +292,8 @@ int enqueue_force(kirin_ctx *c, cudaStream_t st, Shape s, int64_t n_i, const int
 {
     if (n_i == 0)
         return KIRIN_OK;
-    const int ntiles = (int)((std::max(n_j, 1) + TILE_J - 1) / TILE_J);
+    int tile0 = 0;
+    const int ntiles = part_tiles(n_j, c->part, c->n_parts, &tile0);
     ForceArgs a{};
     a.jimg = c->prec == KIRIN_MIXED ? (const void *)c->jm : (const void *)c->jd;
     a.ilist = d_ilist;
@@ -279,6 +301,7 @@ int enqueue_force(kirin_ctx *c, cudaStream_t st, Shape s, int64_t n_i, const int
     a.n_i_dev = n_i_dev;
     a.n_j = n_j;
     a.ntiles = ntiles;
+    a.tile0 = tile0;
     a.n_split = s.n_split;
     a.eps2 = c->eps * c->eps;
     a.rmin2 = c->r_min * c->r_min;
@@ -321,13 +344,32 @@ int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mo
 {
     if (n_i == 0)
         return KIRIN_OK;
-    const int ntiles = (int)((std::max(n_j, 1) + TILE_J - 1) / TILE_J);
+    const bool parted = c->n_parts > 1;
+    if (parted && (accumulate || (mode != MODE_ACC_JERK_POT && mode != MODE_ACC_POT)))
+        return set_msg(c, KIRIN_ESTATE, "this call does not support a j partition (kirin_set_j_partition)");
+    const int ntiles = part_tiles(n_j, c->part, c->n_parts, nullptr);
     const Shape s = choose_shape(c, n_i, ntiles, c->prec, mode, guard_on(c));
     int rc = ensure_partial(c, partial_doubles(c, s, n_i, mode));
     if (rc)
         return rc;
-    return enqueue_force(c, c->stream, s, n_i, nullptr, d_ilist, n_j, mode, acc, jerk, pot, accumulate, nn,
-                         nn_r2);
+    if (!parted || !c->allgather)  // whole sums, or this part's partial sums for the caller to combine
+        return enqueue_force(c, c->stream, s, n_i, nullptr, d_ilist, n_j, mode, acc, jerk, pot, accumulate, nn,
+                             nn_r2);
+    // this part's sums into the send buffer [acc 3 n_i | jerk 3 n_i | pot n_i], every part's gathered by
+    // the caller's exchange, then their sum in part order
+    const int64_t count = 7 * n_i;
+    if ((size_t)count > c->send_cap || (size_t)count * c->n_parts > c->recv_cap)
+        return set_msg(c, KIRIN_EINVAL, "j partition: %lld i-particles exceed the exchange buffers",
+                       (long long)n_i);
+    double *sd = c->d_send;
+    rc = enqueue_force(c, c->stream, s, n_i, nullptr, d_ilist, n_j, mode, sd, sd + 3 * n_i, sd + 6 * n_i);
+    if (rc)
+        return rc;
+    const int ex = c->allgather(c->allgather_user, sd, c->d_recv, count, (void *)c->stream);
+    if (ex != 0)
+        return set_msg(c, KIRIN_EEXCHANGE, "j partition: the all-gather callback returned %d", ex);
+    CK(c, launch_sum_parts(c->n_parts, n_i, c->d_recv, acc, jerk, pot, c->stream));
+    return KIRIN_OK;
 }
 
 int read_device_errors(kirin_ctx *c)
@@ -361,7 +403,7 @@ void free_all(kirin_ctx *c)
 {
     void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
                     c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
-                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts};
+                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts, c->d_send, c->d_recv};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -638,6 +680,7 @@ const char *kirin_strerror(int code)
     case KIRIN_ENONFINITE: return "non-finite particle data";
     case KIRIN_ETIMEOUT: return "device wait timed out";
     case KIRIN_ESTATE: return "call out of order";
+    case KIRIN_EEXCHANGE: return "j-partition exchange failed";
     default: return "unknown error";
     }
 }
@@ -842,7 +885,7 @@ int kirin_get_launch_for(kirin_ctx *ctx, int32_t kind, int64_t n_i, int32_t *gro
     if (!ctx || n_i < 0 || kind < 0 || kind >= kirin_ctx::N_KINDS)
         return KIRIN_EINVAL;
     DeviceGuard dg(ctx->device);
-    const int ntiles = (int)((std::max<int64_t>(ctx->n_j, 1) + TILE_J - 1) / TILE_J);
+    const int ntiles = part_tiles(ctx->n_j, ctx->part, ctx->n_parts, nullptr);
     const Shape s = choose_shape(ctx, n_i, ntiles, ctx->prec, mode_of_kind(kind), guard_on(ctx));
     if (groups)
         *groups = s.groups;
@@ -969,6 +1012,56 @@ int kirin_compute_forces(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list)
     ctx->pending = true;
     ctx->pending_n = n_i;
     ctx->nn_valid = ctx->want_nn;
+    return KIRIN_OK;
+}
+
+int kirin_j_partition_range(int64_t n_j, int32_t part, int32_t n_parts, int64_t *j_begin, int64_t *j_end)
+{
+    if (n_j < 0 || n_parts < 1 || n_parts > KIRIN_MAX_PARTS || part < 0 || part >= n_parts || !j_begin || !j_end)
+        return KIRIN_EINVAL;
+    int tile0 = 0;
+    const int nt = part_tiles(n_j, part, n_parts, &tile0);
+    *j_begin = std::min<int64_t>(n_j, (int64_t)tile0 * TILE_J);
+    *j_end = std::min<int64_t>(n_j, (int64_t)(tile0 + nt) * TILE_J);
+    return KIRIN_OK;
+}
+
+int kirin_set_j_partition(kirin_ctx *ctx, int32_t part, int32_t n_parts, kirin_allgather_fn allgather, void *user)
+{
+    if (!ctx || n_parts < 1 || n_parts > KIRIN_MAX_PARTS || part < 0 || part >= n_parts)
+        return set_msg(ctx, KIRIN_EINVAL, "set_j_partition: part %d of %d", part, n_parts);
+    DeviceGuard dg(ctx->device);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));  // no launch still reads the old buffers
+    if (n_parts > 1 && allgather) {
+        const size_t send = 7 * (size_t)std::max<int64_t>(ctx->n_max, 1);
+        const size_t recv = send * (size_t)n_parts;
+        if (send > ctx->send_cap || recv > ctx->recv_cap) {
+            if (ctx->d_send)
+                cudaFree(ctx->d_send);
+            if (ctx->d_recv)
+                cudaFree(ctx->d_recv);
+            ctx->d_send = ctx->d_recv = nullptr;
+            ctx->send_cap = ctx->recv_cap = 0;
+            if (cudaMalloc(&ctx->d_send, send * sizeof(double)) != cudaSuccess ||
+                cudaMalloc(&ctx->d_recv, recv * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                if (ctx->d_send)
+                    cudaFree(ctx->d_send);
+                ctx->d_send = nullptr;
+                ctx->part = 0;
+                ctx->n_parts = 1;
+                ctx->allgather = nullptr;
+                return set_msg(ctx, KIRIN_ENOMEM, "set_j_partition: exchange buffers of %zu doubles", send + recv);
+            }
+            ctx->send_cap = send;
+            ctx->recv_cap = recv;
+        }
+    }
+    ctx->part = part;
+    ctx->n_parts = n_parts;
+    ctx->allgather = n_parts > 1 ? allgather : nullptr;
+    ctx->allgather_user = n_parts > 1 ? user : nullptr;
+    ctx->pending = false;
     return KIRIN_OK;
 }
 
@@ -1171,7 +1264,7 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
         return KIRIN_EINVAL;
     if (!ctx->hermite_ready)
         return set_msg(ctx, KIRIN_ESTATE, "hermite_run: call kirin_hermite_init first");
-    if (ctx->device_loop)
+    if (ctx->device_loop && ctx->n_parts == 1)  // a partitioned context exchanges from the host each step
         return hermite_run_device(ctx, t_end, max_steps, n_steps, n_pairs);
     int64_t steps = 0;
     double pairs = 0.0, t_last = 0.0;

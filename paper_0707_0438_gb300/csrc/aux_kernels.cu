@@ -867,6 +867,40 @@ cudaError_t launch_pack_adjoint(int n, int n_pad, const double *m, const double 
 
 namespace kirin {
 
+// j partition: output k of the seven per-i quantities is the sum of the
+// parts' partial values in part order, the same on every rank.
+__global__ void k_sum_parts(int n_parts, long long n_i, const double *__restrict__ parts, double *acc,
+                            double *jerk, double *pot)
+{
+    const long long count = 7 * n_i;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count)
+        return;
+    double s = 0.0;
+    for (int r = 0; r < n_parts; ++r)
+        s += __ldcg(parts + (size_t)r * count + k);
+    if (k < 3 * n_i) {
+        if (acc)
+            acc[k] = s;
+    } else if (k < 6 * n_i) {
+        if (jerk)
+            jerk[k - 3 * n_i] = s;
+    } else if (pot) {
+        pot[k - 6 * n_i] = s;
+    }
+}
+
+cudaError_t launch_sum_parts(int n_parts, int64_t n_i, const double *parts, double *acc, double *jerk,
+                             double *pot, cudaStream_t st)
+{
+    if (n_i <= 0)
+        return cudaSuccess;
+    const long long count = 7 * (long long)n_i;
+    k_sum_parts<<<(unsigned)((count + AUX_THREADS - 1) / AUX_THREADS), AUX_THREADS, 0, st>>>(n_parts, n_i, parts,
+                                                                                              acc, jerk, pot);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *err, cudaStream_t st)
 {
     k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, err);

@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force_fp64(const ForceArgs Ai
     const double eps2 = A.eps2, rmin2 = A.rmin2;
 
     const int y = blockIdx.y;
-    const int tb = (int)(((long long)A.ntiles * y) / A.n_split);
-    const int te = (int)(((long long)A.ntiles * (y + 1)) / A.n_split);
+    const int tb = A.tile0 + (int)(((long long)A.ntiles * y) / A.n_split);
+    const int te = A.tile0 + (int)(((long long)A.ntiles * (y + 1)) / A.n_split);
     const int nt = te - tb;
 
     if (tid == 0) {

@@ -146,8 +146,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
 
     // ---- j range of this CTA (grid.y splits the tiles) ----
     const int y = blockIdx.y;
-    const int tb = (int)(((long long)A.ntiles * y) / A.n_split);
-    const int te = (int)(((long long)A.ntiles * (y + 1)) / A.n_split);
+    const int tb = A.tile0 + (int)(((long long)A.ntiles * y) / A.n_split);
+    const int te = A.tile0 + (int)(((long long)A.ntiles * (y + 1)) / A.n_split);
     const int nt = te - tb;
 
     if (tid == 0) {
@@ -320,15 +320,16 @@ __global__ void __launch_bounds__(TINY_THREADS) k_force_tiny(const ForceArgs A)
     if ((int)blockIdx.y * TINY_WARPS >= n_i)
         return;  // no i-particle for this CTA (uniform)
     const JMixed *__restrict__ J = static_cast<const JMixed *>(A.jimg);
-    const int n_pad = A.ntiles * TILE_J;
+    const int n_pad = A.ntiles * TILE_J;  // the records summed: [jb, jb + n_pad) of the padded image
+    const int jb = A.tile0 * TILE_J;
     const int chunk = (n_pad + (int)gridDim.x - 1) / (int)gridDim.x;
     if (chunk > TINY_JCHUNK) {  // the host sizes the grid so that this cannot happen
         if (threadIdx.x == 0)
             atomicOr(A.err, ERR_INDEX);
         return;
     }
-    const int j0 = min(n_pad, (int)blockIdx.x * chunk);
-    const int len = min(n_pad, j0 + chunk) - j0;
+    const int j0 = jb + min(n_pad, (int)blockIdx.x * chunk);
+    const int len = min(jb + n_pad, j0 + chunk) - j0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = (int)blockIdx.y * TINY_WARPS + warp;
     int i = -1;

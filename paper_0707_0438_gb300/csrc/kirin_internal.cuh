@@ -87,7 +87,8 @@ struct ForceArgs {
     const int32_t *ilist;   // device, n_i entries; nullptr = identity
     int n_i;
     int n_j;
-    int ntiles;             // ceil(n_j / TILE_J)
+    int ntiles;             // j tiles summed: [tile0, tile0 + ntiles) of the padded image
+    int tile0;              // first j tile (0 unless the context sums one part of a j partition)
     int n_split;
     double eps2;
     double rmin2;
@@ -195,5 +196,10 @@ cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *err, cud
 cudaError_t launch_copy(int n, const double *src, double *dst, cudaStream_t st);
 cudaError_t launch_pack_adjoint(int n, int n_pad, const double *m, const double *x, const double *lv, double c,
                                 JMixed *jm, JF64 *jd, unsigned *err, cudaStream_t st);
+// Sum of n_parts consecutive blocks of `count` doubles, part 0 first (the same
+// order on every rank), split into acc (3 n_i), jerk (3 n_i) and pot (n_i);
+// count = 7 n_i; any output may be null.
+cudaError_t launch_sum_parts(int n_parts, int64_t n_i, const double *parts, double *acc, double *jerk,
+                             double *pot, cudaStream_t st);
 
 }  // namespace kirin

@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_strerror_names_every_code(lib):
     for code in (abi.KIRIN_OK, abi.KIRIN_EINVAL, abi.KIRIN_ENOMEM, abi.KIRIN_ECUDA, abi.KIRIN_ENONFINITE,
-                 abi.KIRIN_ETIMEOUT, abi.KIRIN_ESTATE):
+                 abi.KIRIN_ETIMEOUT, abi.KIRIN_ESTATE, abi.KIRIN_EEXCHANGE):
         s = lib.kirin_strerror(code).decode()
         assert s and s != "unknown error"
     assert lib.kirin_strerror(-99).decode() == "unknown error"
