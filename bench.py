@@ -262,6 +262,9 @@ def run_native(args):
     k.sync()
     from paper_0707_0438_gb300 import autotune
     tuned = autotune.install(k, n, torch.cuda.get_device_name(dev), "mixed")
+    if args.launch:  # a fixed launch shape (profiling the bench's shape at another size)
+        k.set_launch(*args.launch)
+        tuned = False
     # --parallel jsplit: the ranks share one evaluation, each summing its part of the j tiles; the partial
     # sums are all-gathered over NCCL and added in part order (every rank holds the result)
     jsplit_mode = world > 1 and args.parallel == "jsplit"
@@ -439,7 +442,8 @@ def run_native(args):
         "scaling": "strong" if jsplit_mode else "weak",
         "vs_baseline": None, "dtype": "f32 pair math, double-single positions, f64 results", "data": "synthetic",
         "config": dict(_config(n, "mixed"), launch={"groups": groups, "n_split": n_split,
-                                                     "from": "tuned table" if tuned else "cost model"},
+                                                     "from": "fixed (--launch)" if args.launch else
+                                                     "tuned table" if tuned else "cost model"},
                        parallelism=f"j partition over {world} GPUs (NCCL all-gather of the partial sums)"
                        if jsplit_mode else "replicas"),
         "gflops_k60": 60.0 * value / 1e9, "gflops_k38_equiv": 38.0 * value / 1e9,
@@ -799,6 +803,8 @@ def main():
     ap.add_argument("--workload", choices=["large", "small", "block", "ensemble", "adjoint"], default="large")
     ap.add_argument("--fp64-t-end", type=float, default=1.0 / 8)
     ap.add_argument("--no-sub", action="store_true", help="skip the secondary workloads on the default line")
+    ap.add_argument("--launch", type=lambda t: tuple(int(v) for v in t.split(",")), default=None,
+                    help="fixed launch shape GROUPS,SPLITS of the large-workload force calls")
     ap.add_argument("--parallel", choices=["replicas", "jsplit"], default="replicas",
                     help="N > 1: independent replicas (weak scaling) or one evaluation over a j partition (strong)")
     args = ap.parse_args()
