@@ -98,6 +98,13 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         if self.proc is not None:
+            # a region shorter than the sampling period still gets its first sample
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                self.tmp.flush()
+                if os.path.getsize(self.tmp.name) > 0:
+                    break
+                time.sleep(0.02)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -525,30 +532,32 @@ def measure_small(steps, warmup, device=0):
                 k.hermite_init(0.0)
                 k.hermite_shared_run(1.0 / 1024, 10)
             torch.cuda.synchronize()
+            runs = 0
             with ClockSampler(device) as clk:
                 t0 = time.perf_counter()
-                for _ in range(steps):
+                while runs < steps or time.perf_counter() - t0 < 0.5:  # at least half a second of runs
                     k.hermite_init(0.0)
                     k.hermite_shared_run(1.0 / 1024, 10)  # enqueued back to back, one synchronisation
+                    runs += 1
                 dt = time.perf_counter() - t0
             # every timed run went on from where the last one ended: the parity run starts afresh
             k.set_j_particles(p.m, p.x, p.v)
             k.hermite_init(0.0)
             k.hermite_shared_run(1.0 / 1024, 10)
             st = k.get_state()
-        res[precision] = {"value": 11 * p.n * p.n * steps / dt, "ms_per_run": 1e3 * dt / steps,
+        res[precision] = {"value": 11 * p.n * p.n * runs / dt, "ms_per_run": 1e3 * dt / runs, "runs": runs,
                           "clocks": clk.summary(),
                           "parity": {"first_evaluation_vs_oracle": _errs(first, ref0),
                                      "x_after_10_steps_rel_diff": _rel_diff(st["x"], x_ref),
                                      "v_after_10_steps_rel_diff": _rel_diff(st["v"], v_ref)}}
     m = res["mixed"]
-    return dict(m, unit=UNIT, workload=SMALL_WORKLOAD, runs=steps, fp64=res["fp64"])
+    return dict(m, unit=UNIT, workload=SMALL_WORKLOAD, fp64=res["fp64"])
 
 
 def run_small(args):
     r = measure_small(args.steps, args.warmup)
-    _line("pair interactions/s, 1 evaluation + 10 shared Hermite steps", r["value"], UNIT, args.steps,
-          args.warmup, r["ms_per_run"] * args.steps / 1e3, SMALL_WORKLOAD,
+    _line("pair interactions/s, 1 evaluation + 10 shared Hermite steps", r["value"], UNIT, r["runs"],
+          args.warmup, r["ms_per_run"] * r["runs"] / 1e3, SMALL_WORKLOAD,
           {k: v for k, v in r.items() if k not in ("value", "unit", "workload")})
 
 
@@ -748,9 +757,12 @@ def measure_adjoint(steps, warmup, device=0):
         loss.backward()
         return loss
 
-    for _ in range(warmup):
+    t0 = time.perf_counter()
+    for _ in range(max(1, warmup)):
         run()
     torch.cuda.synchronize()
+    t_run = (time.perf_counter() - t0) / max(1, warmup)
+    steps = max(steps, int(math.ceil(0.5 / max(t_run, 1e-4))))  # at least half a second of runs
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(device) as clk:
         e0.record()
@@ -785,8 +797,8 @@ def measure_adjoint(steps, warmup, device=0):
 
 def run_adjoint(args):
     r = measure_adjoint(args.steps, args.warmup)
-    _line("seconds per forward+backward of a 64-step differentiable leapfrog", r["value"], "s", args.steps,
-          args.warmup, r["value"] * args.steps, r["workload"],
+    _line("seconds per forward+backward of a 64-step differentiable leapfrog", r["value"], "s", r["runs"],
+          args.warmup, r["value"] * r["runs"], r["workload"],
           {k: v for k, v in r.items() if k not in ("value", "unit", "workload")}, higher=False)
 
 

@@ -67,5 +67,5 @@ def test_native_line_contract(kirin_lib):
 
 def test_small_workload_line(kirin_lib):
     line = _run(["--workload", "small", "--steps", "2", "--warmup", "3"])
-    assert line["value"] > 0 and line["steps"] == 2 and "N=1024" in line["config"]["workload"]
+    assert line["value"] > 0 and line["steps"] >= 2 and "N=1024" in line["config"]["workload"]
     assert line["fp64"]["value"] > 0
