@@ -8,6 +8,7 @@
 
 #include "kirin_internal.cuh"
 #include "loop_internal.cuh"
+#include "pair_mixed.cuh"
 #include "tma.cuh"
 
 namespace kirin {
@@ -395,7 +396,19 @@ __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, dou
                                              const double *acc, const double *jerk, double *bx, double *bv,
                                              double *ba, double *bj, double *bt, double *bdt)
 {
-    const double dt = t_next - bt[i];
+    // every input first (independent loads, one memory latency), then the arithmetic, then the stores
+    double a0v[3], j0v[3], a1v[3], j1v[3], xpv[3], vpv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a0v[c] = __ldcg(ba + 3 * i + c);
+        j0v[c] = __ldcg(bj + 3 * i + c);
+        a1v[c] = __ldcg(acc + 3 * (size_t)k + c);
+        j1v[c] = __ldcg(jerk + 3 * (size_t)k + c);
+        xpv[c] = __ldcg(xp + 3 * i + c);
+        vpv[c] = __ldcg(vp + 3 * i + c);
+    }
+    const double t_i = __ldcg(bt + i), dt_i = __ldcg(bdt + i);
+    const double dt = t_next - t_i;
     const bool p2 = is_pow2(dt);
     const double idt = p2 ? __longlong_as_double((2046ll << 52) - (__double_as_longlong(dt) & 0x7ff0000000000000ll))
                           : 1.0 / dt;
@@ -406,13 +419,13 @@ __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, dou
     double A = 0.0, J = 0.0, N2 = 0.0, N3 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
-        const double a1 = acc[3 * (size_t)k + c], j1 = jerk[3 * (size_t)k + c];
+        const double a0 = a0v[c], j0 = j0v[c];
+        const double a1 = a1v[c], j1 = j1v[c];
         const double da = a0 - a1;
         const double a2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da) * idt2;
         const double a3 = fma(dt6, j0 + j1, 12.0 * da) * idt3;
-        bx[3 * i + c] = fma(a3, c5, fma(a2, c4, xp[3 * i + c]));
-        bv[3 * i + c] = fma(a3, c4, fma(a2, c3, vp[3 * i + c]));
+        bx[3 * i + c] = fma(a3, c5, fma(a2, c4, xpv[c]));
+        bv[3 * i + c] = fma(a3, c4, fma(a2, c3, vpv[c]));
         ba[3 * i + c] = a1;
         bj[3 * i + c] = j1;
         const double a2e = fma(dt, a3, a2);  // a2 at the end of the step
@@ -445,7 +458,7 @@ __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, dou
         bdt[i] = q;
         return t_next + q;
     }
-    return t_next + bdt[i];
+    return t_next + dt_i;
 }
 
 __device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double t_next, double eta, double dt_min,
@@ -585,15 +598,17 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_correct(const StepArgs A)
 // Predict every j to t_next and list the next block.  One 64-bit atomic per
 // CTA reserves its range of the list (low word) and counts finished CTAs
 // (high word); the CTA that reserves last publishes the block at once (the
-// list itself is read only by later kernels).
-__global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
+// list itself is read only by later kernels, or after a grid barrier).
+// Shared by k_step_select and the small-step kernel, whose CTAs come back
+// to these words and particles after other CTAs changed them: loads bypass L1.
+__device__ void select_body(const StepArgs &A)
 {
     RunState *R = A.run;
-    const long long steps0 = R->steps;
-    const double tn = key_time(R->minw[steps0 & 1]);
-    const long long lim = R->max_steps;
-    bool due = tn <= R->t_end && (lim <= 0 || steps0 < lim);
-    const bool stall = due && steps0 > 0 && !(tn > R->t_last);
+    const long long steps0 = __ldcg(&R->steps);
+    const double tn = key_time(__ldcg(&R->minw[steps0 & 1]));
+    const long long lim = __ldcg(&R->max_steps);
+    bool due = tn <= __ldcg(&R->t_end) && (lim <= 0 || steps0 < lim);
+    const bool stall = due && steps0 > 0 && !(tn > __ldcg(&R->t_last));
     if (stall)
         due = false;
     if (!due) {
@@ -612,7 +627,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
     int c = 0;
     for (int k = c0 + threadIdx.x; k < c1; k += STEP_THREADS) {
         predict_one(k, A.n, tn, 1, A.bm, A.bx, A.bv, A.ba, A.bj, A.bt, A.xp, A.vp, A.jm, A.jd, A.err);
-        c += A.bt[k] + A.bdt[k] == tn;
+        c += __ldcg(A.bt + k) + __ldcg(A.bdt + k) == tn;
     }
     for (int k = A.n + blockIdx.x * STEP_THREADS + threadIdx.x; k < A.n_pad; k += gridDim.x * STEP_THREADS)
         predict_one(k, A.n, tn, 1, A.bm, A.bx, A.bv, A.ba, A.bj, A.bt, A.xp, A.vp, A.jm, A.jd, A.err);  // padding
@@ -632,7 +647,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
             *A.count_out = count;
             *A.t_next_out = tn;
             R->steps = steps0 + 1;
-            R->pairs += (double)count * (double)A.n_j;
+            R->pairs = __ldcg(&R->pairs) + (double)count * (double)A.n_j;
             R->t_last = tn;
             R->pending = count;
             cudaGraphSetConditional(A.branch, cls);
@@ -644,13 +659,324 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
         int base = base_s;
         for (int i0 = c0; i0 < c1; i0 += STEP_THREADS) {
             const int i = i0 + threadIdx.x;
-            const bool flag = i < c1 && A.bt[i] + A.bdt[i] == tn;
+            const bool flag = i < c1 && __ldcg(A.bt + i) + __ldcg(A.bdt + i) == tn;
             int all;
             const int rank = cta_rank(flag, all);
             if (flag)
                 A.ilist[base + rank] = i;
             base += all;
         }
+    }
+}
+
+__global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A) { select_body(A); }
+
+// ---- small active blocks (at most SMALL_MAX i-particles) -----------------------
+//
+// The chunk of CTA c is the j tiles [tile0 + c T / G, tile0 + (c + 1) T / G) of
+// the padded image (G CTAs, T tiles), staged in shared memory SMALL_STAGE
+// tiles at a time.  Lane l of every warp holds member l (lanes beyond the
+// block idle), and warp w takes the record pairs (2p, 2p + 1) of each staged
+// piece with p = w mod SMALL_WARPS, the two records in the two float2 lanes
+// of the pair body (a broadcast shared-memory read for the whole warp; the
+// member's own record gets zero mass).  Lane sums are folded into
+// double-single after every staged piece; the warps' sums of a member meet in
+// warp order in shared memory, and the chunk's seven sums per member go to
+// the chunk's slots of the scratch.
+
+constexpr int SMALL_THREADS = 256;
+constexpr int SMALL_WARPS = SMALL_THREADS / 32;
+constexpr int SMALL_STAGE = 4;  // j tiles in shared memory at a time
+static_assert(SMALL_MAX == 32, "a lane per member");
+static_assert((size_t)SMALL_WARPS * 7 * 32 * sizeof(float2) <= SMALL_STAGE * TILE_J * sizeof(JMixed),
+              "the warps' sums fit in the staging space");
+
+__device__ __forceinline__ JMixed load_record(const JMixed *J, int r)
+{
+    JMixed out;
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+        out.q[c] = __ldcg(&J[r].q[c]);
+    return out;
+}
+
+template <bool GUARD>
+__device__ void small_chunk_sums(const JMixed *__restrict__ J, const int32_t *ilist, int count, int n_j, int tile0,
+                                 int ntiles, float eps2, float rmin2, float2 *part, unsigned *err, JMixed *js)
+{
+    const int G = (int)gridDim.x, c = (int)blockIdx.x;
+    const int tb = tile0 + (int)((long long)ntiles * c / G);
+    const int te = tile0 + (int)((long long)ntiles * (c + 1) / G);
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    int i = -1;
+    IPair I;
+    if (lane < count) {
+        i = ilist ? __ldcg(ilist + lane) : lane;
+        if (i < 0 || i >= n_j) {
+            if (warp == 0)
+                atomicOr(err, ERR_INDEX);
+            i = -1;
+        } else {
+            const JMixed rec = load_record(J, i);
+            I = load_ipair(&rec, &rec, eps2, rmin2);
+        }
+    }
+    float hi[7], lo[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+        hi[q] = lo[q] = 0.f;
+    for (int s0 = tb; s0 < te; s0 += SMALL_STAGE) {
+        const int s1 = min(te, s0 + SMALL_STAGE);
+        const int len = (s1 - s0) * TILE_J;
+        if (s0 > tb)
+            __syncthreads();  // the previous piece is consumed
+        for (int r = (int)threadIdx.x; r < len; r += SMALL_THREADS)
+            js[r] = load_record(J, s0 * TILE_J + r);
+        __syncthreads();
+        if (i < 0)
+            continue;
+        const int jb = s0 * TILE_J;
+        Tile7 t;
+        t.zero();
+        for (int r = 2 * warp; r < len; r += 2 * SMALL_WARPS) {
+            const JMixed A = js[r], B = js[r + 1];
+            JMixed q;
+            q.q[0] = make_float4(A.q[0].x, B.q[0].x, A.q[0].z, B.q[0].z);
+            q.q[1] = make_float4(A.q[1].x, B.q[1].x, jb + r == i ? 0.f : A.q[1].z, jb + r + 1 == i ? 0.f : B.q[1].z);
+            q.q[2] = make_float4(A.q[2].x, B.q[2].x, A.q[2].z, B.q[2].z);
+            q.q[3] = make_float4(A.q[3].x, B.q[3].x, A.q[3].z, B.q[3].z);
+            q.q[4] = make_float4(A.q[4].x, B.q[4].x, A.q[4].z, B.q[4].z);
+            pair<GUARD, MODE_ACC_JERK_POT>(q, I, t);
+        }
+        const float v[7] = {t.ax.x + t.ax.y, t.ay.x + t.ay.y, t.az.x + t.az.y,
+                            __fmaf_rn(-3.f, t.j2x.x, t.j1x.x) + __fmaf_rn(-3.f, t.j2x.y, t.j1x.y),
+                            __fmaf_rn(-3.f, t.j2y.x, t.j1y.x) + __fmaf_rn(-3.f, t.j2y.y, t.j1y.y),
+                            __fmaf_rn(-3.f, t.j2z.x, t.j1z.x) + __fmaf_rn(-3.f, t.j2z.y, t.j1z.y),
+                            t.pt.x + t.pt.y};
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            two_sum(hi[q], lo[q], v[q]);
+    }
+    // the warps' sums of each member, added in warp order (the staging space is free now)
+    __syncthreads();
+    float2 *red = reinterpret_cast<float2 *>(js);  // [SMALL_WARPS][7][32]
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+        red[(warp * 7 + q) * 32 + lane] = make_float2(hi[q], lo[q]);
+    __syncthreads();
+    for (int o = (int)threadIdx.x; o < 7 * count; o += SMALL_THREADS) {
+        const int q = o / count, k = o - q * count;
+        float h = 0.f, l = 0.f;
+#pragma unroll
+        for (int w = 0; w < SMALL_WARPS; ++w) {
+            const float2 v = red[(w * 7 + q) * 32 + k];
+            two_sum(h, l, v.x);
+            l = __fadd_rn(l, v.y);
+        }
+        part[q * SMALL_MAX + k] = make_float2(h, l);
+    }
+    __syncthreads();  // the staging space is free for the caller again
+}
+
+// The two-level sum of the chunks' sums, in chunk order: returns true in the
+// one CTA that ends up with the final sums, fin[q * SMALL_MAX + k] (FP64,
+// before G).  Each ticket is reset by its last arrival.
+__device__ bool small_reduce(int count, const SmallScratch &S, double *fin)
+{
+    __shared__ int last_s;
+    const int G = (int)gridDim.x, c = (int)blockIdx.x;
+    const int ng = small_groups(G);
+    const int g = c / SMALL_RG;
+    const int g0 = g * SMALL_RG, gsize = min(SMALL_RG, G - g0);
+    const int nout = 7 * count;
+    __threadfence();  // this chunk's sums before its arrival
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last_s = atomicAdd(&S.tickets[g], 1u) + 1u == (unsigned)gsize;
+    __syncthreads();
+    if (!last_s)
+        return false;
+    __threadfence();
+    for (int o = (int)threadIdx.x; o < nout; o += SMALL_THREADS) {
+        const int q = o / count, k = o - q * count;
+        float2 v[SMALL_RG];  // every chunk's value first: one memory latency, not SMALL_RG
+#pragma unroll
+        for (int cc = 0; cc < SMALL_RG; ++cc)
+            v[cc] = cc < gsize ? __ldcg(&S.part[((size_t)(g0 + cc) * 7 + q) * SMALL_MAX + k]) : make_float2(0.f, 0.f);
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < SMALL_RG; ++cc) {
+            if (cc < gsize) {
+                two_sum(hi, lo, v[cc].x);
+                lo = __fadd_rn(lo, v[cc].y);
+            }
+        }
+        S.gpart[((size_t)g * 7 + q) * SMALL_MAX + k] = make_float2(hi, lo);
+    }
+    if (threadIdx.x == 0)
+        S.tickets[g] = 0u;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last_s = atomicAdd(&S.tickets[ng], 1u) + 1u == (unsigned)ng;
+    __syncthreads();
+    if (!last_s)
+        return false;
+    __threadfence();
+    for (int o = (int)threadIdx.x; o < nout; o += SMALL_THREADS) {
+        const int q = o / count, k = o - q * count;
+        float hi = 0.f, lo = 0.f;
+        for (int g1 = 0; g1 < ng; g1 += SMALL_RG) {  // groups SMALL_RG at a time, loads first
+            float2 v[SMALL_RG];
+#pragma unroll
+            for (int gg = 0; gg < SMALL_RG; ++gg)
+                v[gg] = g1 + gg < ng ? __ldcg(&S.gpart[((size_t)(g1 + gg) * 7 + q) * SMALL_MAX + k])
+                                     : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int gg = 0; gg < SMALL_RG; ++gg) {
+                if (g1 + gg < ng) {
+                    two_sum(hi, lo, v[gg].x);
+                    lo = __fadd_rn(lo, v[gg].y);
+                }
+            }
+        }
+        fin[q * SMALL_MAX + k] = (double)hi + (double)lo;
+    }
+    if (threadIdx.x == 0)
+        S.tickets[ng] = 0u;
+    __syncthreads();
+    return true;
+}
+
+// Final values of the sums (acc, jerk: G sum; pot: -G sum) in i-list order.
+__device__ void small_store(int count, const double *fin, double G, double *acc, double *jerk, double *pot)
+{
+    for (int o = (int)threadIdx.x; o < 7 * count; o += SMALL_THREADS) {
+        const int q = o / count, k = o - q * count;
+        const double v = fin[q * SMALL_MAX + k];
+        if (q < 3) {
+            if (acc)
+                acc[3 * (size_t)k + q] = G * v;
+        } else if (q < 6) {
+            if (jerk)
+                jerk[3 * (size_t)k + (q - 3)] = G * v;
+        } else if (pot) {
+            pot[k] = -G * v;
+        }
+    }
+}
+
+template <bool GUARD>
+__global__ void __launch_bounds__(SMALL_THREADS, 2) k_force_small(const SmallForceArgs A)
+{
+    __shared__ __align__(16) JMixed js[SMALL_STAGE * TILE_J];
+    __shared__ double fin[7 * SMALL_MAX];
+    const int count = A.n_i_dev ? *A.n_i_dev : A.n_i;
+    if (count <= 0 || count > SMALL_MAX)
+        return;  // uniform: the device-side size of a launch sized for at most SMALL_MAX
+    small_chunk_sums<GUARD>(A.jimg, A.ilist, count, A.n_j, A.tile0, A.ntiles, A.eps2, A.rmin2,
+                            A.scr.part + (size_t)blockIdx.x * 7 * SMALL_MAX, A.err, js);
+    if (small_reduce(count, A.scr, fin))
+        small_store(count, fin, A.G, A.acc, A.jerk, A.pot);
+}
+
+// Grid-wide barrier of a cooperative launch: one arrival per CTA, the last
+// one resets the count and advances the generation; the wait is bounded
+// (WAIT_LIMIT_NS), after which the CTA sets ERR_TIMEOUT and the caller
+// leaves the kernel.
+__device__ bool grid_barrier(unsigned *bar, unsigned *err)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        bool ok = true;
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g0) {
+                if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Block steps of small blocks (see loop_internal.cuh).  Entered after the
+// step kernels selected a block; leaves when the selected block has more than
+// SMALL_MAX members (the graph's force switch then takes it) or none.
+template <bool GUARD>
+__global__ void __launch_bounds__(SMALL_THREADS, 2) k_small_steps(const SmallStepArgs P)
+{
+    __shared__ __align__(16) JMixed js[SMALL_STAGE * TILE_J];
+    __shared__ double fin[7 * SMALL_MAX];
+    const StepArgs &A = P.st;
+    RunState *R = A.run;
+    for (;;) {
+        const int count = __ldcg(A.count_out);
+        if (count <= 0 || count > SMALL_MAX)
+            return;  // uniform: read after the barrier that followed its publication
+        const long long s = __ldcg(&R->steps);
+        const double tb = __ldcg(&R->t_last);
+        const int par = (int)(s & 1);
+        // the block's forces
+        small_chunk_sums<GUARD>(A.jm, A.ilist, count, A.n, P.tile0, P.ntiles, P.eps2, P.rmin2,
+                                P.scr.part + (size_t)blockIdx.x * 7 * SMALL_MAX, A.err, js);
+        // end times of the particles outside the block; fresh words for the next selection
+        int c0, c1;
+        chunk_of(A.n, c0, c1);
+        unsigned long long mn = ~0ull;
+        for (int i = c0 + (int)threadIdx.x; i < c1; i += SMALL_THREADS) {
+            const double end = __ldcg(A.bt + i) + __ldcg(A.bdt + i);
+            if (end != tb)
+                mn = min(mn, time_key(end));
+        }
+        mn = cta_min_u64(mn);
+        if (threadIdx.x == 0) {
+            atomicMin(&R->minw[par], mn);
+            if (blockIdx.x == 0) {
+                R->minw[par ^ 1] = ~0ull;
+                R->list_done = 0ull;
+            }
+        }
+        // the final sums, the members' corrector and their new end times, in one CTA
+        if (small_reduce(count, P.scr, fin)) {
+            // the step kernels only read the force rows; here they are written first (the context's buffers)
+            small_store(count, fin, P.G, const_cast<double *>(A.acc), const_cast<double *>(A.jerk), nullptr);
+            __syncthreads();  // the stored rows are read back by the corrector
+            if (threadIdx.x < 32) {
+                unsigned long long m2 = ~0ull;
+                const int k = (int)threadIdx.x;
+                if (k < count) {
+                    const double end = correct_at((size_t)__ldcg(A.ilist + k), k, tb, A.eta, A.dt_min, A.dt_max, 1,
+                                                  A.xp, A.vp, A.acc, A.jerk, A.bx, A.bv, A.ba, A.bj, A.bt, A.bdt);
+                    m2 = time_key(end);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    m2 = min(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                if (threadIdx.x == 0)
+                    atomicMin(&R->minw[par], m2);
+            }
+        }
+        if (!grid_barrier(P.bar, A.err))
+            return;
+        select_body(A);
+        if (!grid_barrier(P.bar, A.err))
+            return;
     }
 }
 
@@ -888,6 +1214,46 @@ __global__ void k_sum_parts(int n_parts, long long n_i, const double *__restrict
     } else if (pot) {
         pot[k - 6 * n_i] = s;
     }
+}
+
+cudaError_t launch_force_small(const SmallForceArgs &a, bool guard, cudaStream_t st)
+{
+    if (a.scr.chunks < 1 || (!a.n_i_dev && (a.n_i < 0 || a.n_i > SMALL_MAX)))
+        return cudaErrorInvalidValue;
+    if (!a.n_i_dev && a.n_i == 0)
+        return cudaSuccess;
+    if (guard)
+        k_force_small<true><<<a.scr.chunks, SMALL_THREADS, 0, st>>>(a);
+    else
+        k_force_small<false><<<a.scr.chunks, SMALL_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int small_steps_ctas_per_sm(bool guard)
+{
+    int n = 0;
+    if (guard)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_small_steps<true>, SMALL_THREADS, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_small_steps<false>, SMALL_THREADS, 0);
+    return n;
+}
+
+cudaError_t launch_small_steps(const SmallStepArgs &a, bool guard, int ctas, cudaStream_t st)
+{
+    if (ctas != a.scr.chunks)
+        return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(SMALL_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return guard ? cudaLaunchKernelEx(&cfg, k_small_steps<true>, a) : cudaLaunchKernelEx(&cfg, k_small_steps<false>, a);
 }
 
 cudaError_t launch_sum_parts(int n_parts, int64_t n_i, const double *parts, double *acc, double *jerk,

@@ -63,4 +63,59 @@ struct StepArgs {
 cudaError_t launch_block_step(const StepArgs &a, int ctas, cudaStream_t st);
 constexpr int STEP_CTAS_PER_SM = 2;
 
+// ---- small active blocks ----------------------------------------------------
+//
+// A block of at most SMALL_MAX i-particles against N j is a few hundred
+// thousand pair interactions: launch and latency, not arithmetic, set its
+// time.  The small-block force spreads the j tiles over G CTAs (one chunk
+// each), gives every i a warp whose lanes take the j, and adds the chunks'
+// double-single sums in two levels, in chunk order, inside the same kernel:
+// the last CTA of each group of SMALL_RG chunks sums its group, the last of
+// those sums the groups.  The small-step kernel runs whole block steps of
+// small blocks in one cooperative launch: force, corrector (in the CTA that
+// holds the final sums), then the selection and prediction of the next
+// block, with two grid barriers per step, until a larger block or the end of
+// the run comes up.
+constexpr int SMALL_MAX = 32;
+constexpr int SMALL_RG = 16;
+
+// Scratch of the small-block force for a grid of `chunks` CTAs.
+struct SmallScratch {
+    float2 *part;      // [chunks][7][SMALL_MAX] (hi, lo) sums of each chunk
+    float2 *gpart;     // [groups][7][SMALL_MAX] sums of each group of SMALL_RG chunks
+    unsigned *tickets; // [groups + 1] arrival counters, each reset by its last arrival
+    int chunks;
+};
+__host__ __device__ inline int small_groups(int chunks) { return (chunks + SMALL_RG - 1) / SMALL_RG; }
+
+struct SmallForceArgs {
+    const JMixed *jimg;
+    const int32_t *ilist;    // n_i entries (device); nullptr = identity
+    int n_i;
+    const int32_t *n_i_dev;  // if set, the block size is read here at launch
+    int n_j;
+    int tile0, ntiles;       // j tiles summed: [tile0, tile0 + ntiles)
+    float eps2, rmin2;
+    double G;
+    double *acc, *jerk, *pot;  // outputs in i-list order; any may be null
+    unsigned *err;
+    SmallScratch scr;
+};
+// One small-block force launch of scr.chunks CTAs (n_i <= SMALL_MAX).
+cudaError_t launch_force_small(const SmallForceArgs &a, bool guard, cudaStream_t st);
+
+// The small-step kernel: as long as the selected block has at most SMALL_MAX
+// members, force, correct and select in one cooperative launch over `ctas`
+// CTAs (the step kernels' grid, so the list layout is theirs).
+struct SmallStepArgs {
+    StepArgs st;
+    SmallScratch scr;
+    unsigned *bar;  // grid barrier: [0] arrivals, [1] generation
+    int tile0, ntiles;
+    float eps2, rmin2;
+    double G;
+};
+cudaError_t launch_small_steps(const SmallStepArgs &a, bool guard, int ctas, cudaStream_t st);
+int small_steps_ctas_per_sm(bool guard);
+
 }  // namespace kirin
