@@ -89,10 +89,10 @@ struct kirin_ctx {
     RunState *h_run = nullptr;      // pinned mirror
     int32_t *d_step_counts = nullptr;  // per-CTA list offsets and counts of the step kernels
     int step_ctas = 0;
-    // small active blocks (at most SMALL_MAX i): chunk and group sums, tickets and the grid barrier
-    // of the small-block kernels, whose grid is step_ctas CTAs
-    float2 *d_small_part = nullptr, *d_small_gpart = nullptr;
-    unsigned *d_small_tk = nullptr, *d_small_bar = nullptr;
+    // small active blocks (at most SMALL_MAX i): the chunk sums and the grid barrier of the
+    // small-block kernels, whose grid is step_ctas CTAs
+    float2 *d_small_part = nullptr;
+    unsigned *d_small_bar = nullptr;
     bool small_steps = true;  // device-driven runs take small blocks in the small-step kernel
     int small_resident = -1;  // CTAs per SM of the small-step kernel (-1: not asked yet)
 
@@ -260,7 +260,7 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
 
 SmallScratch small_scratch(const kirin_ctx *c)
 {
-    return SmallScratch{c->d_small_part, c->d_small_gpart, c->d_small_tk, c->step_ctas};
+    return SmallScratch{c->d_small_part, c->step_ctas};
 }
 
 int ensure_partial(kirin_ctx *c, size_t doubles)
@@ -434,7 +434,7 @@ void free_all(kirin_ctx *c)
     void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
                     c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
                     c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts, c->d_send, c->d_recv,
-                    c->d_small_part, c->d_small_gpart, c->d_small_tk, c->d_small_bar};
+                    c->d_small_part, c->d_small_bar};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -711,8 +711,7 @@ int hermite_run_device(kirin_ctx *c, double t_end, int64_t max_steps, int64_t *n
     }
     // the pinned mirror may still be the source or target of the last run's copies
     CK(c, cudaStreamSynchronize(c->stream));
-    // fresh tickets and barrier words (a run that gave up on a wait may have left them mid-count)
-    CK(c, cudaMemsetAsync(c->d_small_tk, 0, (size_t)(small_groups(c->step_ctas) + 1) * sizeof(unsigned), c->stream));
+    // fresh barrier words (a run that gave up on a wait may have left them mid-count)
     CK(c, cudaMemsetAsync(c->d_small_bar, 0, 2 * sizeof(unsigned), c->stream));
     RunState init{};
     init.t_end = t_end;
@@ -837,13 +836,9 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
         ok = false;
     c->step_ctas = std::max(c->nsm, 1) * STEP_CTAS_PER_SM;
     dalloc((void **)&c->d_step_counts, 2 * (size_t)c->step_ctas * sizeof(int32_t));
-    const int small_ng = small_groups(c->step_ctas);
     dalloc((void **)&c->d_small_part, (size_t)c->step_ctas * 7 * SMALL_MAX * sizeof(float2));
-    dalloc((void **)&c->d_small_gpart, (size_t)small_ng * 7 * SMALL_MAX * sizeof(float2));
-    dalloc((void **)&c->d_small_tk, (size_t)(small_ng + 1) * sizeof(unsigned));
     dalloc((void **)&c->d_small_bar, 2 * sizeof(unsigned));
-    if (ok && (cudaMemsetAsync(c->d_small_tk, 0, (size_t)(small_ng + 1) * sizeof(unsigned), c->stream) != cudaSuccess ||
-               cudaMemsetAsync(c->d_small_bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess))
+    if (ok && cudaMemsetAsync(c->d_small_bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess)
         ok = false;
     if (ok && cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream) != cudaSuccess)
         ok = false;

@@ -778,106 +778,105 @@ __device__ void small_chunk_sums(const JMixed *__restrict__ J, const int32_t *il
     __syncthreads();  // the staging space is free for the caller again
 }
 
-// The two-level sum of the chunks' sums, in chunk order: returns true in the
-// one CTA that ends up with the final sums, fin[q * SMALL_MAX + k] (FP64,
-// before G).  Each ticket is reset by its last arrival.
-__device__ bool small_reduce(int count, const SmallScratch &S, double *fin)
+// Member k's seven sums over all G chunks, in one CTA: thread t adds chunks
+// t, t + 256, ... in order (every load first), then the 256 threads' sums
+// meet in a fixed tree (xor shuffles in each warp, the warps in order), all in
+// double-single.  Returns the FP64 sums (before G) in fin[0..6] (shared), valid
+// after the call for every thread.
+__device__ void small_member_sums(const float2 *part, int G, int k, double *fin)
 {
-    __shared__ int last_s;
-    const int G = (int)gridDim.x, c = (int)blockIdx.x;
-    const int ng = small_groups(G);
-    const int g = c / SMALL_RG;
-    const int g0 = g * SMALL_RG, gsize = min(SMALL_RG, G - g0);
-    const int nout = 7 * count;
-    __threadfence();  // this chunk's sums before its arrival
-    __syncthreads();
-    if (threadIdx.x == 0)
-        last_s = atomicAdd(&S.tickets[g], 1u) + 1u == (unsigned)gsize;
-    __syncthreads();
-    if (!last_s)
-        return false;
-    __threadfence();
-    for (int o = (int)threadIdx.x; o < nout; o += SMALL_THREADS) {
-        const int q = o / count, k = o - q * count;
-        float2 v[SMALL_RG];  // every chunk's value first: one memory latency, not SMALL_RG
+    constexpr int PER = 2;  // chunks per thread with up to 512 chunks
+    __shared__ float2 wsum[SMALL_WARPS][7];
+    const int t = (int)threadIdx.x, warp = t >> 5, lane = t & 31;
+    float2 v[7][PER];
 #pragma unroll
-        for (int cc = 0; cc < SMALL_RG; ++cc)
-            v[cc] = cc < gsize ? __ldcg(&S.part[((size_t)(g0 + cc) * 7 + q) * SMALL_MAX + k]) : make_float2(0.f, 0.f);
-        float hi = 0.f, lo = 0.f;
+    for (int q = 0; q < 7; ++q)
 #pragma unroll
-        for (int cc = 0; cc < SMALL_RG; ++cc) {
-            if (cc < gsize) {
-                two_sum(hi, lo, v[cc].x);
-                lo = __fadd_rn(lo, v[cc].y);
-            }
+        for (int r = 0; r < PER; ++r) {
+            const int c = t + r * SMALL_THREADS;
+            v[q][r] = c < G ? __ldcg(&part[((size_t)c * 7 + q) * SMALL_MAX + k]) : make_float2(0.f, 0.f);
         }
-        S.gpart[((size_t)g * 7 + q) * SMALL_MAX + k] = make_float2(hi, lo);
-    }
-    if (threadIdx.x == 0)
-        S.tickets[g] = 0u;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0)
-        last_s = atomicAdd(&S.tickets[ng], 1u) + 1u == (unsigned)ng;
-    __syncthreads();
-    if (!last_s)
-        return false;
-    __threadfence();
-    for (int o = (int)threadIdx.x; o < nout; o += SMALL_THREADS) {
-        const int q = o / count, k = o - q * count;
-        float hi = 0.f, lo = 0.f;
-        for (int g1 = 0; g1 < ng; g1 += SMALL_RG) {  // groups SMALL_RG at a time, loads first
-            float2 v[SMALL_RG];
+    float hi[7], lo[7];
 #pragma unroll
-            for (int gg = 0; gg < SMALL_RG; ++gg)
-                v[gg] = g1 + gg < ng ? __ldcg(&S.gpart[((size_t)(g1 + gg) * 7 + q) * SMALL_MAX + k])
-                                     : make_float2(0.f, 0.f);
+    for (int q = 0; q < 7; ++q) {
+        hi[q] = lo[q] = 0.f;
 #pragma unroll
-            for (int gg = 0; gg < SMALL_RG; ++gg) {
-                if (g1 + gg < ng) {
-                    two_sum(hi, lo, v[gg].x);
-                    lo = __fadd_rn(lo, v[gg].y);
-                }
-            }
+        for (int r = 0; r < PER; ++r) {
+            two_sum(hi[q], lo[q], v[q][r].x);
+            lo[q] = __fadd_rn(lo[q], v[q][r].y);
         }
-        fin[q * SMALL_MAX + k] = (double)hi + (double)lo;
     }
-    if (threadIdx.x == 0)
-        S.tickets[ng] = 0u;
+    for (int c = t + PER * SMALL_THREADS; c < G; c += SMALL_THREADS)  // beyond 512 chunks: not in one round
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const float2 w = __ldcg(&part[((size_t)c * 7 + q) * SMALL_MAX + k]);
+            two_sum(hi[q], lo[q], w.x);
+            lo[q] = __fadd_rn(lo[q], w.y);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi[q], o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo[q], o);
+            two_sum(hi[q], lo[q], h2);
+            lo[q] = __fadd_rn(lo[q], l2);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            wsum[warp][q] = make_float2(hi[q], lo[q]);
     __syncthreads();
-    return true;
+    if (t < 7) {
+        float h = 0.f, l = 0.f;
+#pragma unroll
+        for (int w = 0; w < SMALL_WARPS; ++w) {
+            two_sum(h, l, wsum[w][t].x);
+            l = __fadd_rn(l, wsum[w][t].y);
+        }
+        fin[t] = (double)h + (double)l;
+    }
+    __syncthreads();
 }
 
-// Final values of the sums (acc, jerk: G sum; pot: -G sum) in i-list order.
-__device__ void small_store(int count, const double *fin, double G, double *acc, double *jerk, double *pot)
+// Member k's final values (acc, jerk: G sum; pot: -G sum) in i-list row k.
+__device__ __forceinline__ void small_store_member(int k, const double *fin, double G, double *acc, double *jerk,
+                                                   double *pot)
 {
-    for (int o = (int)threadIdx.x; o < 7 * count; o += SMALL_THREADS) {
-        const int q = o / count, k = o - q * count;
-        const double v = fin[q * SMALL_MAX + k];
-        if (q < 3) {
-            if (acc)
-                acc[3 * (size_t)k + q] = G * v;
-        } else if (q < 6) {
-            if (jerk)
-                jerk[3 * (size_t)k + (q - 3)] = G * v;
-        } else if (pot) {
-            pot[k] = -G * v;
-        }
+    const int q = (int)threadIdx.x;
+    if (q < 3) {
+        if (acc)
+            acc[3 * (size_t)k + q] = G * fin[q];
+    } else if (q < 6) {
+        if (jerk)
+            jerk[3 * (size_t)k + (q - 3)] = G * fin[q];
+    } else if (q == 6 && pot) {
+        pot[k] = -G * fin[6];
     }
 }
 
+// The small-block force in two kernels: every chunk's sums, then one CTA per
+// member adds them up and stores the member's row.
 template <bool GUARD>
 __global__ void __launch_bounds__(SMALL_THREADS, 2) k_force_small(const SmallForceArgs A)
 {
     __shared__ __align__(16) JMixed js[SMALL_STAGE * TILE_J];
-    __shared__ double fin[7 * SMALL_MAX];
     const int count = A.n_i_dev ? *A.n_i_dev : A.n_i;
     if (count <= 0 || count > SMALL_MAX)
         return;  // uniform: the device-side size of a launch sized for at most SMALL_MAX
     small_chunk_sums<GUARD>(A.jimg, A.ilist, count, A.n_j, A.tile0, A.ntiles, A.eps2, A.rmin2,
                             A.scr.part + (size_t)blockIdx.x * 7 * SMALL_MAX, A.err, js);
-    if (small_reduce(count, A.scr, fin))
-        small_store(count, fin, A.G, A.acc, A.jerk, A.pot);
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_final(const SmallForceArgs A)
+{
+    __shared__ double fin[7];
+    const int count = A.n_i_dev ? *A.n_i_dev : A.n_i;
+    const int k = (int)blockIdx.x;
+    if (k >= count)
+        return;  // uniform over the CTA
+    small_member_sums(A.scr.part, A.scr.chunks, k, fin);
+    small_store_member(k, fin, A.G, A.acc, A.jerk, A.pot);
 }
 
 // Grid-wide barrier of a cooperative launch: one arrival per CTA, the last
@@ -922,7 +921,7 @@ template <bool GUARD>
 __global__ void __launch_bounds__(SMALL_THREADS, 2) k_small_steps(const SmallStepArgs P)
 {
     __shared__ __align__(16) JMixed js[SMALL_STAGE * TILE_J];
-    __shared__ double fin[7 * SMALL_MAX];
+    __shared__ double fin[7];
     const StepArgs &A = P.st;
     RunState *R = A.run;
     for (;;) {
@@ -952,24 +951,19 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) k_small_steps(const SmallSte
                 R->list_done = 0ull;
             }
         }
-        // the final sums, the members' corrector and their new end times, in one CTA
-        if (small_reduce(count, P.scr, fin)) {
+        if (!grid_barrier(P.bar, A.err))
+            return;
+        // member k in CTA k: its sums over every chunk, its row, its corrector and new end time
+        const int k = (int)blockIdx.x;
+        if (k < count) {
+            small_member_sums(P.scr.part, (int)gridDim.x, k, fin);
             // the step kernels only read the force rows; here they are written first (the context's buffers)
-            small_store(count, fin, P.G, const_cast<double *>(A.acc), const_cast<double *>(A.jerk), nullptr);
-            __syncthreads();  // the stored rows are read back by the corrector
-            if (threadIdx.x < 32) {
-                unsigned long long m2 = ~0ull;
-                const int k = (int)threadIdx.x;
-                if (k < count) {
-                    const double end = correct_at((size_t)__ldcg(A.ilist + k), k, tb, A.eta, A.dt_min, A.dt_max, 1,
-                                                  A.xp, A.vp, A.acc, A.jerk, A.bx, A.bv, A.ba, A.bj, A.bt, A.bdt);
-                    m2 = time_key(end);
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    m2 = min(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-                if (threadIdx.x == 0)
-                    atomicMin(&R->minw[par], m2);
+            small_store_member(k, fin, P.G, const_cast<double *>(A.acc), const_cast<double *>(A.jerk), nullptr);
+            __syncthreads();  // the stored row is read back by the corrector
+            if (threadIdx.x == 0) {
+                const double end = correct_at((size_t)__ldcg(A.ilist + k), k, tb, A.eta, A.dt_min, A.dt_max, 1, A.xp,
+                                              A.vp, A.acc, A.jerk, A.bx, A.bv, A.ba, A.bj, A.bt, A.bdt);
+                atomicMin(&R->minw[par], time_key(end));
             }
         }
         if (!grid_barrier(P.bar, A.err))
@@ -1226,6 +1220,7 @@ cudaError_t launch_force_small(const SmallForceArgs &a, bool guard, cudaStream_t
         k_force_small<true><<<a.scr.chunks, SMALL_THREADS, 0, st>>>(a);
     else
         k_force_small<false><<<a.scr.chunks, SMALL_THREADS, 0, st>>>(a);
+    k_small_final<<<a.n_i_dev ? SMALL_MAX : a.n_i, SMALL_THREADS, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -68,25 +68,20 @@ constexpr int STEP_CTAS_PER_SM = 2;
 // A block of at most SMALL_MAX i-particles against N j is a few hundred
 // thousand pair interactions: launch and latency, not arithmetic, set its
 // time.  The small-block force spreads the j tiles over G CTAs (one chunk
-// each), gives every i a warp whose lanes take the j, and adds the chunks'
-// double-single sums in two levels, in chunk order, inside the same kernel:
-// the last CTA of each group of SMALL_RG chunks sums its group, the last of
-// those sums the groups.  The small-step kernel runs whole block steps of
-// small blocks in one cooperative launch: force, corrector (in the CTA that
-// holds the final sums), then the selection and prediction of the next
-// block, with two grid barriers per step, until a larger block or the end of
-// the run comes up.
+// each; a lane per member, the warps over the chunk's j) and leaves each
+// chunk's double-single sums in a scratch; then one CTA per member adds its
+// sums over the chunks in one round of loads and a fixed tree.  The
+// small-step kernel runs whole block steps of small blocks in one cooperative
+// launch: chunk sums, a grid barrier, the member CTAs' sums and correctors, a
+// barrier, the selection and prediction of the next block, a barrier, until a
+// larger block or the end of the run comes up.
 constexpr int SMALL_MAX = 32;
-constexpr int SMALL_RG = 16;
 
 // Scratch of the small-block force for a grid of `chunks` CTAs.
 struct SmallScratch {
-    float2 *part;      // [chunks][7][SMALL_MAX] (hi, lo) sums of each chunk
-    float2 *gpart;     // [groups][7][SMALL_MAX] sums of each group of SMALL_RG chunks
-    unsigned *tickets; // [groups + 1] arrival counters, each reset by its last arrival
+    float2 *part;  // [chunks][7][SMALL_MAX] (hi, lo) sums of each chunk
     int chunks;
 };
-__host__ __device__ inline int small_groups(int chunks) { return (chunks + SMALL_RG - 1) / SMALL_RG; }
 
 struct SmallForceArgs {
     const JMixed *jimg;
@@ -101,7 +96,7 @@ struct SmallForceArgs {
     unsigned *err;
     SmallScratch scr;
 };
-// One small-block force launch of scr.chunks CTAs (n_i <= SMALL_MAX).
+// One small-block force (n_i <= SMALL_MAX): the chunk kernel over scr.chunks CTAs, then the member kernel.
 cudaError_t launch_force_small(const SmallForceArgs &a, bool guard, cudaStream_t st);
 
 // The small-step kernel: as long as the selected block has at most SMALL_MAX
