@@ -118,11 +118,9 @@ int kirin_set_launch_table_for(kirin_ctx *ctx, int32_t kind, int32_t n_entries, 
 int kirin_get_launch_for(kirin_ctx *ctx, int32_t kind, int64_t n_i, int32_t *groups, int32_t *n_split);
 
 /* The shape that a force call for n_i i-particles would use now.  groups = 0
- * names the small-block kernel, which serves automatic mixed-precision
- * acc + jerk + pot calls with n_i <= 32 (the small active blocks of Sect.
- * 3.2): n_split = 2 x the SM count CTAs each take a range of the j tiles,
- * give every i a warp whose lanes take the j, and add their double-single
- * sums in two levels, in range order, inside the same kernel. */
+ * names the tiny-block kernel, which serves automatic mixed-precision calls
+ * with n_i <= 8 (and n_j <= 512 x the SM count): n_split CTAs each stage a
+ * range of j in shared memory and give every i a warp. */
 int kirin_get_launch(kirin_ctx *ctx, int64_t n_i, int32_t *groups, int32_t *n_split);
 
 /* GPU_set_j_particle (Appendix A), in bulk: particles [first, first + n) get
@@ -252,23 +250,6 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
 /* Choose how kirin_hermite_run drives its block steps: enable != 0, one
  * device-driven graph per call (default); 0, one host round trip per step. */
 int kirin_set_device_loop(kirin_ctx *ctx, int32_t enable);
-
-/* Device-driven runs (kirin_hermite_run with the device loop, mixed
- * precision) take every block of at most 32 members in one cooperative
- * small-step kernel: the small-block force, the corrector in the CTA that
- * holds the final sums, and the selection and prediction of the next block,
- * with two grid barriers per block step, until a larger block or the end of
- * the run comes up.  Results are those of the host-driven loop, whose small
- * blocks use the same small-block force.  Enabled by default; it is off under
- * a fixed launch shape (kirin_set_launch), which names the regular kernels
- * for every block, and on GPUs that cannot hold its grid (2 CTAs per SM) at
- * once.  Every grid-barrier wait is bounded: a wait that gives up ends the
- * run with KIRIN_ETIMEOUT.  Errors: EINVAL (NULL ctx). */
-int kirin_set_small_steps(kirin_ctx *ctx, int32_t enable);
-/* *active = 1 if device-driven runs of the context use the small-step kernel
- * now (enabled, mixed precision, no fixed shape, its grid resident, and its
- * cooperative launch accepted in the run's graph), else 0. */
-int kirin_get_small_steps(kirin_ctx *ctx, int32_t *active);
 
 /* One shared step of size dt for all particles (no step-size update). */
 int kirin_hermite_shared_step(kirin_ctx *ctx, double dt);

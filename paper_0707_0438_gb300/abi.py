@@ -83,8 +83,6 @@ _SIGS = {
     "kirin_hermite_block_step": (ctypes.c_int, [_P, _D, _PD, _PI64]),
     "kirin_hermite_run": (ctypes.c_int, [_P, _D, _I64, _PI64, _PD]),
     "kirin_set_device_loop": (ctypes.c_int, [_P, _I32]),
-    "kirin_set_small_steps": (ctypes.c_int, [_P, _I32]),
-    "kirin_get_small_steps": (ctypes.c_int, [_P, _PI32]),
     "kirin_hermite_shared_run": (ctypes.c_int, [_P, _D, _I64]),
     "kirin_hermite_shared_step": (ctypes.c_int, [_P, _D]),
     "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
@@ -397,16 +395,6 @@ class Kirin:
 
     def set_device_loop(self, enable=True):
         self._check(self.lib.kirin_set_device_loop(self.ctx, 1 if enable else 0), "kirin_set_device_loop")
-
-    def set_small_steps(self, enable=True):
-        """Device-driven runs take blocks of at most 32 members in the cooperative small-step kernel."""
-        self._check(self.lib.kirin_set_small_steps(self.ctx, 1 if enable else 0), "kirin_set_small_steps")
-
-    def small_steps_active(self):
-        """Whether device-driven runs use the small-step kernel now."""
-        a = ctypes.c_int32()
-        self._check(self.lib.kirin_get_small_steps(self.ctx, ctypes.byref(a)), "kirin_get_small_steps")
-        return bool(a.value)
 
     def hermite_shared_step(self, dt):
         self._check(self.lib.kirin_hermite_shared_step(self.ctx, float(dt)), "kirin_hermite_shared_step")

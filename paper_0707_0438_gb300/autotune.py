@@ -129,7 +129,7 @@ def tune(k: Kirin, n_j: int, reps: int = 3, seed: int = 5, quick: bool = True, d
         k.set_launch(0, 0)
         k.set_launch_table([])
         auto = k.get_launch(n_i)
-        if auto[0] == 0:  # the small-block kernel serves this size; time the regular shapes around 8 groups
+        if auto[0] == 0:  # the tiny-block kernel serves this size; time the regular shapes around 8 groups
             auto = (8, 1)
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         cands = _candidates(auto, ntiles, big=n_i >= 16 * nsm * 512)

@@ -33,7 +33,6 @@ struct RunKey {
     int32_t n_classes;
     int32_t class_max[MAX_SEL_CLASSES];
     Shape shape[MAX_SEL_CLASSES];
-    int32_t small_steps;
 };
 
 struct kirin_ctx {
@@ -89,12 +88,6 @@ struct kirin_ctx {
     RunState *h_run = nullptr;      // pinned mirror
     int32_t *d_step_counts = nullptr;  // per-CTA list offsets and counts of the step kernels
     int step_ctas = 0;
-    // small active blocks (at most SMALL_MAX i): the chunk sums and the grid barrier of the
-    // small-block kernels, whose grid is step_ctas CTAs
-    float2 *d_small_part = nullptr;
-    unsigned *d_small_bar = nullptr;
-    bool small_steps = true;  // device-driven runs take small blocks in the small-step kernel
-    int small_resident = -1;  // CTAs per SM of the small-step kernel (-1: not asked yet)
 
     // launch-shape override (0 = automatic), tuned table and occupancy cache
     int fix_groups = 0, fix_split = 0;
@@ -221,8 +214,12 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
         Shape s{c->fix_groups, std::min(c->fix_split, std::max(1, ntiles))};
         return s;
     }
-    if (prec == KIRIN_MIXED && mode == MODE_ACC_JERK_POT && n_i <= SMALL_MAX)
-        return Shape{0, c->step_ctas};  // the small-block kernel: a j chunk per CTA, a warp per i
+    if (prec == KIRIN_MIXED && mode == MODE_ACC_JERK_POT && n_i <= TINY_MAX &&
+        (int64_t)ntiles * TILE_J <= (int64_t)TINY_JCHUNK * 2 * c->nsm) {
+        // tiny block: j ranges of 64..TINY_JCHUNK records, about two CTAs per SM
+        const int ctas = std::max(1, std::min(2 * c->nsm, ntiles * TILE_J / 64));
+        return Shape{0, ctas};
+    }
     const int kind = call_kind(mode);
     if (kind >= 0 && c->table_n[kind] > 0 && prec == c->table_prec[kind]) {
         for (int k = 0; k < c->table_n[kind]; ++k)
@@ -256,11 +253,6 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
         }
     }
     return best;
-}
-
-SmallScratch small_scratch(const kirin_ctx *c)
-{
-    return SmallScratch{c->d_small_part, c->step_ctas};
 }
 
 int ensure_partial(kirin_ctx *c, size_t doubles)
@@ -302,28 +294,6 @@ int enqueue_force(kirin_ctx *c, cudaStream_t st, Shape s, int64_t n_i, const int
         return KIRIN_OK;
     int tile0 = 0;
     const int ntiles = part_tiles(n_j, c->part, c->n_parts, &tile0);
-    if (s.groups == 0) {  // the small-block kernel (mixed, acc + jerk + pot, n_i <= SMALL_MAX)
-        if (c->prec != KIRIN_MIXED || mode != MODE_ACC_JERK_POT || n_i > SMALL_MAX || accumulate)
-            return set_msg(c, KIRIN_EINVAL, "small-block kernel: unsupported call");
-        SmallForceArgs b{};
-        b.jimg = c->jm;
-        b.ilist = d_ilist;
-        b.n_i = (int)n_i;
-        b.n_i_dev = n_i_dev;
-        b.n_j = n_j;
-        b.tile0 = tile0;
-        b.ntiles = ntiles;
-        b.eps2 = (float)(c->eps * c->eps);
-        b.rmin2 = (float)(c->r_min * c->r_min);
-        b.G = c->G;
-        b.acc = acc;
-        b.jerk = jerk;
-        b.pot = pot;
-        b.err = c->d_err;
-        b.scr = small_scratch(c);
-        CK(c, launch_force_small(b, guard_on(c), st));
-        return KIRIN_OK;
-    }
     ForceArgs a{};
     a.jimg = c->prec == KIRIN_MIXED ? (const void *)c->jm : (const void *)c->jd;
     a.ilist = d_ilist;
@@ -362,7 +332,7 @@ int enqueue_force(kirin_ctx *c, cudaStream_t st, Shape s, int64_t n_i, const int
 // Doubles of split partials a launch of n_i i-particles with shape s needs.
 size_t partial_doubles(const kirin_ctx *c, Shape s, int64_t n_i, int mode)
 {
-    if (s.n_split <= 1 || s.groups == 0)  // the small-block kernel keeps its sums in its own scratch
+    if (s.n_split <= 1)
         return 0;
     return (size_t)s.n_split * (mode == MODE_NN ? 9 : 7) * (size_t)round_up(n_i, shape_i_cta(s, c->prec == KIRIN_MIXED));
 }
@@ -433,8 +403,7 @@ void free_all(kirin_ctx *c)
 {
     void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
                     c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
-                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts, c->d_send, c->d_recv,
-                    c->d_small_part, c->d_small_bar};
+                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts, c->d_send, c->d_recv};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -493,44 +462,27 @@ RunPlan plan_run(kirin_ctx *c)
 {
     RunPlan p;
     const int64_t n = c->n_j;
-    // halving from the whole set down; every block of at most SMALL_MAX members falls in the lowest
-    // class, which the small-block kernel serves
     int64_t hi = n;
     int32_t desc[MAX_SEL_CLASSES];
     int k = 0;
-    while (hi > SMALL_MAX && k < MAX_SEL_CLASSES - 1) {
+    while (hi > TINY_MAX && k < MAX_SEL_CLASSES - 1) {
         desc[k++] = (int32_t)hi;
         hi = (hi + 1) / 2;
     }
-    desc[k++] = (int32_t)std::min<int64_t>(hi, SMALL_MAX);
+    desc[k++] = (int32_t)hi;
     p.n_classes = k;
     const int ntiles = (int)((std::max<int64_t>(n, 1) + TILE_J - 1) / TILE_J);
     for (int q = 0; q < k; ++q) {
         p.class_max[q] = desc[k - 1 - q];
-        // a class above the small-block bound needs a regular shape (its grid covers class_max)
-        const int64_t floor_rep = p.class_max[q] > SMALL_MAX ? SMALL_MAX + 1 : 1;
+        // a class above the tiny-block bound needs a regular shape (its grid covers class_max)
+        const int64_t floor_rep = p.class_max[q] > TINY_MAX ? TINY_MAX + 1 : 1;
         const int64_t rep = std::max<int64_t>(floor_rep, (int64_t)(0.7 * p.class_max[q]));
         p.shape[q] = choose_shape(c, rep, ntiles, c->prec, MODE_ACC_JERK_POT, guard_on(c));
     }
     return p;
 }
 
-// Whether device-driven runs take blocks of at most SMALL_MAX members in the
-// small-step kernel: mixed precision, no fixed launch shape (which names the
-// regular kernels for every block), and its grid resident on this GPU.
-bool small_steps_on(kirin_ctx *c)
-{
-    if (!c->small_steps || c->prec != KIRIN_MIXED || (c->fix_groups > 0 && c->fix_split > 0))
-        return false;
-    if (c->small_resident < 0) {
-        const int a = small_steps_ctas_per_sm(false), b = small_steps_ctas_per_sm(true);
-        cudaGetLastError();
-        c->small_resident = std::min(a, b);
-    }
-    return c->small_resident >= STEP_CTAS_PER_SM;
-}
-
-RunKey run_key(kirin_ctx *c, const RunPlan &p)
+RunKey run_key(const kirin_ctx *c, const RunPlan &p)
 {
     RunKey k;
     memset(&k, 0, sizeof(k));
@@ -540,7 +492,6 @@ RunKey run_key(kirin_ctx *c, const RunPlan &p)
     k.prec = c->prec;
     k.partial = c->d_partial;
     k.n_classes = p.n_classes;
-    k.small_steps = small_steps_on(c) ? 1 : 0;
     for (int q = 0; q < p.n_classes; ++q) {
         k.class_max[q] = p.class_max[q];
         k.shape[q] = p.shape[q];
@@ -573,7 +524,6 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     cudaStreamCaptureStatus status;
     StepArgs a{};
     const int n = (int)c->n_j;
-    const bool small = small_steps_on(c);
 
     CKG(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     CKG(cudaGraphCreate(&top, 0));
@@ -625,18 +575,6 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     for (int u = 0; u < RUN_UNROLL; ++u) {
         a.branch = h_branch[u];
         CKG(launch_block_step(a, c->step_ctas, cs));
-        if (small) {
-            SmallStepArgs sa{};
-            sa.st = a;
-            sa.scr = small_scratch(c);
-            sa.bar = c->d_small_bar;
-            sa.tile0 = 0;
-            sa.ntiles = (int)(a.n_pad / TILE_J);
-            sa.eps2 = (float)(c->eps * c->eps);
-            sa.rmin2 = (float)(c->r_min * c->r_min);
-            sa.G = c->G;
-            CKG(launch_small_steps(sa, guard_on(c), c->step_ctas, cs));
-        }
         CKG(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cap_graph, &deps, nullptr, &ndeps));
         sp[u].type = cudaGraphNodeTypeConditional;
         sp[u].conditional.handle = h_branch[u];
@@ -695,24 +633,14 @@ int hermite_run_device(kirin_ctx *c, double t_end, int64_t max_steps, int64_t *n
             c->run_exec = nullptr;
         }
         rc = build_run_graph(c, p, &c->run_exec);
-        if (rc && small_steps_on(c)) {
-            // no cooperative kernel in this graph (the small-step kernel's CTAs wait on one another, so it
-            // runs only as a cooperative launch): small blocks go through the force switch instead
-            c->small_resident = 0;
-            cudaGetLastError();
-            rc = build_run_graph(c, p, &c->run_exec);
-        }
         if (rc) {
             c->run_exec = nullptr;
             return rc;
         }
-        const RunKey built = run_key(c, p);  // the fallback above changes what was built
-        memcpy(&c->run_key, &built, sizeof(built));
+        memcpy(&c->run_key, &key, sizeof(key));
     }
     // the pinned mirror may still be the source or target of the last run's copies
     CK(c, cudaStreamSynchronize(c->stream));
-    // fresh barrier words (a run that gave up on a wait may have left them mid-count)
-    CK(c, cudaMemsetAsync(c->d_small_bar, 0, 2 * sizeof(unsigned), c->stream));
     RunState init{};
     init.t_end = t_end;
     init.max_steps = (long long)std::max<int64_t>(max_steps, 0);
@@ -836,10 +764,6 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
         ok = false;
     c->step_ctas = std::max(c->nsm, 1) * STEP_CTAS_PER_SM;
     dalloc((void **)&c->d_step_counts, 2 * (size_t)c->step_ctas * sizeof(int32_t));
-    dalloc((void **)&c->d_small_part, (size_t)c->step_ctas * 7 * SMALL_MAX * sizeof(float2));
-    dalloc((void **)&c->d_small_bar, 2 * sizeof(unsigned));
-    if (ok && cudaMemsetAsync(c->d_small_bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess)
-        ok = false;
     if (ok && cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream) != cudaSuccess)
         ok = false;
     if (ok && cudaMemsetAsync(c->bt, 0, n * sizeof(double), c->stream) != cudaSuccess)
@@ -1364,23 +1288,6 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
         *n_pairs = pairs;
     DeviceGuard dg(ctx->device);
     return read_device_errors(ctx);
-}
-
-int kirin_set_small_steps(kirin_ctx *ctx, int32_t enable)
-{
-    if (!ctx)
-        return KIRIN_EINVAL;
-    ctx->small_steps = enable != 0;
-    return KIRIN_OK;
-}
-
-int kirin_get_small_steps(kirin_ctx *ctx, int32_t *active)
-{
-    if (!ctx || !active)
-        return KIRIN_EINVAL;
-    DeviceGuard dg(ctx->device);
-    *active = small_steps_on(ctx) ? 1 : 0;
-    return KIRIN_OK;
 }
 
 int kirin_set_device_loop(kirin_ctx *ctx, int32_t enable)

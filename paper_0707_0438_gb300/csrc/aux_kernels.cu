@@ -8,7 +8,6 @@
 
 #include "kirin_internal.cuh"
 #include "loop_internal.cuh"
-#include "pair_mixed.cuh"
 #include "tma.cuh"
 
 namespace kirin {
@@ -396,19 +395,7 @@ __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, dou
                                              const double *acc, const double *jerk, double *bx, double *bv,
                                              double *ba, double *bj, double *bt, double *bdt)
 {
-    // every input first (independent loads, one memory latency), then the arithmetic, then the stores
-    double a0v[3], j0v[3], a1v[3], j1v[3], xpv[3], vpv[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        a0v[c] = __ldcg(ba + 3 * i + c);
-        j0v[c] = __ldcg(bj + 3 * i + c);
-        a1v[c] = __ldcg(acc + 3 * (size_t)k + c);
-        j1v[c] = __ldcg(jerk + 3 * (size_t)k + c);
-        xpv[c] = __ldcg(xp + 3 * i + c);
-        vpv[c] = __ldcg(vp + 3 * i + c);
-    }
-    const double t_i = __ldcg(bt + i), dt_i = __ldcg(bdt + i);
-    const double dt = t_next - t_i;
+    const double dt = t_next - bt[i];
     const bool p2 = is_pow2(dt);
     const double idt = p2 ? __longlong_as_double((2046ll << 52) - (__double_as_longlong(dt) & 0x7ff0000000000000ll))
                           : 1.0 / dt;
@@ -419,13 +406,13 @@ __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, dou
     double A = 0.0, J = 0.0, N2 = 0.0, N3 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double a0 = a0v[c], j0 = j0v[c];
-        const double a1 = a1v[c], j1 = j1v[c];
+        const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
+        const double a1 = acc[3 * (size_t)k + c], j1 = jerk[3 * (size_t)k + c];
         const double da = a0 - a1;
         const double a2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da) * idt2;
         const double a3 = fma(dt6, j0 + j1, 12.0 * da) * idt3;
-        bx[3 * i + c] = fma(a3, c5, fma(a2, c4, xpv[c]));
-        bv[3 * i + c] = fma(a3, c4, fma(a2, c3, vpv[c]));
+        bx[3 * i + c] = fma(a3, c5, fma(a2, c4, xp[3 * i + c]));
+        bv[3 * i + c] = fma(a3, c4, fma(a2, c3, vp[3 * i + c]));
         ba[3 * i + c] = a1;
         bj[3 * i + c] = j1;
         const double a2e = fma(dt, a3, a2);  // a2 at the end of the step
@@ -458,7 +445,7 @@ __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, dou
         bdt[i] = q;
         return t_next + q;
     }
-    return t_next + dt_i;
+    return t_next + bdt[i];
 }
 
 __device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double t_next, double eta, double dt_min,
@@ -598,17 +585,15 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_correct(const StepArgs A)
 // Predict every j to t_next and list the next block.  One 64-bit atomic per
 // CTA reserves its range of the list (low word) and counts finished CTAs
 // (high word); the CTA that reserves last publishes the block at once (the
-// list itself is read only by later kernels, or after a grid barrier).
-// Shared by k_step_select and the small-step kernel, whose CTAs come back
-// to these words and particles after other CTAs changed them: loads bypass L1.
-__device__ void select_body(const StepArgs &A)
+// list itself is read only by later kernels).
+__global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A)
 {
     RunState *R = A.run;
-    const long long steps0 = __ldcg(&R->steps);
-    const double tn = key_time(__ldcg(&R->minw[steps0 & 1]));
-    const long long lim = __ldcg(&R->max_steps);
-    bool due = tn <= __ldcg(&R->t_end) && (lim <= 0 || steps0 < lim);
-    const bool stall = due && steps0 > 0 && !(tn > __ldcg(&R->t_last));
+    const long long steps0 = R->steps;
+    const double tn = key_time(R->minw[steps0 & 1]);
+    const long long lim = R->max_steps;
+    bool due = tn <= R->t_end && (lim <= 0 || steps0 < lim);
+    const bool stall = due && steps0 > 0 && !(tn > R->t_last);
     if (stall)
         due = false;
     if (!due) {
@@ -627,7 +612,7 @@ __device__ void select_body(const StepArgs &A)
     int c = 0;
     for (int k = c0 + threadIdx.x; k < c1; k += STEP_THREADS) {
         predict_one(k, A.n, tn, 1, A.bm, A.bx, A.bv, A.ba, A.bj, A.bt, A.xp, A.vp, A.jm, A.jd, A.err);
-        c += __ldcg(A.bt + k) + __ldcg(A.bdt + k) == tn;
+        c += A.bt[k] + A.bdt[k] == tn;
     }
     for (int k = A.n + blockIdx.x * STEP_THREADS + threadIdx.x; k < A.n_pad; k += gridDim.x * STEP_THREADS)
         predict_one(k, A.n, tn, 1, A.bm, A.bx, A.bv, A.ba, A.bj, A.bt, A.xp, A.vp, A.jm, A.jd, A.err);  // padding
@@ -647,7 +632,7 @@ __device__ void select_body(const StepArgs &A)
             *A.count_out = count;
             *A.t_next_out = tn;
             R->steps = steps0 + 1;
-            R->pairs = __ldcg(&R->pairs) + (double)count * (double)A.n_j;
+            R->pairs += (double)count * (double)A.n_j;
             R->t_last = tn;
             R->pending = count;
             cudaGraphSetConditional(A.branch, cls);
@@ -659,318 +644,13 @@ __device__ void select_body(const StepArgs &A)
         int base = base_s;
         for (int i0 = c0; i0 < c1; i0 += STEP_THREADS) {
             const int i = i0 + threadIdx.x;
-            const bool flag = i < c1 && __ldcg(A.bt + i) + __ldcg(A.bdt + i) == tn;
+            const bool flag = i < c1 && A.bt[i] + A.bdt[i] == tn;
             int all;
             const int rank = cta_rank(flag, all);
             if (flag)
                 A.ilist[base + rank] = i;
             base += all;
         }
-    }
-}
-
-__global__ void __launch_bounds__(STEP_THREADS) k_step_select(const StepArgs A) { select_body(A); }
-
-// ---- small active blocks (at most SMALL_MAX i-particles) -----------------------
-//
-// The chunk of CTA c is the j tiles [tile0 + c T / G, tile0 + (c + 1) T / G) of
-// the padded image (G CTAs, T tiles), staged in shared memory SMALL_STAGE
-// tiles at a time.  Lane l of every warp holds member l (lanes beyond the
-// block idle), and warp w takes the record pairs (2p, 2p + 1) of each staged
-// piece with p = w mod SMALL_WARPS, the two records in the two float2 lanes
-// of the pair body (a broadcast shared-memory read for the whole warp; the
-// member's own record gets zero mass).  Lane sums are folded into
-// double-single after every staged piece; the warps' sums of a member meet in
-// warp order in shared memory, and the chunk's seven sums per member go to
-// the chunk's slots of the scratch.
-
-constexpr int SMALL_THREADS = 256;
-constexpr int SMALL_WARPS = SMALL_THREADS / 32;
-constexpr int SMALL_STAGE = 4;  // j tiles in shared memory at a time
-static_assert(SMALL_MAX == 32, "a lane per member");
-static_assert((size_t)SMALL_WARPS * 7 * 32 * sizeof(float2) <= SMALL_STAGE * TILE_J * sizeof(JMixed),
-              "the warps' sums fit in the staging space");
-
-__device__ __forceinline__ JMixed load_record(const JMixed *J, int r)
-{
-    JMixed out;
-#pragma unroll
-    for (int c = 0; c < 5; ++c)
-        out.q[c] = __ldcg(&J[r].q[c]);
-    return out;
-}
-
-template <bool GUARD>
-__device__ void small_chunk_sums(const JMixed *__restrict__ J, const int32_t *ilist, int count, int n_j, int tile0,
-                                 int ntiles, float eps2, float rmin2, float2 *part, unsigned *err, JMixed *js)
-{
-    const int G = (int)gridDim.x, c = (int)blockIdx.x;
-    const int tb = tile0 + (int)((long long)ntiles * c / G);
-    const int te = tile0 + (int)((long long)ntiles * (c + 1) / G);
-    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-    int i = -1;
-    IPair I;
-    if (lane < count) {
-        i = ilist ? __ldcg(ilist + lane) : lane;
-        if (i < 0 || i >= n_j) {
-            if (warp == 0)
-                atomicOr(err, ERR_INDEX);
-            i = -1;
-        } else {
-            const JMixed rec = load_record(J, i);
-            I = load_ipair(&rec, &rec, eps2, rmin2);
-        }
-    }
-    float hi[7], lo[7];
-#pragma unroll
-    for (int q = 0; q < 7; ++q)
-        hi[q] = lo[q] = 0.f;
-    for (int s0 = tb; s0 < te; s0 += SMALL_STAGE) {
-        const int s1 = min(te, s0 + SMALL_STAGE);
-        const int len = (s1 - s0) * TILE_J;
-        if (s0 > tb)
-            __syncthreads();  // the previous piece is consumed
-        for (int r = (int)threadIdx.x; r < len; r += SMALL_THREADS)
-            js[r] = load_record(J, s0 * TILE_J + r);
-        __syncthreads();
-        if (i < 0)
-            continue;
-        const int jb = s0 * TILE_J;
-        Tile7 t;
-        t.zero();
-        for (int r = 2 * warp; r < len; r += 2 * SMALL_WARPS) {
-            const JMixed A = js[r], B = js[r + 1];
-            JMixed q;
-            q.q[0] = make_float4(A.q[0].x, B.q[0].x, A.q[0].z, B.q[0].z);
-            q.q[1] = make_float4(A.q[1].x, B.q[1].x, jb + r == i ? 0.f : A.q[1].z, jb + r + 1 == i ? 0.f : B.q[1].z);
-            q.q[2] = make_float4(A.q[2].x, B.q[2].x, A.q[2].z, B.q[2].z);
-            q.q[3] = make_float4(A.q[3].x, B.q[3].x, A.q[3].z, B.q[3].z);
-            q.q[4] = make_float4(A.q[4].x, B.q[4].x, A.q[4].z, B.q[4].z);
-            pair<GUARD, MODE_ACC_JERK_POT>(q, I, t);
-        }
-        const float v[7] = {t.ax.x + t.ax.y, t.ay.x + t.ay.y, t.az.x + t.az.y,
-                            __fmaf_rn(-3.f, t.j2x.x, t.j1x.x) + __fmaf_rn(-3.f, t.j2x.y, t.j1x.y),
-                            __fmaf_rn(-3.f, t.j2y.x, t.j1y.x) + __fmaf_rn(-3.f, t.j2y.y, t.j1y.y),
-                            __fmaf_rn(-3.f, t.j2z.x, t.j1z.x) + __fmaf_rn(-3.f, t.j2z.y, t.j1z.y),
-                            t.pt.x + t.pt.y};
-#pragma unroll
-        for (int q = 0; q < 7; ++q)
-            two_sum(hi[q], lo[q], v[q]);
-    }
-    // the warps' sums of each member, added in warp order (the staging space is free now)
-    __syncthreads();
-    float2 *red = reinterpret_cast<float2 *>(js);  // [SMALL_WARPS][7][32]
-#pragma unroll
-    for (int q = 0; q < 7; ++q)
-        red[(warp * 7 + q) * 32 + lane] = make_float2(hi[q], lo[q]);
-    __syncthreads();
-    for (int o = (int)threadIdx.x; o < 7 * count; o += SMALL_THREADS) {
-        const int q = o / count, k = o - q * count;
-        float h = 0.f, l = 0.f;
-#pragma unroll
-        for (int w = 0; w < SMALL_WARPS; ++w) {
-            const float2 v = red[(w * 7 + q) * 32 + k];
-            two_sum(h, l, v.x);
-            l = __fadd_rn(l, v.y);
-        }
-        part[q * SMALL_MAX + k] = make_float2(h, l);
-    }
-    __syncthreads();  // the staging space is free for the caller again
-}
-
-// Member k's seven sums over all G chunks, in one CTA: thread t adds chunks
-// t, t + 256, ... in order (every load first), then the 256 threads' sums
-// meet in a fixed tree (xor shuffles in each warp, the warps in order), all in
-// double-single.  Returns the FP64 sums (before G) in fin[0..6] (shared), valid
-// after the call for every thread.
-__device__ void small_member_sums(const float2 *part, int G, int k, double *fin)
-{
-    constexpr int PER = 2;  // chunks per thread with up to 512 chunks
-    __shared__ float2 wsum[SMALL_WARPS][7];
-    const int t = (int)threadIdx.x, warp = t >> 5, lane = t & 31;
-    float2 v[7][PER];
-#pragma unroll
-    for (int q = 0; q < 7; ++q)
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int c = t + r * SMALL_THREADS;
-            v[q][r] = c < G ? __ldcg(&part[((size_t)c * 7 + q) * SMALL_MAX + k]) : make_float2(0.f, 0.f);
-        }
-    float hi[7], lo[7];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        hi[q] = lo[q] = 0.f;
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            two_sum(hi[q], lo[q], v[q][r].x);
-            lo[q] = __fadd_rn(lo[q], v[q][r].y);
-        }
-    }
-    for (int c = t + PER * SMALL_THREADS; c < G; c += SMALL_THREADS)  // beyond 512 chunks: not in one round
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            const float2 w = __ldcg(&part[((size_t)c * 7 + q) * SMALL_MAX + k]);
-            two_sum(hi[q], lo[q], w.x);
-            lo[q] = __fadd_rn(lo[q], w.y);
-        }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, hi[q], o);
-            const float l2 = __shfl_xor_sync(0xffffffffu, lo[q], o);
-            two_sum(hi[q], lo[q], h2);
-            lo[q] = __fadd_rn(lo[q], l2);
-        }
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 7; ++q)
-            wsum[warp][q] = make_float2(hi[q], lo[q]);
-    __syncthreads();
-    if (t < 7) {
-        float h = 0.f, l = 0.f;
-#pragma unroll
-        for (int w = 0; w < SMALL_WARPS; ++w) {
-            two_sum(h, l, wsum[w][t].x);
-            l = __fadd_rn(l, wsum[w][t].y);
-        }
-        fin[t] = (double)h + (double)l;
-    }
-    __syncthreads();
-}
-
-// Member k's final values (acc, jerk: G sum; pot: -G sum) in i-list row k.
-__device__ __forceinline__ void small_store_member(int k, const double *fin, double G, double *acc, double *jerk,
-                                                   double *pot)
-{
-    const int q = (int)threadIdx.x;
-    if (q < 3) {
-        if (acc)
-            acc[3 * (size_t)k + q] = G * fin[q];
-    } else if (q < 6) {
-        if (jerk)
-            jerk[3 * (size_t)k + (q - 3)] = G * fin[q];
-    } else if (q == 6 && pot) {
-        pot[k] = -G * fin[6];
-    }
-}
-
-// The small-block force in two kernels: every chunk's sums, then one CTA per
-// member adds them up and stores the member's row.
-template <bool GUARD>
-__global__ void __launch_bounds__(SMALL_THREADS, 2) k_force_small(const SmallForceArgs A)
-{
-    __shared__ __align__(16) JMixed js[SMALL_STAGE * TILE_J];
-    const int count = A.n_i_dev ? *A.n_i_dev : A.n_i;
-    if (count <= 0 || count > SMALL_MAX)
-        return;  // uniform: the device-side size of a launch sized for at most SMALL_MAX
-    small_chunk_sums<GUARD>(A.jimg, A.ilist, count, A.n_j, A.tile0, A.ntiles, A.eps2, A.rmin2,
-                            A.scr.part + (size_t)blockIdx.x * 7 * SMALL_MAX, A.err, js);
-}
-
-__global__ void __launch_bounds__(SMALL_THREADS) k_small_final(const SmallForceArgs A)
-{
-    __shared__ double fin[7];
-    const int count = A.n_i_dev ? *A.n_i_dev : A.n_i;
-    const int k = (int)blockIdx.x;
-    if (k >= count)
-        return;  // uniform over the CTA
-    small_member_sums(A.scr.part, A.scr.chunks, k, fin);
-    small_store_member(k, fin, A.G, A.acc, A.jerk, A.pot);
-}
-
-// Grid-wide barrier of a cooperative launch: one arrival per CTA, the last
-// one resets the count and advances the generation; the wait is bounded
-// (WAIT_LIMIT_NS), after which the CTA sets ERR_TIMEOUT and the caller
-// leaves the kernel.
-__device__ bool grid_barrier(unsigned *bar, unsigned *err)
-{
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
-        bool ok = true;
-        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (*gen == g0) {
-                if (global_ns() - t0 > WAIT_LIMIT_NS) {
-                    atomicOr(err, ERR_TIMEOUT);
-                    ok = false;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
-
-// Block steps of small blocks (see loop_internal.cuh).  Entered after the
-// step kernels selected a block; leaves when the selected block has more than
-// SMALL_MAX members (the graph's force switch then takes it) or none.
-template <bool GUARD>
-__global__ void __launch_bounds__(SMALL_THREADS, 2) k_small_steps(const SmallStepArgs P)
-{
-    __shared__ __align__(16) JMixed js[SMALL_STAGE * TILE_J];
-    __shared__ double fin[7];
-    const StepArgs &A = P.st;
-    RunState *R = A.run;
-    for (;;) {
-        const int count = __ldcg(A.count_out);
-        if (count <= 0 || count > SMALL_MAX)
-            return;  // uniform: read after the barrier that followed its publication
-        const long long s = __ldcg(&R->steps);
-        const double tb = __ldcg(&R->t_last);
-        const int par = (int)(s & 1);
-        // the block's forces
-        small_chunk_sums<GUARD>(A.jm, A.ilist, count, A.n, P.tile0, P.ntiles, P.eps2, P.rmin2,
-                                P.scr.part + (size_t)blockIdx.x * 7 * SMALL_MAX, A.err, js);
-        // end times of the particles outside the block; fresh words for the next selection
-        int c0, c1;
-        chunk_of(A.n, c0, c1);
-        unsigned long long mn = ~0ull;
-        for (int i = c0 + (int)threadIdx.x; i < c1; i += SMALL_THREADS) {
-            const double end = __ldcg(A.bt + i) + __ldcg(A.bdt + i);
-            if (end != tb)
-                mn = min(mn, time_key(end));
-        }
-        mn = cta_min_u64(mn);
-        if (threadIdx.x == 0) {
-            atomicMin(&R->minw[par], mn);
-            if (blockIdx.x == 0) {
-                R->minw[par ^ 1] = ~0ull;
-                R->list_done = 0ull;
-            }
-        }
-        if (!grid_barrier(P.bar, A.err))
-            return;
-        // member k in CTA k: its sums over every chunk, its row, its corrector and new end time
-        const int k = (int)blockIdx.x;
-        if (k < count) {
-            small_member_sums(P.scr.part, (int)gridDim.x, k, fin);
-            // the step kernels only read the force rows; here they are written first (the context's buffers)
-            small_store_member(k, fin, P.G, const_cast<double *>(A.acc), const_cast<double *>(A.jerk), nullptr);
-            __syncthreads();  // the stored row is read back by the corrector
-            if (threadIdx.x == 0) {
-                const double end = correct_at((size_t)__ldcg(A.ilist + k), k, tb, A.eta, A.dt_min, A.dt_max, 1, A.xp,
-                                              A.vp, A.acc, A.jerk, A.bx, A.bv, A.ba, A.bj, A.bt, A.bdt);
-                atomicMin(&R->minw[par], time_key(end));
-            }
-        }
-        if (!grid_barrier(P.bar, A.err))
-            return;
-        select_body(A);
-        if (!grid_barrier(P.bar, A.err))
-            return;
     }
 }
 
@@ -1208,47 +888,6 @@ __global__ void k_sum_parts(int n_parts, long long n_i, const double *__restrict
     } else if (pot) {
         pot[k - 6 * n_i] = s;
     }
-}
-
-cudaError_t launch_force_small(const SmallForceArgs &a, bool guard, cudaStream_t st)
-{
-    if (a.scr.chunks < 1 || (!a.n_i_dev && (a.n_i < 0 || a.n_i > SMALL_MAX)))
-        return cudaErrorInvalidValue;
-    if (!a.n_i_dev && a.n_i == 0)
-        return cudaSuccess;
-    if (guard)
-        k_force_small<true><<<a.scr.chunks, SMALL_THREADS, 0, st>>>(a);
-    else
-        k_force_small<false><<<a.scr.chunks, SMALL_THREADS, 0, st>>>(a);
-    k_small_final<<<a.n_i_dev ? SMALL_MAX : a.n_i, SMALL_THREADS, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-int small_steps_ctas_per_sm(bool guard)
-{
-    int n = 0;
-    if (guard)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_small_steps<true>, SMALL_THREADS, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_small_steps<false>, SMALL_THREADS, 0);
-    return n;
-}
-
-cudaError_t launch_small_steps(const SmallStepArgs &a, bool guard, int ctas, cudaStream_t st)
-{
-    if (ctas != a.scr.chunks)
-        return cudaErrorInvalidValue;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)ctas);
-    cfg.blockDim = dim3(SMALL_THREADS);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return guard ? cudaLaunchKernelEx(&cfg, k_small_steps<true>, a) : cudaLaunchKernelEx(&cfg, k_small_steps<false>, a);
 }
 
 cudaError_t launch_sum_parts(int n_parts, int64_t n_i, const double *parts, double *acc, double *jerk,

@@ -302,6 +302,120 @@ __global__ void __launch_bounds__(FORCE_THREADS, KIRIN_MIX_MINB) k_force_mixed(c
     }
 }
 
+// Tiny blocks (n_i <= TINY_MAX): CTA (x, y) stages the j range x of the
+// padded image (at most TINY_JCHUNK records) in shared memory, and its warp
+// w takes i-particle k = 8 y + w, lane l the records l, l + 32 of each 64 in
+// the two float2 lanes of the pair body (the i duplicated in both; the self
+// pair gets zero mass).  Lane sums meet across the warp in double-single;
+// lanes 0..6 convert one output each to FP64 and write the CTA's partial
+// (n_split = gridDim.x), which the split reduction sums.
+constexpr int TINY_THREADS = 256;
+constexpr int TINY_WARPS = TINY_THREADS / 32;
+
+template <bool GUARD, bool DEVN>
+__global__ void __launch_bounds__(TINY_THREADS) k_force_tiny(const ForceArgs A)
+{
+    __shared__ __align__(16) JMixed js[TINY_JCHUNK];
+    const int n_i = DEVN ? *A.n_i_dev : A.n_i;
+    if ((int)blockIdx.y * TINY_WARPS >= n_i)
+        return;  // no i-particle for this CTA (uniform)
+    const JMixed *__restrict__ J = static_cast<const JMixed *>(A.jimg);
+    const int n_pad = A.ntiles * TILE_J;  // the records summed: [jb, jb + n_pad) of the padded image
+    const int jb = A.tile0 * TILE_J;
+    const int chunk = (n_pad + (int)gridDim.x - 1) / (int)gridDim.x;
+    if (chunk > TINY_JCHUNK) {  // the host sizes the grid so that this cannot happen
+        if (threadIdx.x == 0)
+            atomicOr(A.err, ERR_INDEX);
+        return;
+    }
+    const int j0 = jb + min(n_pad, (int)blockIdx.x * chunk);
+    const int len = min(jb + n_pad, j0 + chunk) - j0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = (int)blockIdx.y * TINY_WARPS + warp;
+    int i = -1;
+    JMixed rec;
+    if (k < n_i) {
+        i = A.ilist ? A.ilist[k] : k;
+        if (i < 0 || i >= A.n_j) {
+            if (lane == 0)
+                atomicOr(A.err, ERR_INDEX);
+            i = -1;
+        } else {
+            rec = J[i];
+        }
+    }
+    for (int r = threadIdx.x; r < len; r += TINY_THREADS)
+        js[r] = J[j0 + r];
+    __syncthreads();
+    if (k >= n_i)
+        return;
+    Tile7 t;
+    t.zero();
+    if (i >= 0) {
+        const IPair I = load_ipair(&rec, &rec, (float)A.eps2, (float)A.rmin2);
+        for (int b0 = 0; b0 < len; b0 += 64) {
+            const int ra = b0 + lane, rb = ra + 32;
+            float4 a[5], b[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                a[c] = ra < len ? js[ra].q[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                b[c] = rb < len ? js[rb].q[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            JMixed r;
+            r.q[0] = make_float4(a[0].x, b[0].x, a[0].z, b[0].z);
+            r.q[1] = make_float4(a[1].x, b[1].x, j0 + ra == i ? 0.f : a[1].z, j0 + rb == i ? 0.f : b[1].z);
+            r.q[2] = make_float4(a[2].x, b[2].x, a[2].z, b[2].z);
+            r.q[3] = make_float4(a[3].x, b[3].x, a[3].z, b[3].z);
+            r.q[4] = make_float4(a[4].x, b[4].x, a[4].z, b[4].z);
+            pair<GUARD, MODE_ACC_JERK_POT>(r, I, t);
+        }
+    }
+    float hi[7], lo[7];
+    hi[0] = t.ax.x + t.ax.y;
+    hi[1] = t.ay.x + t.ay.y;
+    hi[2] = t.az.x + t.az.y;
+    hi[3] = __fmaf_rn(-3.f, t.j2x.x, t.j1x.x) + __fmaf_rn(-3.f, t.j2x.y, t.j1x.y);
+    hi[4] = __fmaf_rn(-3.f, t.j2y.x, t.j1y.x) + __fmaf_rn(-3.f, t.j2y.y, t.j1y.y);
+    hi[5] = __fmaf_rn(-3.f, t.j2z.x, t.j1z.x) + __fmaf_rn(-3.f, t.j2z.y, t.j1z.y);
+    hi[6] = t.pt.x + t.pt.y;
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+        lo[q] = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi[q], o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo[q], o);
+            two_sum(hi[q], lo[q], h2);
+            lo[q] = __fadd_rn(lo[q], l2);
+        }
+    }
+    float h = hi[0], l = lo[0];
+#pragma unroll
+    for (int q = 1; q < 7; ++q)
+        if (lane == q) {
+            h = hi[q];
+            l = lo[q];
+        }
+    if (lane < 7)
+        A.partial[((size_t)blockIdx.x * A.nq + lane) * A.n_i_pad + k] = (double)h + (double)l;
+}
+
+template <bool GUARD>
+cudaError_t launch_tiny(const ForceArgs &a, int ctas, cudaStream_t st)
+{
+    if (a.n_i > TINY_MAX || a.n_split != ctas || a.nq != 7 || !a.partial || a.n_i_pad < TINY_MAX || ctas < 1 ||
+        (a.ntiles * TILE_J + ctas - 1) / ctas > TINY_JCHUNK)
+        return cudaErrorInvalidValue;
+    const dim3 grid(ctas, (a.n_i + TINY_WARPS - 1) / TINY_WARPS);
+    if (a.n_i_dev)
+        k_force_tiny<GUARD, true><<<grid, TINY_THREADS, 0, st>>>(a);
+    else
+        k_force_tiny<GUARD, false><<<grid, TINY_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int GROUPS, bool GUARD, int MODE, bool DEVN>
 cudaError_t launch_v(const ForceArgs &a, int iblocks, int n_split, cudaStream_t st)
 {
@@ -382,6 +496,13 @@ cudaError_t launch_m(const ForceArgs &a, Shape s, bool guard, cudaStream_t st)
 
 cudaError_t launch_force_mixed(const ForceArgs &a, Shape s, bool guard, int mode, cudaStream_t st)
 {
+    if (s.groups == 0) {  // tiny-block kernel
+        if (mode != MODE_ACC_JERK_POT)
+            return cudaErrorInvalidValue;
+        if (a.n_i == 0)
+            return cudaSuccess;
+        return guard ? launch_tiny<true>(a, s.n_split, st) : launch_tiny<false>(a, s.n_split, st);
+    }
     switch (mode) {
     case MODE_ACC_JERK_POT: return launch_m<MODE_ACC_JERK_POT>(a, s, guard, st);
     case MODE_ACC_POT: return launch_m<MODE_ACC_POT>(a, s, guard, st);

@@ -61,15 +61,24 @@ constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 // Launch shape of one force evaluation.
 struct Shape {
     int groups;   // j-groups per CTA (1, 2, 4, 8); i per CTA = 2*256/groups (mixed) or 256/groups (fp64);
-                  // 0: the small-block kernel (mixed, acc+jerk+pot, at most 32 i; loop_internal.cuh)
-    int n_split;  // CTAs splitting the j range (grid.y; the grid of the small-block kernel)
+                  // 0: the tiny-block kernel (mixed, acc+jerk+pot, n_i <= TINY_MAX)
+    int n_split;  // CTAs splitting the j range (grid.y; the grid of the tiny-block kernel)
 };
+
+// Blocks of at most this many i-particles go to the tiny-block kernel: each
+// CTA stages a range of at most TINY_JCHUNK j in shared memory, each warp
+// takes one i-particle and its lanes the j.  (At N = 65536 on GB300 it takes
+// 7.2 us for one i and 8.5 us for four, against 11.4 us for the best regular
+// shape, but loses beyond about 12 i: every further group of 8 i re-stages the
+// j range.)
+constexpr int TINY_MAX = 8;
+constexpr int TINY_JCHUNK = 256;
 
 // i-slots per CTA of a launch shape (the padding unit of the split partials).
 inline int shape_i_cta(Shape s, bool mixed)
 {
     if (s.groups == 0)
-        return 1;  // the small-block kernel keeps no split partials
+        return TINY_MAX;
     return (mixed ? MIX_I_PER_THREAD : 1) * FORCE_THREADS / s.groups;
 }
 

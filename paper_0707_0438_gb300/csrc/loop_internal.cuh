@@ -63,54 +63,4 @@ struct StepArgs {
 cudaError_t launch_block_step(const StepArgs &a, int ctas, cudaStream_t st);
 constexpr int STEP_CTAS_PER_SM = 2;
 
-// ---- small active blocks ----------------------------------------------------
-//
-// A block of at most SMALL_MAX i-particles against N j is a few hundred
-// thousand pair interactions: launch and latency, not arithmetic, set its
-// time.  The small-block force spreads the j tiles over G CTAs (one chunk
-// each; a lane per member, the warps over the chunk's j) and leaves each
-// chunk's double-single sums in a scratch; then one CTA per member adds its
-// sums over the chunks in one round of loads and a fixed tree.  The
-// small-step kernel runs whole block steps of small blocks in one cooperative
-// launch: chunk sums, a grid barrier, the member CTAs' sums and correctors, a
-// barrier, the selection and prediction of the next block, a barrier, until a
-// larger block or the end of the run comes up.
-constexpr int SMALL_MAX = 32;
-
-// Scratch of the small-block force for a grid of `chunks` CTAs.
-struct SmallScratch {
-    float2 *part;  // [chunks][7][SMALL_MAX] (hi, lo) sums of each chunk
-    int chunks;
-};
-
-struct SmallForceArgs {
-    const JMixed *jimg;
-    const int32_t *ilist;    // n_i entries (device); nullptr = identity
-    int n_i;
-    const int32_t *n_i_dev;  // if set, the block size is read here at launch
-    int n_j;
-    int tile0, ntiles;       // j tiles summed: [tile0, tile0 + ntiles)
-    float eps2, rmin2;
-    double G;
-    double *acc, *jerk, *pot;  // outputs in i-list order; any may be null
-    unsigned *err;
-    SmallScratch scr;
-};
-// One small-block force (n_i <= SMALL_MAX): the chunk kernel over scr.chunks CTAs, then the member kernel.
-cudaError_t launch_force_small(const SmallForceArgs &a, bool guard, cudaStream_t st);
-
-// The small-step kernel: as long as the selected block has at most SMALL_MAX
-// members, force, correct and select in one cooperative launch over `ctas`
-// CTAs (the step kernels' grid, so the list layout is theirs).
-struct SmallStepArgs {
-    StepArgs st;
-    SmallScratch scr;
-    unsigned *bar;  // grid barrier: [0] arrivals, [1] generation
-    int tile0, ntiles;
-    float eps2, rmin2;
-    double G;
-};
-cudaError_t launch_small_steps(const SmallStepArgs &a, bool guard, int ctas, cudaStream_t st);
-int small_steps_ctas_per_sm(bool guard);
-
 }  // namespace kirin

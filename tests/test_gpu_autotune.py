@@ -18,7 +18,7 @@ def test_autotuned_table_is_used_and_correct(kirin_lib, tmp_path):
         assert entries and entries[-1][0] == p.n
         assert all(a[0] < b[0] for a, b in zip(entries, entries[1:]))
         for n_i_max, g, s, _ in entries:
-            if n_i_max <= 32:  # blocks this small go to the small-block kernel whatever the table says
+            if n_i_max <= 8:  # blocks this small go to the tiny-block kernel whatever the table says
                 assert k.get_launch(n_i_max)[0] == 0
             else:
                 assert k.get_launch(n_i_max) == (g, min(s, (p.n + 127) // 128))

@@ -254,53 +254,3 @@ def test_host_and_device_steps_interleave(kirin_lib):
     assert done == total and steps == 50
     for key in STATE_KEYS:
         assert np.array_equal(st[key], ref[key]), key
-
-
-@pytest.mark.parametrize("eps,r_min", [(1e-3, 0.0), (0.0, 1e-6)])
-def test_small_step_kernel_is_bitwise_the_host_loop(kirin_lib, eps, r_min):
-    """Blocks of at most 32 members run inside the cooperative small-step kernel (force, corrector and
-    the next selection, two grid barriers per step); the host-driven loop forces them with the same
-    small-block kernel and corrects them with the corrector kernel.  With one launch table entry for
-    the larger blocks (so both loops give them the same shape) the two loops, and the device loop with
-    the small-step kernel switched off, end in the same bits, step for step (Sect. 3.1 block steps)."""
-    p = workloads.plummer(4096, 1009, eps=eps)
-
-    def run(device_loop, small_steps):
-        with abi.Kirin(p.n, eps, r_min=r_min, precision="mixed") as k:
-            k.set_launch_table([(p.n, 4, 8)])
-            k.set_j_particles(p.m, p.x, p.v)
-            k.hermite_init(0.0)
-            k.set_device_loop(device_loop)
-            k.set_small_steps(small_steps)
-            counts = k.hermite_run(1.0 / 32)
-            return counts, k.get_state()
-
-    host = run(False, True)
-    small = run(True, True)
-    switch = run(True, False)
-    assert host[0][0] > 100
-    for dev in (small, switch):
-        assert dev[0] == host[0]
-        for key in STATE_KEYS:
-            assert np.array_equal(dev[1][key], host[1][key]), key
-
-
-def test_small_step_kernel_block_sizes_and_energy(kirin_lib):
-    """A run whose blocks are almost all small: the small-step kernel takes them, the schedule and the
-    energy are those of the host loop, and runs continue across calls."""
-    p = workloads.plummer(2048, 1010, eps=1e-3)
-    out = {}
-    for device_loop in (True, False):
-        with abi.Kirin(p.n, p.eps, precision="mixed") as k:
-            k.set_j_particles(p.m, p.x, p.v)
-            e0 = sum(k.energy())
-            k.hermite_init(0.0)
-            k.set_device_loop(device_loop)
-            s1, _ = k.hermite_run(1.0 / 16)
-            s2, _ = k.hermite_run(1.0 / 8)
-            out[device_loop] = (s1, s2, k.get_state(), e0, sum(k.energy()))
-    d, h = out[True], out[False]
-    assert d[0] == h[0] and d[1] == h[1] and d[0] > 100
-    assert np.array_equal(d[2]["t"], h[2]["t"]) and np.array_equal(d[2]["dt"], h[2]["dt"])
-    assert np.abs(d[2]["x"] - h[2]["x"]).max() <= 1e-9 * np.abs(p.x).max()
-    assert abs(metrics.energy_error(d[3], d[4])) < 1e-5

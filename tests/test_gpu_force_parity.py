@@ -129,28 +129,28 @@ def test_maximum_size_sampled_parity(kirin_lib):
     assert_parity(got, ref, "mixed", "N=2^25")
 
 
-@pytest.mark.parametrize("n_i", [1, 2, 5, 8, 9, 17, 32])
-def test_small_block_kernel(kirin_lib, n_i):
-    """Blocks of at most 32 i go to the small-block kernel (j chunks per CTA, lanes over j, a warp per i:
-    Sect. 3.2's j-split taken to the limit, its sums added in two levels inside the kernel); ragged j
-    count, the self pair inside the list, and agreement with the regular kernel under a fixed shape."""
+@pytest.mark.parametrize("n_i", [1, 2, 5, 8])
+def test_tiny_block_kernel(kirin_lib, n_i):
+    """Blocks of at most 8 i go to the tiny-block kernel (j ranges per CTA, lanes over j, Sect. 3.2's
+    j-split taken to the limit); ragged j count, the self pair inside the list, and agreement with the
+    regular kernel under a fixed launch shape."""
     p = workloads.plummer(40000, 93, masses="lognormal", eps=1e-3)  # 313 tiles, the last one ragged
     il = workloads.i_subset(p.n, n_i, seed=n_i)
     il[0] = p.n - 1  # the last particle, in the ragged tile
     ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps, i_idx=il)
     with _ctx(p, "mixed") as k:
-        assert k.get_launch(n_i)[0] == 0 and k.get_launch(33)[0] != 0
-        small = k.forces(il)
+        assert k.get_launch(n_i)[0] == 0 and k.get_launch(9)[0] != 0
+        tiny = k.forces(il)
         k.set_launch(8, 64)
         regular = k.forces(il)
         k.set_launch(0, 0)
-    assert_parity(small, ref, "mixed", f"small n_i={n_i}")
-    for a, b in zip(small, regular):
+    assert_parity(tiny, ref, "mixed", f"tiny n_i={n_i}")
+    for a, b in zip(tiny, regular):
         assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
 
 
-def test_small_block_kernel_guard_and_duplicates(kirin_lib):
-    """eps = 0 with r_min through the small-block kernel: a coincident distinct pair contributes
+def test_tiny_block_kernel_guard_and_duplicates(kirin_lib):
+    """eps = 0 with r_min through the tiny-block kernel: a coincident distinct pair contributes
     nothing, repeated and unordered i are each evaluated."""
     p = workloads.plummer(3001, 94, eps=0.0)
     x = p.x.copy()
@@ -162,7 +162,7 @@ def test_small_block_kernel_guard_and_duplicates(kirin_lib):
         assert k.get_launch(len(il))[0] == 0
         got = k.forces(il)
     ref = oracle.acc_jerk_pot(p.m, x, p.v, 0.0, r_min=r_min, i_idx=il)
-    assert_parity(got, ref, "mixed", "small eps=0")
+    assert_parity(got, ref, "mixed", "tiny eps=0")
     assert np.array_equal(got[0][0], got[0][3])
 
 
