@@ -122,3 +122,76 @@ def test_exchange_failures_are_reported(kirin_lib):
         k.set_j_partition(0, 1)
         got = k.forces()
     assert_parity(got, oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps), "mixed")
+
+
+def test_torch_allgather_on_device_buffers_over_nccl(kirin_lib):
+    """jsplit.TorchAllGather on CUDA device pointers, as kirin_set_j_partition calls it, over an NCCL
+    group of one rank (this runs on one GPU): the device views, the stream ordering against the
+    context's stream and the gathered layout."""
+    import os
+    import socket
+
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda:0")
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("nccl", rank=0, world_size=1, device_id=dev)
+    try:
+        side = torch.cuda.Stream(device=dev)
+        send = torch.empty(7 * 37, dtype=torch.float64, device=dev)
+        recv = torch.full((7 * 37,), float("nan"), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(side):
+            send.copy_(torch.arange(7 * 37, dtype=torch.float64, device=dev))  # enqueued before the call
+        rc = jsplit.TorchAllGather(device=dev)(send.data_ptr(), recv.data_ptr(), send.numel(), side.cuda_stream)
+        side.synchronize()
+        assert rc == 0 and torch.equal(recv, send)
+        # and through a context: with one part the callback is never needed, the sums are whole
+        p = workloads.plummer(700, 41, eps=0.01)
+        with abi.Kirin(p.n, p.eps, precision="fp64") as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            k.set_j_partition(0, 1, jsplit.TorchAllGather(device=dev))
+            got = k.forces()
+        assert_parity(got, oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps), "fp64")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_threaded_parts_leapfrog_in_lockstep(kirin_lib):
+    """The force-only calls of the leapfrog (Sect. 4.3 client) through the exchange: two threaded parts
+    give the same bits, and the unpartitioned context's trajectory to rounding (FP64)."""
+    import torch
+    dev = torch.device("cuda:0")
+    p = workloads.plummer(3000, 4444, eps=0.02)
+    ex = jsplit.LocalAllGather([0, 0])
+    out, errs = [None, None], []
+
+    def drive(r):
+        try:
+            with abi.Kirin(p.n, p.eps, precision="fp64") as k:
+                k.set_j_partition(r, 2, ex.for_part(r))
+                m, x, v = (torch.tensor(a, device=dev) for a in (p.m, p.x, p.v))
+                acc = torch.empty_like(x)
+                k.leapfrog_dev(m, x, v, acc, 1.0 / 128, 8)
+                k.sync()
+                out[r] = (x.cpu().numpy(), v.cpu().numpy())
+        except BaseException as exc:
+            errs.append(exc)
+            ex.barrier.abort()
+
+    th = [threading.Thread(target=drive, args=(r,)) for r in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert not errs, errs
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    with abi.Kirin(p.n, p.eps, precision="fp64") as k:
+        m, x, v = (torch.tensor(a, device=dev) for a in (p.m, p.x, p.v))
+        acc = torch.empty_like(x)
+        k.leapfrog_dev(m, x, v, acc, 1.0 / 128, 8)
+        k.sync()
+        ref = x.cpu().numpy()
+    assert np.abs(out[0][0] - ref).max() <= 1e-12 * np.abs(p.x).max()
