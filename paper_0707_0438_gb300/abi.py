@@ -218,9 +218,9 @@ class Kirin:
             detail = ""
             if ctx and getattr(self, "ctx", None):
                 detail = self.lib.kirin_last_error(self.ctx).decode()
-            exc = getattr(self, "_exchange_error", None)
-            if rc == KIRIN_EEXCHANGE and exc is not None:
-                self._exchange_error = None
+            box = getattr(self, "_exchange_box", None)
+            if rc == KIRIN_EEXCHANGE and box and box[0] is not None:
+                exc, box[0] = box[0], None
                 raise KirinError(rc, what, detail) from exc
             raise KirinError(rc, what, detail)
 
@@ -341,15 +341,15 @@ class Kirin:
         are this part's partial sums) or a callable (send, recv, count, stream) -> int over device pointers
         (ints), e.g. a jsplit.TorchAllGather; the context keeps it alive."""
         cb = None
+        box = self._exchange_box = [None]  # the callback's failure, without a reference back to self
         if allgather is not None:
-            def trampoline(user, send, recv, count, stream, _f=allgather):
+            def trampoline(user, send, recv, count, stream, _f=allgather, _box=box):
                 try:
                     return int(_f(send, recv, count, stream))
                 except BaseException as exc:  # never let ctypes swallow a failed exchange
-                    self._exchange_error = exc
+                    _box[0] = exc
                     return 1
             cb = ALLGATHER_FN(trampoline)
-        self._exchange_error = None
         rc = self.lib.kirin_set_j_partition(self.ctx, int(part), int(n_parts),
                                             ctypes.cast(cb, ctypes.c_void_p) if cb is not None else None, None)
         self._check(rc, "kirin_set_j_partition")
