@@ -254,11 +254,29 @@ int kirin_set_device_loop(kirin_ctx *ctx, int32_t enable);
 /* One shared step of size dt for all particles (no step-size update). */
 int kirin_hermite_shared_step(kirin_ctx *ctx, double dt);
 
-/* n_steps shared steps of size dt, enqueued back to back with a single
- * synchronisation (and error check) at the end; the same kernels and
- * results as n_steps calls of kirin_hermite_shared_step.  Errors: EINVAL
- * (dt <= 0, n_steps < 0), ESTATE before kirin_hermite_init. */
+/* n_steps shared steps of size dt, with a single synchronisation (and error
+ * check) at the end.  A mixed-precision system of at most 2048 particles
+ * (no fixed launch shape, no j partition) runs the whole call in one
+ * cooperative launch, one CTA per SM: each CTA owns a slice of the particles,
+ * corrects it with the step kernels' corrector and predicts it with their
+ * FP64 predictor into a global j image (two images, for even and odd steps);
+ * after one bounded grid barrier per step every CTA copies the image into its
+ * shared memory and sums its slice's acc, jerk and pot against all j with the
+ * force kernels' pair arithmetic.  Otherwise the steps are the predictor,
+ * force and corrector kernels enqueued back to back, the same kernels and
+ * results as n_steps calls of kirin_hermite_shared_step.  The two paths sum
+ * the j in different orders, so they agree to rounding; each gives the same
+ * bits on every call.  kirin_hermite_shared_step is this call with one step.
+ * Errors: EINVAL (dt <= 0, n_steps < 0), ESTATE before kirin_hermite_init,
+ * ENOMEM (the two images), ETIMEOUT (a grid barrier or copy wait gave up). */
 int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps);
+
+/* kirin_set_shared_persistent: enable != 0 (default) lets
+ * kirin_hermite_shared_run use the single-launch kernel where it can; 0 keeps
+ * the per-kernel steps.  kirin_get_shared_persistent: *active = 1 if the next
+ * shared run would use it.  Errors: EINVAL (NULL). */
+int kirin_set_shared_persistent(kirin_ctx *ctx, int32_t enable);
+int kirin_get_shared_persistent(kirin_ctx *ctx, int32_t *active);
 
 /* Copy the integrator state (host arrays, each may be NULL): x, v, a, jerk
  * (n_j x 3), t and dt (n_j). */

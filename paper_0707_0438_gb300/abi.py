@@ -83,6 +83,8 @@ _SIGS = {
     "kirin_hermite_block_step": (ctypes.c_int, [_P, _D, _PD, _PI64]),
     "kirin_hermite_run": (ctypes.c_int, [_P, _D, _I64, _PI64, _PD]),
     "kirin_set_device_loop": (ctypes.c_int, [_P, _I32]),
+    "kirin_set_shared_persistent": (ctypes.c_int, [_P, _I32]),
+    "kirin_get_shared_persistent": (ctypes.c_int, [_P, _PI32]),
     "kirin_hermite_shared_run": (ctypes.c_int, [_P, _D, _I64]),
     "kirin_hermite_shared_step": (ctypes.c_int, [_P, _D]),
     "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
@@ -395,6 +397,17 @@ class Kirin:
 
     def set_device_loop(self, enable=True):
         self._check(self.lib.kirin_set_device_loop(self.ctx, 1 if enable else 0), "kirin_set_device_loop")
+
+    def set_shared_persistent(self, enable=True):
+        """Let shared-step runs of small mixed-precision systems take the single-launch kernel."""
+        self._check(self.lib.kirin_set_shared_persistent(self.ctx, 1 if enable else 0),
+                    "kirin_set_shared_persistent")
+
+    def shared_persistent_active(self):
+        """Whether the next kirin_hermite_shared_run takes the single-launch kernel."""
+        a = ctypes.c_int32()
+        self._check(self.lib.kirin_get_shared_persistent(self.ctx, ctypes.byref(a)), "kirin_get_shared_persistent")
+        return bool(a.value)
 
     def hermite_shared_step(self, dt):
         self._check(self.lib.kirin_hermite_shared_step(self.ctx, float(dt)), "kirin_hermite_shared_step")

@@ -110,6 +110,15 @@ struct kirin_ctx {
     double *d_send = nullptr, *d_recv = nullptr;
     size_t send_cap = 0, recv_cap = 0;  // doubles
 
+    // shared-step runs of small systems in one cooperative launch (shared_steps.cu)
+    bool shared_persistent = true;
+    int sh_grid = 0;  // CTAs of that launch for sh_fit_n particles; 0: it does not fit
+    int64_t sh_fit_n = -1;
+    int sh_fit_guard = -1;
+    JMixed *sh_img = nullptr;  // [2][sh_img_pad]: the even and odd steps' j images
+    int64_t sh_img_pad = 0;
+    unsigned *sh_bar = nullptr;  // grid barrier words (zero between launches)
+
     // nearest-neighbour search of the host-pointer path (GRAPE's neighbour list)
     bool want_nn = false;
     bool nn_valid = false;
@@ -403,7 +412,8 @@ void free_all(kirin_ctx *c)
 {
     void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
                     c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
-                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts, c->d_send, c->d_recv};
+                    c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts, c->d_send, c->d_recv,
+                    c->sh_img, c->sh_bar};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -480,6 +490,24 @@ RunPlan plan_run(kirin_ctx *c)
         p.shape[q] = choose_shape(c, rep, ntiles, c->prec, MODE_ACC_JERK_POT, guard_on(c));
     }
     return p;
+}
+
+// Whether shared-step runs take the single-launch kernel: mixed precision, at most SH_MAX_N
+// particles, no fixed launch shape (which names the per-kernel path) and no j partition, enabled, and
+// its cooperative launch fitting on this GPU.
+bool shared_steps_on(kirin_ctx *c)
+{
+    if (!c->shared_persistent || c->prec != KIRIN_MIXED || c->n_j < 1 || c->n_j > SH_MAX_N || c->n_parts > 1 ||
+        (c->fix_groups > 0 && c->fix_split > 0))
+        return false;
+    const bool guard = guard_on(c);
+    if (c->sh_fit_n != c->n_j || c->sh_fit_guard != (int)guard) {
+        c->sh_grid = shared_steps_grid((int)c->n_j, guard);
+        cudaGetLastError();
+        c->sh_fit_n = c->n_j;
+        c->sh_fit_guard = (int)guard;
+    }
+    return c->sh_grid > 0;
 }
 
 RunKey run_key(const kirin_ctx *c, const RunPlan &p)
@@ -1290,6 +1318,23 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
     return read_device_errors(ctx);
 }
 
+int kirin_set_shared_persistent(kirin_ctx *ctx, int32_t enable)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    ctx->shared_persistent = enable != 0;
+    return KIRIN_OK;
+}
+
+int kirin_get_shared_persistent(kirin_ctx *ctx, int32_t *active)
+{
+    if (!ctx || !active)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    *active = shared_steps_on(ctx) ? 1 : 0;
+    return KIRIN_OK;
+}
+
 int kirin_set_device_loop(kirin_ctx *ctx, int32_t enable)
 {
     if (!ctx)
@@ -1308,6 +1353,71 @@ int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps)
         return set_msg(ctx, KIRIN_ESTATE, "hermite_shared_run: call kirin_hermite_init first");
     DeviceGuard dg(ctx->device);
     const int n = (int)ctx->n_j;
+    if (shared_steps_on(ctx) && n_steps > 0 && n_steps <= INT32_MAX) {
+        // the whole run in one cooperative launch (small systems, mixed precision)
+        const int64_t n_pad = round_up(n, TILE_J);
+        if (ctx->sh_img_pad < n_pad) {
+            if (ctx->sh_img)
+                cudaFree(ctx->sh_img);
+            ctx->sh_img = nullptr;
+            ctx->sh_img_pad = 0;
+            if (cudaMalloc(&ctx->sh_img, 2 * (size_t)n_pad * sizeof(JMixed)) != cudaSuccess) {
+                ctx->sh_img = nullptr;
+                cudaGetLastError();
+                return set_msg(ctx, KIRIN_ENOMEM, "hermite_shared_run: no room for the two j images");
+            }
+            ctx->sh_img_pad = n_pad;
+        }
+        if (!ctx->sh_bar) {
+            if (cudaMalloc(&ctx->sh_bar, 2 * sizeof(unsigned)) != cudaSuccess) {
+                ctx->sh_bar = nullptr;
+                cudaGetLastError();
+                return set_msg(ctx, KIRIN_ENOMEM, "hermite_shared_run: no room for the barrier words");
+            }
+            CK(ctx, cudaMemsetAsync(ctx->sh_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+        }
+        SharedStepArgs a{};
+        a.n = n;
+        a.n_pad = (int)n_pad;
+        a.img = ctx->sh_img;
+        a.bar = ctx->sh_bar;
+        a.ctas = ctx->sh_grid;
+        a.m = ctx->bm;
+        a.x = ctx->bx;
+        a.v = ctx->bv;
+        a.a = ctx->ba;
+        a.jerk_b = ctx->bj;
+        a.t_b = ctx->bt;
+        a.dt_b = ctx->bdt;
+        a.xp = ctx->xp;
+        a.vp = ctx->vp;
+        a.f_acc = ctx->d_acc;
+        a.f_jerk = ctx->d_jerk;
+        a.f_pot = ctx->d_pot;
+        a.eps2 = ctx->eps * ctx->eps;
+        a.rmin2 = ctx->r_min * ctx->r_min;
+        a.G = ctx->G;
+        a.eta = ctx->eta;
+        a.dt_min = ctx->dt_min;
+        a.dt_max = ctx->dt_max;
+        a.t0 = ctx->t_shared;
+        a.dt = dt;
+        a.n_steps = (int)n_steps;
+        a.err = ctx->d_err;
+        CK(ctx, launch_shared_steps(a, guard_on(ctx), ctx->stream));
+        double t = ctx->t_shared;
+        for (int64_t s = 0; s < n_steps; ++s)  // the kernel's time arithmetic, step by step
+            t = t + dt;
+        ctx->t_shared = t;
+        ctx->pred_mode = 1;
+        ctx->pred_t = t;
+        ctx->images_dirty = true;
+        ctx->pending = false;
+        const int rc = read_device_errors(ctx);
+        if (rc == KIRIN_ETIMEOUT)  // CTAs left mid-barrier: the words start from zero again
+            CK(ctx, cudaMemsetAsync(ctx->sh_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+        return rc;
+    }
     for (int64_t s = 0; s < n_steps; ++s) {  // enqueued back to back; one synchronisation at the end
         const double t_next = ctx->t_shared + dt;
         ctx->pred_mode = 1;

@@ -8,6 +8,7 @@
 
 #include "kirin_internal.cuh"
 #include "loop_internal.cuh"
+#include "step_math.cuh"
 #include "tma.cuh"
 
 namespace kirin {
@@ -64,84 +65,6 @@ __global__ void k_reduce_splits(const ForceArgs Ain)
         if (lane == 0)
             store_nn(A, k, r2, j);
     }
-}
-
-__device__ __forceinline__ void split_ds(double v, float &hi, float &lo)
-{
-    hi = __double2float_rn(v);
-    lo = __double2float_rn(v - (double)hi);
-}
-
-__device__ __forceinline__ void write_images(int k, double X, double Y, double Z, double M, double VX,
-                                             double VY, double VZ, JMixed *jm, JF64 *jd)
-{
-    if (jm) {
-        float xh, xl, yh, yl, zh, zl;
-        split_ds(X, xh, xl);
-        split_ds(Y, yh, yl);
-        split_ds(Z, zh, zl);
-        const float m = __double2float_rn(M);
-        const float vx = __double2float_rn(VX), vy = __double2float_rn(VY), vz = __double2float_rn(VZ);
-        JMixed r;
-        r.q[0] = make_float4(xh, xh, yh, yh);
-        r.q[1] = make_float4(zh, zh, m, m);
-        r.q[2] = make_float4(xl, xl, yl, yl);
-        r.q[3] = make_float4(zl, zl, vx, vx);
-        r.q[4] = make_float4(vy, vy, vz, vz);
-        jm[k] = r;
-    }
-    if (jd) {
-        JF64 r;
-        r.q[0] = make_double2(X, Y);
-        r.q[1] = make_double2(Z, M);
-        r.q[2] = make_double2(VX, VY);
-        r.q[3] = make_double2(VZ, 0.0);
-        jd[k] = r;
-    }
-}
-
-// Predictor x_p = x + v dt + a dt^2/2 + jerk dt^3/6, v_p = v + a dt + jerk dt^2/2
-// (dt = t - t0) of record k, then its j images; records [n, n_pad) are
-// zero-mass padding.  Loads bypass L1: inside the fused step kernel other
-// CTAs have just corrected some of these particles.
-__device__ __forceinline__ void predict_one(int k, int n, double t, int predict, const double *m, const double *x,
-                                            const double *v, const double *a, const double *jk, const double *t0,
-                                            double *xp, double *vp, JMixed *jm, JF64 *jd, unsigned *err)
-{
-    if (k >= n) {
-        write_images(k, PAD_POS, PAD_POS, PAD_POS, 0.0, 0.0, 0.0, 0.0, jm, jd);
-        return;
-    }
-    double X[3], V[3];
-    if (predict) {
-        const double dt = t - __ldcg(t0 + k);
-        const double dt2 = dt * dt * 0.5, dt3 = dt2 * dt * (1.0 / 3.0);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const size_t o = 3 * (size_t)k + c;
-            const double vo = __ldcg(v + o), ao = __ldcg(a + o);
-            X[c] = __ldcg(x + o) + vo * dt + ao * dt2 + __ldcg(jk + o) * dt3;
-            V[c] = vo + ao * dt + __ldcg(jk + o) * dt2;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            X[c] = __ldcg(x + 3 * (size_t)k + c);
-            V[c] = __ldcg(v + 3 * (size_t)k + c);
-        }
-    }
-    if (xp) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            xp[3 * (size_t)k + c] = X[c];
-            vp[3 * (size_t)k + c] = V[c];
-        }
-    }
-    const double M = m[k];
-    if (!(isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2]) && isfinite(V[0]) && isfinite(V[1]) &&
-          isfinite(V[2]) && isfinite(M)))
-        atomicOr(err, ERR_NONFINITE);
-    write_images(k, X[0], X[1], X[2], M, V[0], V[1], V[2], jm, jd);
 }
 
 __global__ void k_predict_pack(int n, int n_pad, double t, int predict, const double *__restrict__ m,
@@ -366,86 +289,6 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *
         *count_out = due ? base : 0;
         *t_next_out = tn;
     }
-}
-
-// Hermite corrector for the block (Sect. 3): a2, a3 from the two (a, jerk)
-// pairs, corrected x and v, and (update_dt) Aarseth's step on the
-// power-of-two ladder.
-__device__ __forceinline__ bool is_pow2(double d)
-{
-    return (__double_as_longlong(d) & 0x000fffffffffffffll) == 0 && d > 0.0 && isfinite(d);
-}
-
-// Hermite corrector of block member k (particle ilist[k], or k) at t_next
-// from its new a, jerk (acc/jerk row k), and with update_dt its new block
-// step: Aarseth's criterion quantised to a power of two that may shrink
-// freely and double only where t_next is a multiple of the doubled step.
-// FP64 is the scarce pipe on this part (about 1 TFLOP/s, and a single
-// member's dependency chain is latency-bound), so this spends it sparingly:
-//  - 1/dt of a power-of-two step from its exponent (exact), else a divide;
-//  - the powers of dt shared by the three components, fused multiply-adds;
-//  - the criterion dt_A = sqrt(X / Y), X = eta (|a||a2| + |j|^2),
-//    Y = |j||a3| + |a2|^2, compared in squared form (q < dt_A <=> q^2 Y < X),
-//    with |a||a2| = sqrt(|a|^2 |a2|^2): two square roots, no divide;
-//  - "t_next is a multiple of 2 dt" tested exactly by scaling when 2 dt is a
-//    power of two, by fmod otherwise.
-// Member k of the block is particle i; returns its new t_i + dt_i.
-__device__ __forceinline__ double correct_at(size_t i, int k, double t_next, double eta, double dt_min,
-                                             double dt_max, int update_dt, const double *xp, const double *vp,
-                                             const double *acc, const double *jerk, double *bx, double *bv,
-                                             double *ba, double *bj, double *bt, double *bdt)
-{
-    const double dt = t_next - bt[i];
-    const bool p2 = is_pow2(dt);
-    const double idt = p2 ? __longlong_as_double((2046ll << 52) - (__double_as_longlong(dt) & 0x7ff0000000000000ll))
-                          : 1.0 / dt;
-    const double idt2 = idt * idt, idt3 = idt2 * idt;
-    const double dt2 = dt * dt, dt4 = dt2 * dt2;
-    const double c3 = dt2 * dt * (1.0 / 6.0), c4 = dt4 * (1.0 / 24.0), c5 = dt4 * dt * (1.0 / 120.0);
-    const double dt6 = 6.0 * dt;
-    double A = 0.0, J = 0.0, N2 = 0.0, N3 = 0.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
-        const double a1 = acc[3 * (size_t)k + c], j1 = jerk[3 * (size_t)k + c];
-        const double da = a0 - a1;
-        const double a2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da) * idt2;
-        const double a3 = fma(dt6, j0 + j1, 12.0 * da) * idt3;
-        bx[3 * i + c] = fma(a3, c5, fma(a2, c4, xp[3 * i + c]));
-        bv[3 * i + c] = fma(a3, c4, fma(a2, c3, vp[3 * i + c]));
-        ba[3 * i + c] = a1;
-        bj[3 * i + c] = j1;
-        const double a2e = fma(dt, a3, a2);  // a2 at the end of the step
-        A = fma(a1, a1, A);
-        J = fma(j1, j1, J);
-        N2 = fma(a2e, a2e, N2);
-        N3 = fma(a3, a3, N3);
-    }
-    bt[i] = t_next;
-    if (update_dt) {
-        const double X = eta * (sqrt(A * N2) + J), Y = sqrt(J * N3) + N2;
-        double q = dt;
-        if (X == 0.0 && Y == 0.0) {
-            // no criterion (0 / 0): keep the step
-        } else if (X < dt2 * Y) {
-            while (q > dt_min && X < q * q * Y)
-                q *= 0.5;
-        } else if (X >= 4.0 * dt2 * Y && 2.0 * dt <= dt_max) {
-            bool multiple;
-            if (p2) {
-                const double r = t_next * (0.5 * idt);  // exact: a power-of-two scaling
-                multiple = r == trunc(r);
-            } else {
-                multiple = fmod(t_next, 2.0 * dt) == 0.0;
-            }
-            if (multiple)
-                q = 2.0 * dt;
-        }
-        q = fmin(fmax(q, dt_min), dt_max);
-        bdt[i] = q;
-        return t_next + q;
-    }
-    return t_next + bdt[i];
 }
 
 __device__ __forceinline__ void correct_one(int k, const int32_t *ilist, double t_next, double eta, double dt_min,

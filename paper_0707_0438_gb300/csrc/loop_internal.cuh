@@ -63,4 +63,31 @@ struct StepArgs {
 cudaError_t launch_block_step(const StepArgs &a, int ctas, cudaStream_t st);
 constexpr int STEP_CTAS_PER_SM = 2;
 
+// Shared-step Hermite runs of at most SH_MAX_N particles in one cooperative
+// launch (shared_steps.cu): one CTA per SM owns a slice of the particles and
+// predicts and corrects it; the predicted j image goes through two global
+// buffers (even and odd steps) and one bounded grid barrier per step; each
+// CTA copies the whole image into its shared memory and sums its own
+// particles against it (mixed precision).
+constexpr int SH_MAX_N = 2048;
+struct SharedStepArgs {
+    int n, n_pad;             // particles; image records (a multiple of TILE_J)
+    const double *m;
+    double *x, *v, *a, *jerk_b, *t_b, *dt_b;  // FP64 base state, corrected in place
+    double *xp, *vp;          // predicted positions and velocities (the corrector's input)
+    double *f_acc, *f_jerk, *f_pot;  // force rows of the last evaluation (pot may be null)
+    JMixed *img;              // [2][n_pad] predicted j images of even and odd steps
+    unsigned *bar;            // [2] grid barrier: arrivals, generation (arrivals 0 between launches)
+    double eps2, rmin2, G;
+    double eta, dt_min, dt_max;
+    double t0, dt;            // the run starts at t0 and takes n_steps steps of dt
+    int n_steps;
+    int ctas;                 // CTAs of the launch (all resident: a cooperative launch)
+    unsigned *err;
+};
+// CTAs of a shared-step launch for n particles on the current device (one per SM, at most n), or 0
+// when the kernel does not fit.
+int shared_steps_grid(int n, bool guard);
+cudaError_t launch_shared_steps(const SharedStepArgs &a, bool guard, cudaStream_t st);
+
 }  // namespace kirin

@@ -1,0 +1,85 @@
+"""Shared-step Hermite runs of small systems in one cooperative launch (one CTA per SM; the predicted
+j image published through global memory and a grid barrier per step): against the FP64 oracle's
+Hermite steps (Sect. 3) and against the per-kernel path, for ragged sizes up to 2048, with and without
+the zero-softening guard."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hermite
+from paper_0707_0438_gb300 import abi, metrics, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(p, eps, dt, steps, persistent, r_min=0.0):
+    with abi.Kirin(p.n, eps, r_min=r_min, precision="mixed") as k:
+        k.set_shared_persistent(persistent)
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        active = k.shared_persistent_active()
+        k.hermite_shared_run(dt, steps)
+        st = k.get_state()
+        after = k.forces()  # the run leaves a consistent context behind
+    return active, st, after
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 151, 152, 153, 777, 1024, 1500, 2048])
+def test_persistent_shared_run_matches_the_oracle(kirin_lib, n):
+    """Sizes below, at and above one particle per CTA (152 SMs), ragged tiles and the largest system."""
+    p = workloads.plummer(n, (1001, n), eps=1.0 / 256)
+    dt, steps = 1.0 / 1024, 10
+    xr, vr, ar, _, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, dt, steps)
+    active, st, after = _run(p, p.eps, dt, steps, True)
+    assert active
+    assert np.all(st["t"] == steps * dt)
+    assert np.abs(st["x"] - xr).max() <= 1e-7 * max(np.abs(p.x).max(), 1e-300)
+    assert np.abs(st["v"] - vr).max() <= 1e-6 * max(np.abs(p.v).max(), 1e-300)
+    if n > 1:
+        assert np.median(metrics.rel_err_vec(st["a"], ar)) <= 1e-6
+        ref = oracle.acc_jerk_pot(p.m, st["x"], st["v"], p.eps)
+        assert np.median(metrics.rel_err_vec(after[0], ref[0])) <= 1e-6
+
+
+@pytest.mark.parametrize("n,eps,r_min,tol", [(1024, 1.0 / 256, 0.0, 1e-10), (900, 0.0, 1e-6, 1e-8)])
+def test_persistent_shared_run_agrees_with_the_kernel_path(kirin_lib, n, eps, r_min, tol):
+    """The same 64 steps through the single launch and through the predictor, force and corrector
+    kernels.  The j are summed in other orders, so the states agree to rounding.  Without softening a
+    close pair magnifies that difference step by step (3e-10 of max |x| measured after 64 steps),
+    hence the wider bound there."""
+    p = workloads.plummer(n, 4040, eps=eps)
+    dt, steps = 1.0 / 1024, 64
+    a_on, on, _ = _run(p, eps, dt, steps, True, r_min)
+    a_off, off, _ = _run(p, eps, dt, steps, False, r_min)
+    assert a_on and not a_off
+    assert np.all(on["t"] == off["t"])
+    assert np.abs(on["x"] - off["x"]).max() <= tol * np.abs(p.x).max()
+    assert np.median(metrics.rel_err_vec(on["a"], off["a"])) <= 1e-6
+
+
+def test_persistent_shared_run_is_deterministic(kirin_lib):
+    """Two contexts, the same run: the same bits (fixed CTA slices, fixed reduction order)."""
+    p = workloads.plummer(1500, 77, eps=1.0 / 256)
+    _, a, fa = _run(p, p.eps, 1.0 / 1024, 20, True)
+    _, b, fb = _run(p, p.eps, 1.0 / 1024, 20, True)
+    for key in ("x", "v", "a", "j", "t", "dt"):
+        assert np.array_equal(a[key], b[key]), key
+    for u, w in zip(fa, fb):
+        assert np.array_equal(u, w)
+
+
+def test_persistent_shared_run_limits(kirin_lib):
+    """Above 2048 particles, in FP64 and under a fixed launch shape the per-kernel path runs."""
+    p = workloads.plummer(2049, 1, eps=0.01)
+    with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        assert not k.shared_persistent_active()
+    q = workloads.plummer(1000, 2, eps=0.01)
+    with abi.Kirin(q.n, q.eps, precision="fp64") as k:
+        k.set_j_particles(q.m, q.x, q.v)
+        assert not k.shared_persistent_active()
+    with abi.Kirin(q.n, q.eps, precision="mixed") as k:
+        k.set_j_particles(q.m, q.x, q.v)
+        assert k.shared_persistent_active()
+        k.set_launch(2, 4)
+        assert not k.shared_persistent_active()
