@@ -117,7 +117,8 @@ struct kirin_ctx {
     int sh_fit_guard = -1;
     JMixed *sh_img = nullptr;  // [2][sh_img_pad]: the even and odd steps' j images
     int64_t sh_img_pad = 0;
-    unsigned *sh_bar = nullptr;  // grid barrier words (zero between launches)
+    unsigned *sh_arrivals = nullptr;  // the launch's arrival counter
+    uint32_t sh_count = 0;            // its value between launches
 
     // nearest-neighbour search of the host-pointer path (GRAPE's neighbour list)
     bool want_nn = false;
@@ -413,7 +414,7 @@ void free_all(kirin_ctx *c)
     void *ptrs[] = {c->bm, c->bx, c->bv, c->ba, c->bj, c->bt, c->bdt, c->xp, c->vp, c->jm, c->jd,
                     c->d_ilist, c->d_acc, c->d_jerk, c->d_pot, c->d_partial, c->d_err, c->d_scal,
                     c->d_count, c->d_sel_counts, c->d_nn, c->d_nn_r2, c->d_step_counts, c->d_send, c->d_recv,
-                    c->sh_img, c->sh_bar};
+                    c->sh_img, c->sh_arrivals};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -1368,19 +1369,21 @@ int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps)
             }
             ctx->sh_img_pad = n_pad;
         }
-        if (!ctx->sh_bar) {
-            if (cudaMalloc(&ctx->sh_bar, 2 * sizeof(unsigned)) != cudaSuccess) {
-                ctx->sh_bar = nullptr;
+        if (!ctx->sh_arrivals) {
+            if (cudaMalloc(&ctx->sh_arrivals, sizeof(unsigned)) != cudaSuccess) {
+                ctx->sh_arrivals = nullptr;
                 cudaGetLastError();
-                return set_msg(ctx, KIRIN_ENOMEM, "hermite_shared_run: no room for the barrier words");
+                return set_msg(ctx, KIRIN_ENOMEM, "hermite_shared_run: no room for the arrival counter");
             }
-            CK(ctx, cudaMemsetAsync(ctx->sh_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+            CK(ctx, cudaMemsetAsync(ctx->sh_arrivals, 0, sizeof(unsigned), ctx->stream));
+            ctx->sh_count = 0;
         }
         SharedStepArgs a{};
         a.n = n;
         a.n_pad = (int)n_pad;
         a.img = ctx->sh_img;
-        a.bar = ctx->sh_bar;
+        a.arrivals = ctx->sh_arrivals;
+        a.arrivals0 = ctx->sh_count;
         a.ctas = ctx->sh_grid;
         a.m = ctx->bm;
         a.x = ctx->bx;
@@ -1405,6 +1408,7 @@ int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps)
         a.n_steps = (int)n_steps;
         a.err = ctx->d_err;
         CK(ctx, launch_shared_steps(a, guard_on(ctx), ctx->stream));
+        ctx->sh_count += (uint32_t)ctx->sh_grid * (uint32_t)n_steps;  // every CTA arrives once per step
         double t = ctx->t_shared;
         for (int64_t s = 0; s < n_steps; ++s)  // the kernel's time arithmetic, step by step
             t = t + dt;
@@ -1414,8 +1418,11 @@ int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps)
         ctx->images_dirty = true;
         ctx->pending = false;
         const int rc = read_device_errors(ctx);
-        if (rc == KIRIN_ETIMEOUT)  // CTAs left mid-barrier: the words start from zero again
-            CK(ctx, cudaMemsetAsync(ctx->sh_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+        if (rc == KIRIN_ETIMEOUT) {  // CTAs left mid-run: the counter starts from zero again
+            CK(ctx, cudaMemsetAsync(ctx->sh_arrivals, 0, sizeof(unsigned), ctx->stream));
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+            ctx->sh_count = 0;
+        }
         return rc;
     }
     for (int64_t s = 0; s < n_steps; ++s) {  // enqueued back to back; one synchronisation at the end

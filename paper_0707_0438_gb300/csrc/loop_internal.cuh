@@ -66,9 +66,10 @@ constexpr int STEP_CTAS_PER_SM = 2;
 // Shared-step Hermite runs of at most SH_MAX_N particles in one cooperative
 // launch (shared_steps.cu): one CTA per SM owns a slice of the particles and
 // predicts and corrects it; the predicted j image goes through two global
-// buffers (even and odd steps) and one bounded grid barrier per step; each
-// CTA copies the whole image into its shared memory and sums its own
-// particles against it (mixed precision).
+// buffers (even and odd steps), and each CTA counts its arrival on a counter
+// that only grows; each CTA waits for all arrivals of the step, copies the
+// whole image into its shared memory and sums its own particles against it
+// (mixed precision).
 constexpr int SH_MAX_N = 2048;
 struct SharedStepArgs {
     int n, n_pad;             // particles; image records (a multiple of TILE_J)
@@ -77,7 +78,8 @@ struct SharedStepArgs {
     double *xp, *vp;          // predicted positions and velocities (the corrector's input)
     double *f_acc, *f_jerk, *f_pot;  // force rows of the last evaluation (pot may be null)
     JMixed *img;              // [2][n_pad] predicted j images of even and odd steps
-    unsigned *bar;            // [2] grid barrier: arrivals, generation (arrivals 0 between launches)
+    unsigned *arrivals;       // the arrival counter: each CTA adds n_steps per launch (mod 2^32)
+    unsigned arrivals0;       // its value before this launch
     double eps2, rmin2, G;
     double eta, dt_min, dt_max;
     double t0, dt;            // the run starts at t0 and takes n_steps steps of dt

@@ -6,19 +6,26 @@
 // predictor, force, split-reduction and corrector kernels of a step waits
 // microseconds on its launch and on memory for well under a microsecond of
 // arithmetic.  Here one CTA per SM stays resident for the whole run:
-//  * CTA b owns particles [b n / P, (b + 1) n / P) of P CTAs.  It corrects
-//    them (the step kernels' corrector) and at once predicts them to the
-//    next step (the step kernels' predictor), into the global j image of
-//    the step's parity;
-//  * one grid barrier per step publishes the image.  Two images alternate, so
-//    a CTA that is still summing step s never sees step s + 1's records;
+//  * CTA b owns particles [b n / P, (b + 1) n / P) of P CTAs and keeps their
+//    FP64 state in shared memory for the launch (written through to the
+//    context's arrays every step).  Warps 0, 1 and 2 correct the x, y and z
+//    components of the slice and predict them at once to the next step, with
+//    the step kernels' arithmetic: FP64 is the scarce pipe on this part and
+//    a warp instruction costs the same with 1 or 32 lanes, so three short
+//    chains on three SM sub-partitions beat one long chain;
+//  * the predicted records go to the global j image of the next step's
+//    parity (two images alternate), and the CTA adds 1 to an arrival counter
+//    that only grows (a fire-and-forget release add).  Before step s each CTA
+//    waits until the counter holds (s + 1) arrivals per CTA (one thread polls,
+//    bounded), which also proves that nobody still reads the image it is
+//    about to overwrite: no CTA can arrive a (s + 2)-th time before that;
 //  * every CTA copies the whole image into its shared memory (a 1-D bulk copy
 //    and an mbarrier per tile) and sums its own particles against it with the
-//    pair body of the force kernels: two i per thread, j-groups of threads
-//    over the j of each tile, partial sums folded in double-single, the
-//    groups of a warp combined by shuffles and the warps in warp order.
-// FP64 work stays on the owning thread (FP64 is the scarce pipe here); the
-// step's only grid-wide dependency is the barrier.
+//    pair body of the force kernels: two i per thread; each warp takes a
+//    contiguous sixteenth of the j, its groups of threads interleaved record
+//    by record (consecutive 80-byte records fall on disjoint banks); partial
+//    sums folded in double-single, the groups of a warp combined by shuffles
+//    and the warps in warp order.
 #include <cuda_runtime.h>
 
 #include "kirin_internal.cuh"
@@ -32,22 +39,38 @@ namespace {
 
 constexpr int SH_THREADS = 512;
 constexpr int SH_WARPS = SH_THREADS / 32;
+constexpr int SH_MAX_OWN = 32;  // particles per CTA (groups of up to 16 threads, two i each)
 constexpr int SH_FLUSH_J = 256;  // j per FP32 partial sum and thread, as in the force kernels
 constexpr int SH_MAX_TILES = SH_MAX_N / TILE_J;
 constexpr int SH_BAR_BYTES = 256;  // the tiles' mbarriers, ahead of the image
 constexpr uint32_t SH_TILE_BYTES = TILE_J * sizeof(JMixed);
 static_assert(SH_MAX_N % TILE_J == 0 && SH_MAX_TILES * 8 <= SH_BAR_BYTES, "mbarrier area");
 static_assert(SH_TILE_BYTES % 16 == 0 && SH_BAR_BYTES % 16 == 0, "bulk copies want 16-byte multiples");
+static_assert(SH_MAX_N * (SH_MAX_OWN / 2) / SH_THREADS <= SH_FLUSH_J, "one fold per step holds a group's j");
 
-// GT threads of a j-group hold up to 2 GT particles, two per thread (packed FP32x2 lanes); the
-// SH_THREADS / GT groups share out the j of every tile.
+// Own-state rows in shared memory, doubles [row][I_CTA]: per component c the
+// rows 6c + (x, v, a, jerk, x_p, v_p), the 7 force rows of the step, then the
+// step's corrector and predictor intervals and powers (computed while the CTA
+// waits for the others).
+constexpr int ST_ROWS = 3 * 6 + 7 + 7 + 3;
+__device__ __forceinline__ int st_row(int c, int f) { return 6 * c + f; }
+__device__ __forceinline__ int force_row(int q7) { return 18 + q7; }
+constexpr int CORR_ROW = 25, PRED_ROW = 32;
+
 template <int GT>
 __host__ __device__ constexpr size_t sh_red_bytes() { return (size_t)SH_WARPS * 7 * 2 * GT * sizeof(float2); }
 
 template <int GT>
 __host__ __device__ constexpr size_t sh_smem_bytes(int n_pad)
 {
-    return SH_BAR_BYTES + (size_t)n_pad * sizeof(JMixed) + sh_red_bytes<GT>();
+    return SH_BAR_BYTES + (size_t)n_pad * sizeof(JMixed) + sh_red_bytes<GT>() + (size_t)ST_ROWS * 2 * GT * sizeof(double);
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
@@ -62,43 +85,69 @@ __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Order this thread's earlier global accesses (made visible to it by the grid barrier) before its
-// later bulk copies, which read global memory through the async proxy.
+// Order this thread's earlier global accesses before later bulk copies, which read global memory
+// through the async proxy.
 __device__ __forceinline__ void fence_proxy_async_global()
 {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Grid-wide barrier of a cooperative launch, bounded: bar[0] counts the CTAs that arrived, bar[1] is
-// the generation.  The last CTA to arrive zeroes the count and advances the generation; the others
-// wait for it at most WAIT_LIMIT_NS, then flag ERR_TIMEOUT and return false (the host zeroes the
-// barrier after a failed run).  Every thread of the CTA calls it.
-__device__ bool grid_sync(unsigned *bar, unsigned *err)
+// This CTA's image records of its next step are written (the CTA barrier orders every thread's
+// stores before thread 0's release): one more arrival.
+__device__ __forceinline__ void arrive(unsigned *arrivals)
 {
-    __shared__ int s_ok;
     __syncthreads();
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(arrivals) : "memory");
+}
+
+// Wait until the counter reaches target (compared modulo 2^32): thread 0 polls relaxed for at most
+// WAIT_LIMIT_NS, then one acquire load orders what the arrivals published.  False (and
+// ERR_TIMEOUT) when it never came; every thread of the CTA calls it and gets the same answer.
+__device__ __forceinline__ bool wait_arrivals(const unsigned *arrivals, unsigned target, unsigned *err)
+{
+    bool ok = true;
     if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned gen = ld_acquire_gpu(bar + 1);
-        __threadfence();  // the CTA's writes (ordered before by the CTA barrier) before the arrival
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            st_release_gpu(bar + 1, gen + 1);
-        } else {
+        if ((int)(ld_relaxed_gpu(arrivals) - target) < 0) {
             const unsigned long long t0 = global_ns();
-            while (ld_acquire_gpu(bar + 1) == gen) {
+            while ((int)(ld_relaxed_gpu(arrivals) - target) < 0)
                 if (global_ns() - t0 > WAIT_LIMIT_NS) {
-                    atomicOr(err, ERR_TIMEOUT);
-                    ok = 0;
+                    ok = false;
                     break;
                 }
-            }
         }
-        __threadfence();
-        s_ok = ok;
+        if (ok)
+            ok = (int)(ld_acquire_gpu(arrivals) - target) >= 0;  // it only grows: true, and now ordered
     }
-    __syncthreads();
-    return s_ok != 0;
+    const bool failed = __syncthreads_or(!ok);
+    if (failed && threadIdx.x == 0)
+        atomicOr(err, ERR_TIMEOUT);
+    return !failed;
+}
+
+// Component c of particle k predicted to X, V: the FP64 rows x_p, v_p, and the c-parts of its j
+// image record (the layout write_images gives, written here a float2 at a time).
+__device__ __forceinline__ void emit_component(const SharedStepArgs &A, JMixed *img, int c, int k, double X, double V,
+                                               double M)
+{
+    A.xp[3 * (size_t)k + c] = X;
+    A.vp[3 * (size_t)k + c] = V;
+    float h, l;
+    split_ds(X, h, l);
+    const float vf = __double2float_rn(V);
+    float2 *rec = reinterpret_cast<float2 *>(img + k);
+    rec[c] = make_float2(h, h);           // q[0].xy, q[0].zw, q[1].xy: x, y, z high words
+    rec[4 + c] = make_float2(l, l);       // q[2].xy, q[2].zw, q[3].xy: low words
+    rec[7 + c] = make_float2(vf, vf);     // q[3].zw, q[4].xy, q[4].zw: velocity
+    bool bad = !(isfinite(X) && isfinite(V));
+    if (c == 0) {
+        const float mf = __double2float_rn(M);
+        rec[3] = make_float2(mf, mf);     // q[1].zw: mass
+        bad = bad || !isfinite(M);
+    }
+    if (bad)
+        atomicOr(A.err, ERR_NONFINITE);
+    fence_proxy_async_global();
 }
 
 template <int GT, bool GUARD>
@@ -106,43 +155,82 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
 {
     constexpr int GROUPS = SH_THREADS / GT;
     constexpr int I_CTA = 2 * GT;
-    constexpr int JG = TILE_J / GROUPS;  // j per group and tile
-    static_assert(32 % GT == 0 && JG >= 1, "groups tile the warps and the j tile");
+    static_assert(32 % GT == 0 && I_CTA <= SH_MAX_OWN, "groups tile the warps");
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int n = A.n, n_pad = A.n_pad, n_tiles = n_pad / TILE_J;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);                     // [n_tiles]
     JMixed *img = reinterpret_cast<JMixed *>(smem_raw + SH_BAR_BYTES);           // [n_pad]
-    float2 *red = reinterpret_cast<float2 *>(smem_raw + SH_BAR_BYTES + (size_t)A.n_pad * sizeof(JMixed));
-    const int n = A.n, n_pad = A.n_pad, n_tiles = n_pad / TILE_J;
+    float2 *red = reinterpret_cast<float2 *>(img + n_pad);                        // [SH_WARPS][7][I_CTA]
+    double *st = reinterpret_cast<double *>(red + SH_WARPS * 7 * I_CTA);          // [ST_ROWS][I_CTA]
     const int P = (int)gridDim.x, b = (int)blockIdx.x;
     const int lo = (int)((long long)n * b / P), hi = (int)((long long)n * (b + 1) / P);
-    const int own = hi - lo;  // at most I_CTA (the launch checks)
+    const int own = hi - lo;  // 1 .. I_CTA (the launch checks)
     const int tid = (int)threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = tid / GT, s = tid - g * GT;
+    // warp w's j: [wb, wb + n_pad / SH_WARPS); group gw of the warp reads wb + gw + W jj, jj < L
+    constexpr int W = 32 / GT;
+    const int L = n_pad / GROUPS, wb = warp * (n_pad / SH_WARPS), gw = g - warp * W;
     const float eps2f = (float)A.eps2, rmin2f = (float)A.rmin2;
     const bool need_mask = eps2f != 0.f;  // with eps = 0 the guard zeroes the self pair anyway
+    const unsigned count0 = A.arrivals0, per_step = (unsigned)P;
+    // the component lanes: warp c < 3, lane = slot of the particle
+    const bool comp = warp < 3 && lane < own;
+    const int c = warp, kc = lo + lane;
     if (tid == 0) {
         for (int q = 0; q < n_tiles; ++q)
             mbar_init(&bars[q], 1);
         mbar_fence_init();
     }
+    for (int o = tid; o < 12 * own; o += SH_THREADS) {
+        const int slot = o / 12, r = o - 12 * slot, f = r / 3, cc = r - 3 * f;
+        const double *src = f == 0 ? A.x : f == 1 ? A.v : f == 2 ? A.a : A.jerk_b;
+        st[st_row(cc, f) * I_CTA + slot] = src[3 * (size_t)(lo + slot) + cc];
+    }
+    double tb = 0.0, M = 0.0;  // the component lane's particle time and mass
+    if (comp) {
+        tb = A.t_b[kc];
+        M = A.m[kc];
+    }
+    __syncthreads();
     // step 0's image: own particles predicted to t0 + dt; the last CTA writes both images' padding
-    if (tid < own)
-        predict_one(lo + tid, n, A.t0 + A.dt, 1, A.m, A.x, A.v, A.a, A.jerk_b, A.t_b, A.xp, A.vp, A.img, nullptr,
-                    A.err);
-    if (b == P - 1)
+    if (comp) {
+        const PredictDt Pd = predict_dt((A.t0 + A.dt) - tb);
+        double X, V;
+        predict_xv(Pd, st[st_row(c, 0) * I_CTA + lane], st[st_row(c, 1) * I_CTA + lane],
+                   st[st_row(c, 2) * I_CTA + lane], st[st_row(c, 3) * I_CTA + lane], X, V);
+        st[st_row(c, 4) * I_CTA + lane] = X;
+        st[st_row(c, 5) * I_CTA + lane] = V;
+        emit_component(A, A.img, c, kc, X, V, M);
+    }
+    if (b == P - 1) {
         for (int k = n + tid; k < n_pad; k += SH_THREADS) {
-            predict_one(k, n, 0.0, 0, A.m, A.x, A.v, A.a, A.jerk_b, A.t_b, nullptr, nullptr, A.img, nullptr, A.err);
-            predict_one(k, n, 0.0, 0, A.m, A.x, A.v, A.a, A.jerk_b, A.t_b, nullptr, nullptr, A.img + n_pad, nullptr,
-                        A.err);
+            write_images(k, PAD_POS, PAD_POS, PAD_POS, 0.0, 0.0, 0.0, 0.0, A.img, nullptr);
+            write_images(k, PAD_POS, PAD_POS, PAD_POS, 0.0, 0.0, 0.0, 0.0, A.img + n_pad, nullptr);
         }
-    fence_proxy_async_global();  // the image records written above are read by bulk copies
-    if (!grid_sync(A.bar, A.err))
-        return;
+        fence_proxy_async_global();
+    }
+    arrive(A.arrivals);
     double t = A.t0;
     for (int step = 0; step < A.n_steps; ++step) {
         const double tn = t + A.dt;
         const uint32_t parity = (uint32_t)(step & 1);
-        // 1. the whole image of this step into shared memory, a tile per mbarrier
+        // 0. while thread 0 waits: the corrector's interval and powers (warp 1, from the particle's
+        //    own time) and the predictor's for the next step (warp 2), into shared memory
+        if (warp == 1 && lane < own) {
+            const CorrectDt S = correct_dt(tn - tb);
+            const double r[7] = {S.dt, S.idt2, S.idt3, S.c3, S.c4, S.c5, S.dt6};
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+                st[(CORR_ROW + q) * I_CTA + lane] = r[q];
+        } else if (warp == 2 && lane < own) {
+            const PredictDt Pd = predict_dt((tn + A.dt) - tn);
+            st[PRED_ROW * I_CTA + lane] = Pd.dt;
+            st[(PRED_ROW + 1) * I_CTA + lane] = Pd.dt2;
+            st[(PRED_ROW + 2) * I_CTA + lane] = Pd.dt3;
+        }
+        // 1. every CTA's records of this step are out: the whole image into shared memory
+        if (!wait_arrivals(A.arrivals, count0 + ((unsigned)step + 1u) * per_step, A.err))
+            return;  // no copy of this step was issued yet
         if (tid == 0) {
             fence_proxy_async_global();
             const JMixed *src = A.img + (size_t)(step & 1) * n_pad;
@@ -151,10 +239,13 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
                 bulk_g2s(img + (size_t)q * TILE_J, src + (size_t)q * TILE_J, SH_TILE_BYTES, &bars[q]);
             }
         }
-        // 2. own particles (thread s of group g holds slots s and s + GT) against every j
-        //    (a failed wait is made warp-uniform, so no lane leaves its warp's votes behind)
+        // 2. own particles (thread s of group g holds slots s and s + GT) against the group's j; wait
+        //    for the tiles this thread reads (a failed wait is made warp-uniform, so no lane leaves its
+        //    warp's votes behind)
         bool failed = !__all_sync(0xffffffffu, mbar_wait_bounded(&bars[lo / TILE_J], parity) &&
-                                                   mbar_wait_bounded(&bars[(hi - 1) / TILE_J], parity));
+                                                   mbar_wait_bounded(&bars[(hi - 1) / TILE_J], parity) &&
+                                                   mbar_wait_bounded(&bars[wb / TILE_J], parity) &&
+                                                   mbar_wait_bounded(&bars[(wb + W * L - 1) / TILE_J], parity));
         int idx[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -169,29 +260,16 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
                                        rmin2f);
             Tile7 tt;
             tt.zero();
-            int since = 0;
-            for (int q = 0; q < n_tiles; ++q) {
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[q], parity))) {
-                    failed = true;
-                    break;
-                }
-                const int j0 = q * TILE_J + g * JG;
-                const JMixed *T = img + j0;
-                const bool mine =
-                    (unsigned)(idx[0] - j0) < (unsigned)JG || (unsigned)(idx[1] - j0) < (unsigned)JG;
-                if (need_mask && __any_sync(0xffffffffu, mine)) {
-                    for (int jj = 0; jj < JG; ++jj)
-                        pair<GUARD, MODE_ACC_JERK_POT, true>(T[jj], I, tt, j0 + jj, idx[0], idx[1]);
-                } else {
-#pragma unroll
-                    for (int jj = 0; jj < JG; ++jj)
-                        pair<GUARD, MODE_ACC_JERK_POT>(T[jj], I, tt);
-                }
-                since += JG;
-                if (since >= SH_FLUSH_J) {
-                    fold<MODE_ACC_JERK_POT>(tt, acc0, acc1);
-                    since = 0;
-                }
+            const JMixed *T = img + wb + gw;
+            const bool mine =
+                (unsigned)(idx[0] - wb) < (unsigned)(W * L) || (unsigned)(idx[1] - wb) < (unsigned)(W * L);
+            if (need_mask && __any_sync(0xffffffffu, mine)) {
+                for (int jj = 0; jj < L; ++jj)
+                    pair<GUARD, MODE_ACC_JERK_POT, true>(T[W * jj], I, tt, wb + gw + W * jj, idx[0], idx[1]);
+            } else {
+#pragma unroll 4
+                for (int jj = 0; jj < L; ++jj)
+                    pair<GUARD, MODE_ACC_JERK_POT>(T[W * jj], I, tt);
             }
             fold<MODE_ACC_JERK_POT>(tt, acc0, acc1);
         }
@@ -205,7 +283,7 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
                         break;
                     }
             }
-            return;  // the other CTAs give up at their next grid barrier
+            return;  // the other CTAs give up waiting for this one's flag
         }
         // 3. the groups of a warp combined by shuffles (a fixed tree), then the warps in warp order
 #pragma unroll
@@ -238,28 +316,58 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
                 l = __fadd_rn(l, v.y);
             }
             const double val = (double)h + (double)l;
+            const double row = q7 < 6 ? A.G * val : -A.G * val;
+            st[force_row(q7) * I_CTA + slot] = row;
             const int p = lo + slot;
             if (q7 < 3)
-                A.f_acc[3 * (size_t)p + q7] = A.G * val;
+                A.f_acc[3 * (size_t)p + q7] = row;
             else if (q7 < 6)
-                A.f_jerk[3 * (size_t)p + (q7 - 3)] = A.G * val;
+                A.f_jerk[3 * (size_t)p + (q7 - 3)] = row;
             else if (A.f_pot)
-                A.f_pot[p] = -A.G * val;
+                A.f_pot[p] = row;
         }
-        __syncthreads();  // the rows are read back by the corrector
-        // 4. own particles corrected (shared step: the step size stays), then predicted to the next
-        //    step into the other image
-        if (tid < own) {
-            const int k = lo + tid;
-            correct_at((size_t)k, k, tn, A.eta, A.dt_min, A.dt_max, 0, A.xp, A.vp, A.f_acc, A.f_jerk, A.x, A.v,
-                       A.a, A.jerk_b, A.t_b, A.dt_b);
-            if (step + 1 < A.n_steps)
-                predict_one(k, n, tn + A.dt, 1, A.m, A.x, A.v, A.a, A.jerk_b, A.t_b, A.xp, A.vp,
-                            A.img + (size_t)((step + 1) & 1) * n_pad, nullptr, A.err);
-            fence_proxy_async_global();
+        __syncthreads();
+        // 4. component c of each own particle corrected (shared step: the step size stays), then
+        //    predicted to the next step into the other image
+        if (comp) {
+            CorrectDt S;
+            S.dt = st[CORR_ROW * I_CTA + lane];
+            S.idt2 = st[(CORR_ROW + 1) * I_CTA + lane];
+            S.idt3 = st[(CORR_ROW + 2) * I_CTA + lane];
+            S.c3 = st[(CORR_ROW + 3) * I_CTA + lane];
+            S.c4 = st[(CORR_ROW + 4) * I_CTA + lane];
+            S.c5 = st[(CORR_ROW + 5) * I_CTA + lane];
+            S.dt6 = st[(CORR_ROW + 6) * I_CTA + lane];
+            const double a1 = st[force_row(c) * I_CTA + lane], j1 = st[force_row(3 + c) * I_CTA + lane];
+            double x1, v1, a2, a3;
+            correct_xv(S, st[st_row(c, 2) * I_CTA + lane], st[st_row(c, 3) * I_CTA + lane], a1, j1,
+                       st[st_row(c, 4) * I_CTA + lane], st[st_row(c, 5) * I_CTA + lane], x1, v1, a2, a3);
+            tb = tn;
+            st[st_row(c, 0) * I_CTA + lane] = x1;
+            st[st_row(c, 1) * I_CTA + lane] = v1;
+            st[st_row(c, 2) * I_CTA + lane] = a1;
+            st[st_row(c, 3) * I_CTA + lane] = j1;
+            const size_t o = 3 * (size_t)kc + c;
+            A.x[o] = x1;
+            A.v[o] = v1;
+            A.a[o] = a1;
+            A.jerk_b[o] = j1;
+            if (c == 0)
+                A.t_b[kc] = tn;
+            if (step + 1 < A.n_steps) {
+                PredictDt Pd;
+                Pd.dt = st[PRED_ROW * I_CTA + lane];
+                Pd.dt2 = st[(PRED_ROW + 1) * I_CTA + lane];
+                Pd.dt3 = st[(PRED_ROW + 2) * I_CTA + lane];
+                double X, V;
+                predict_xv(Pd, x1, v1, a1, j1, X, V);
+                st[st_row(c, 4) * I_CTA + lane] = X;
+                st[st_row(c, 5) * I_CTA + lane] = V;
+                emit_component(A, A.img + (size_t)((step + 1) & 1) * n_pad, c, kc, X, V, M);
+            }
         }
-        if (step + 1 < A.n_steps && !grid_sync(A.bar, A.err))
-            return;
+        if (step + 1 < A.n_steps)
+            arrive(A.arrivals);
         t = tn;
     }
 }
@@ -280,7 +388,7 @@ cudaError_t sh_launch(const SharedStepArgs &a, bool query_only, int *grid, cudaS
             (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH_THREADS, sh_smem_bytes<GT>(a.n_pad))) !=
                 cudaSuccess)
             return e;
-        const int ctas = nsm * (per_sm > 0 ? 1 : 0);  // one CTA per SM
+        const int ctas = per_sm > 0 ? nsm : 0;  // one CTA per SM
         *grid = ctas < a.n ? ctas : a.n;
         return cudaSuccess;
     }
@@ -301,12 +409,12 @@ cudaError_t sh_launch(const SharedStepArgs &a, bool query_only, int *grid, cudaS
 template <bool GUARD>
 cudaError_t sh_dispatch(const SharedStepArgs &a, int own_max, bool query_only, int *grid, cudaStream_t st)
 {
+    if (own_max <= 8)
+        return sh_launch<4, GUARD>(a, query_only, grid, st);
     if (own_max <= 16)
         return sh_launch<8, GUARD>(a, query_only, grid, st);
-    if (own_max <= 32)
+    if (own_max <= SH_MAX_OWN)
         return sh_launch<16, GUARD>(a, query_only, grid, st);
-    if (own_max <= 64)
-        return sh_launch<32, GUARD>(a, query_only, grid, st);
     return cudaErrorInvalidValue;
 }
 
@@ -324,8 +432,9 @@ int shared_steps_grid(int n, bool guard)
     // the grid does not depend on the group width (one CTA per SM): ask the widest, then check the
     // share against the width that will run
     int grid = 0;
-    cudaError_t e = guard ? sh_dispatch<true>(a, 64, true, &grid, nullptr) : sh_dispatch<false>(a, 64, true, &grid, nullptr);
-    if (e != cudaSuccess || grid < 1 || own_max_of(n, grid) > 64) {
+    cudaError_t e = guard ? sh_dispatch<true>(a, SH_MAX_OWN, true, &grid, nullptr)
+                          : sh_dispatch<false>(a, SH_MAX_OWN, true, &grid, nullptr);
+    if (e != cudaSuccess || grid < 1 || own_max_of(n, grid) > SH_MAX_OWN) {
         cudaGetLastError();
         return 0;
     }
@@ -342,7 +451,8 @@ int shared_steps_grid(int n, bool guard)
 cudaError_t launch_shared_steps(const SharedStepArgs &a, bool guard, cudaStream_t st)
 {
     if (a.n < 1 || a.n > SH_MAX_N || a.n_pad % TILE_J != 0 || a.n_pad < a.n || a.n_pad > SH_MAX_N ||
-        a.n_steps < 0 || a.ctas < 1 || a.ctas > a.n || own_max_of(a.n, a.ctas) > 64 || !a.img || !a.bar)
+        a.n_steps < 0 || a.ctas < 1 || a.ctas > a.n || own_max_of(a.n, a.ctas) > SH_MAX_OWN || !a.img ||
+        !a.arrivals)
         return cudaErrorInvalidValue;
     if (a.n_steps == 0)
         return cudaSuccess;

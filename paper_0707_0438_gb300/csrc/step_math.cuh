@@ -1,7 +1,7 @@
 // The FP64 step arithmetic of the Hermite integrator (Sect. 3: predictor,
 // Hermite interpolation, corrector and Aarseth's block step; Sect. 3.1: the
 // j images the force kernels read), shared by the step kernels and the
-// cluster-resident shared-step kernel so that both compute the same bits.
+// single-launch shared-step kernel so that both compute the same bits.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,6 +45,28 @@ __device__ __forceinline__ void write_images(int k, double X, double Y, double Z
     }
 }
 
+// Powers of the prediction interval dt and one component of the predictor
+// x_p = x + v dt + a dt^2/2 + jerk dt^3/6, v_p = v + a dt + jerk dt^2/2.
+struct PredictDt {
+    double dt, dt2, dt3;  // dt, dt^2 / 2, dt^3 / 6
+};
+
+__device__ __forceinline__ PredictDt predict_dt(double dt)
+{
+    PredictDt P;
+    P.dt = dt;
+    P.dt2 = dt * dt * 0.5;
+    P.dt3 = P.dt2 * dt * (1.0 / 3.0);
+    return P;
+}
+
+__device__ __forceinline__ void predict_xv(const PredictDt &P, double x, double v, double a, double j, double &X,
+                                           double &V)
+{
+    X = x + v * P.dt + a * P.dt2 + j * P.dt3;
+    V = v + a * P.dt + j * P.dt2;
+}
+
 // Predictor x_p = x + v dt + a dt^2/2 + jerk dt^3/6, v_p = v + a dt + jerk dt^2/2
 // (dt = t - t0) of record k, then its j images; records [n, n_pad) are
 // zero-mass padding.  Loads bypass L1: inside the fused step kernel other
@@ -59,14 +81,11 @@ __device__ __forceinline__ void predict_one(int k, int n, double t, int predict,
     }
     double X[3], V[3];
     if (predict) {
-        const double dt = t - __ldcg(t0 + k);
-        const double dt2 = dt * dt * 0.5, dt3 = dt2 * dt * (1.0 / 3.0);
+        const PredictDt P = predict_dt(t - __ldcg(t0 + k));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t o = 3 * (size_t)k + c;
-            const double vo = __ldcg(v + o), ao = __ldcg(a + o);
-            X[c] = __ldcg(x + o) + vo * dt + ao * dt2 + __ldcg(jk + o) * dt3;
-            V[c] = vo + ao * dt + __ldcg(jk + o) * dt2;
+            predict_xv(P, __ldcg(x + o), __ldcg(v + o), __ldcg(a + o), __ldcg(jk + o), X[c], V[c]);
         }
     } else {
 #pragma unroll
@@ -97,6 +116,44 @@ __device__ __forceinline__ bool is_pow2(double d)
     return (__double_as_longlong(d) & 0x000fffffffffffffll) == 0 && d > 0.0 && isfinite(d);
 }
 
+// The step's interval dt and the powers the corrector needs: 1/dt of a
+// power-of-two step from its exponent (exact), else a divide; the powers of
+// dt shared by the three components.
+struct CorrectDt {
+    double dt, idt, idt2, idt3, dt2, c3, c4, c5, dt6;
+    bool p2;
+};
+
+__device__ __forceinline__ CorrectDt correct_dt(double dt)
+{
+    CorrectDt S;
+    S.dt = dt;
+    S.p2 = is_pow2(dt);
+    S.idt = S.p2 ? __longlong_as_double((2046ll << 52) - (__double_as_longlong(dt) & 0x7ff0000000000000ll))
+                 : 1.0 / dt;
+    S.idt2 = S.idt * S.idt;
+    S.idt3 = S.idt2 * S.idt;
+    S.dt2 = dt * dt;
+    const double dt4 = S.dt2 * S.dt2;
+    S.c3 = S.dt2 * dt * (1.0 / 6.0);
+    S.c4 = dt4 * (1.0 / 24.0);
+    S.c5 = dt4 * dt * (1.0 / 120.0);
+    S.dt6 = 6.0 * dt;
+    return S;
+}
+
+// One component of the Hermite corrector: a2 and a3 (Hermite interpolation
+// of the old a0, j0 and the new a1, j1 over the step), corrected x and v.
+__device__ __forceinline__ void correct_xv(const CorrectDt &S, double a0, double j0, double a1, double j1,
+                                           double xp, double vp, double &x1, double &v1, double &a2, double &a3)
+{
+    const double da = a0 - a1;
+    a2 = fma(-S.dt, fma(4.0, j0, 2.0 * j1), -6.0 * da) * S.idt2;
+    a3 = fma(S.dt6, j0 + j1, 12.0 * da) * S.idt3;
+    x1 = fma(a3, S.c5, fma(a2, S.c4, xp));
+    v1 = fma(a3, S.c4, fma(a2, S.c3, vp));
+}
+
 // Hermite corrector of block member k (particle ilist[k], or k) at t_next
 // from its new a, jerk (acc/jerk row k), and with update_dt its new block
 // step: Aarseth's criterion quantised to a power of two that may shrink
@@ -116,24 +173,15 @@ __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, dou
                                              const double *acc, const double *jerk, double *bx, double *bv,
                                              double *ba, double *bj, double *bt, double *bdt)
 {
-    const double dt = t_next - bt[i];
-    const bool p2 = is_pow2(dt);
-    const double idt = p2 ? __longlong_as_double((2046ll << 52) - (__double_as_longlong(dt) & 0x7ff0000000000000ll))
-                          : 1.0 / dt;
-    const double idt2 = idt * idt, idt3 = idt2 * idt;
-    const double dt2 = dt * dt, dt4 = dt2 * dt2;
-    const double c3 = dt2 * dt * (1.0 / 6.0), c4 = dt4 * (1.0 / 24.0), c5 = dt4 * dt * (1.0 / 120.0);
-    const double dt6 = 6.0 * dt;
+    const CorrectDt S = correct_dt(t_next - bt[i]);
+    const double dt = S.dt, dt2 = S.dt2;
     double A = 0.0, J = 0.0, N2 = 0.0, N3 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double a0 = ba[3 * i + c], j0 = bj[3 * i + c];
         const double a1 = acc[3 * (size_t)k + c], j1 = jerk[3 * (size_t)k + c];
-        const double da = a0 - a1;
-        const double a2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da) * idt2;
-        const double a3 = fma(dt6, j0 + j1, 12.0 * da) * idt3;
-        bx[3 * i + c] = fma(a3, c5, fma(a2, c4, xp[3 * i + c]));
-        bv[3 * i + c] = fma(a3, c4, fma(a2, c3, vp[3 * i + c]));
+        double a2, a3;
+        correct_xv(S, ba[3 * i + c], bj[3 * i + c], a1, j1, xp[3 * i + c], vp[3 * i + c], bx[3 * i + c],
+                   bv[3 * i + c], a2, a3);
         ba[3 * i + c] = a1;
         bj[3 * i + c] = j1;
         const double a2e = fma(dt, a3, a2);  // a2 at the end of the step
@@ -143,6 +191,8 @@ __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, dou
         N3 = fma(a3, a3, N3);
     }
     bt[i] = t_next;
+    const bool p2 = S.p2;
+    const double idt = S.idt;
     if (update_dt) {
         const double X = eta * (sqrt(A * N2) + J), Y = sqrt(J * N3) + N2;
         double q = dt;
