@@ -214,7 +214,12 @@ int kirin_energy(kirin_ctx *ctx, const double *v, double *kin, double *pot);
  *   time is a multiple of the doubled step. */
 
 /* Evaluate a, jerk for all particles at their current state, set t_i = t and
- * dt_i = 0.01 |a| / |jerk| quantised down to a power of two in [dt_min, dt_max]. */
+ * dt_i = 0.01 |a| / |jerk| quantised down to a power of two in [dt_min, dt_max].
+ * Where kirin_hermite_shared_run would take its single-launch kernel (see
+ * there), the evaluation and the initialisation are one launch of that kernel;
+ * otherwise the force kernels and an initialisation kernel.  Errors: EINVAL
+ * (eta <= 0, dt_min <= 0, dt_max < dt_min, t not finite), ESTATE (no
+ * particles), ETIMEOUT, ENONFINITE. */
 int kirin_hermite_init(kirin_ctx *ctx, double t, double eta, double dt_min, double dt_max);
 
 /* One block step: t_next = min_i (t_i + dt_i); if t_next > t_end nothing is

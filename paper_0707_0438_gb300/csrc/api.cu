@@ -511,6 +511,83 @@ bool shared_steps_on(kirin_ctx *c)
     return c->sh_grid > 0;
 }
 
+// One launch of the shared-step kernel (shared_steps_on(c) holds): n_steps shared steps of dt from
+// t0, or with init the evaluation at t0 and the initialisation of the integrator.  Allocates the two
+// j images and the arrival counter on first use.
+int shared_launch(kirin_ctx *c, double t0, double dt, int64_t n_steps, int init, double dt_min, double dt_max)
+{
+    const int n = (int)c->n_j;
+    const int64_t n_pad = round_up(n, TILE_J);
+    if (c->sh_img_pad < n_pad) {
+        if (c->sh_img)
+            cudaFree(c->sh_img);
+        c->sh_img = nullptr;
+        c->sh_img_pad = 0;
+        if (cudaMalloc(&c->sh_img, 2 * (size_t)n_pad * sizeof(JMixed)) != cudaSuccess) {
+            c->sh_img = nullptr;
+            cudaGetLastError();
+            return set_msg(c, KIRIN_ENOMEM, "shared steps: no room for the two j images");
+        }
+        c->sh_img_pad = n_pad;
+    }
+    if (!c->sh_arrivals) {
+        if (cudaMalloc(&c->sh_arrivals, sizeof(unsigned)) != cudaSuccess) {
+            c->sh_arrivals = nullptr;
+            cudaGetLastError();
+            return set_msg(c, KIRIN_ENOMEM, "shared steps: no room for the arrival counter");
+        }
+        CK(c, cudaMemsetAsync(c->sh_arrivals, 0, sizeof(unsigned), c->stream));
+        c->sh_count = 0;
+    }
+    SharedStepArgs a{};
+    a.n = n;
+    a.n_pad = (int)n_pad;
+    a.img = c->sh_img;
+    a.arrivals = c->sh_arrivals;
+    a.arrivals0 = c->sh_count;
+    a.ctas = c->sh_grid;
+    a.m = c->bm;
+    a.x = c->bx;
+    a.v = c->bv;
+    a.a = c->ba;
+    a.jerk_b = c->bj;
+    a.t_b = c->bt;
+    a.dt_b = c->bdt;
+    a.xp = c->xp;
+    a.vp = c->vp;
+    a.f_acc = c->d_acc;
+    a.f_jerk = c->d_jerk;
+    a.f_pot = c->d_pot;
+    a.eps2 = c->eps * c->eps;
+    a.rmin2 = c->r_min * c->r_min;
+    a.G = c->G;
+    a.eta = c->eta;
+    a.dt_min = dt_min;
+    a.dt_max = dt_max;
+    a.t0 = t0;
+    a.dt = dt;
+    a.n_steps = init ? 0 : (int)n_steps;
+    a.init = init;
+    a.err = c->d_err;
+    CK(c, launch_shared_steps(a, guard_on(c), c->stream));
+    // every CTA arrives once per step (once when initialising)
+    c->sh_count += (uint32_t)c->sh_grid * (uint32_t)(init ? 1 : n_steps);
+    return KIRIN_OK;
+}
+
+// read_device_errors after a shared-step launch; after a timeout (CTAs left mid-run) the arrival
+// counter starts from zero again.
+int read_shared_errors(kirin_ctx *c)
+{
+    const int rc = read_device_errors(c);
+    if (rc == KIRIN_ETIMEOUT) {
+        CK(c, cudaMemsetAsync(c->sh_arrivals, 0, sizeof(unsigned), c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        c->sh_count = 0;
+    }
+    return rc;
+}
+
 RunKey run_key(const kirin_ctx *c, const RunPlan &p)
 {
     RunKey k;
@@ -1227,16 +1304,25 @@ int kirin_hermite_init(kirin_ctx *ctx, double t, double eta, double dt_min, doub
     DeviceGuard dg(ctx->device);
     ctx->pred_mode = 0;
     ctx->images_dirty = true;
-    int rc = ensure_images(ctx);
-    if (rc)
-        return rc;
-    const int n = (int)ctx->n_j;
-    rc = run_force(ctx, n, nullptr, n, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
-    if (rc)
-        return rc;
-    CK(ctx, launch_hermite_init(n, t, ctx->d_acc, ctx->d_jerk, dt_min, dt_max, ctx->ba, ctx->bj, ctx->bt,
-                                ctx->bdt, ctx->stream));
-    rc = read_device_errors(ctx);
+    int rc;
+    if (shared_steps_on(ctx)) {
+        // small systems: evaluation and initialisation in one launch of the shared-step kernel
+        rc = shared_launch(ctx, t, 0.0, 0, 1, dt_min, dt_max);
+        if (rc)
+            return rc;
+        rc = read_shared_errors(ctx);
+    } else {
+        rc = ensure_images(ctx);
+        if (rc)
+            return rc;
+        const int n = (int)ctx->n_j;
+        rc = run_force(ctx, n, nullptr, n, MODE_ACC_JERK_POT, ctx->d_acc, ctx->d_jerk, ctx->d_pot);
+        if (rc)
+            return rc;
+        CK(ctx, launch_hermite_init(n, t, ctx->d_acc, ctx->d_jerk, dt_min, dt_max, ctx->ba, ctx->bj, ctx->bt,
+                                    ctx->bdt, ctx->stream));
+        rc = read_device_errors(ctx);
+    }
     if (rc)
         return rc;
     ctx->eta = eta;
@@ -1356,59 +1442,9 @@ int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps)
     const int n = (int)ctx->n_j;
     if (shared_steps_on(ctx) && n_steps > 0 && n_steps <= INT32_MAX) {
         // the whole run in one cooperative launch (small systems, mixed precision)
-        const int64_t n_pad = round_up(n, TILE_J);
-        if (ctx->sh_img_pad < n_pad) {
-            if (ctx->sh_img)
-                cudaFree(ctx->sh_img);
-            ctx->sh_img = nullptr;
-            ctx->sh_img_pad = 0;
-            if (cudaMalloc(&ctx->sh_img, 2 * (size_t)n_pad * sizeof(JMixed)) != cudaSuccess) {
-                ctx->sh_img = nullptr;
-                cudaGetLastError();
-                return set_msg(ctx, KIRIN_ENOMEM, "hermite_shared_run: no room for the two j images");
-            }
-            ctx->sh_img_pad = n_pad;
-        }
-        if (!ctx->sh_arrivals) {
-            if (cudaMalloc(&ctx->sh_arrivals, sizeof(unsigned)) != cudaSuccess) {
-                ctx->sh_arrivals = nullptr;
-                cudaGetLastError();
-                return set_msg(ctx, KIRIN_ENOMEM, "hermite_shared_run: no room for the arrival counter");
-            }
-            CK(ctx, cudaMemsetAsync(ctx->sh_arrivals, 0, sizeof(unsigned), ctx->stream));
-            ctx->sh_count = 0;
-        }
-        SharedStepArgs a{};
-        a.n = n;
-        a.n_pad = (int)n_pad;
-        a.img = ctx->sh_img;
-        a.arrivals = ctx->sh_arrivals;
-        a.arrivals0 = ctx->sh_count;
-        a.ctas = ctx->sh_grid;
-        a.m = ctx->bm;
-        a.x = ctx->bx;
-        a.v = ctx->bv;
-        a.a = ctx->ba;
-        a.jerk_b = ctx->bj;
-        a.t_b = ctx->bt;
-        a.dt_b = ctx->bdt;
-        a.xp = ctx->xp;
-        a.vp = ctx->vp;
-        a.f_acc = ctx->d_acc;
-        a.f_jerk = ctx->d_jerk;
-        a.f_pot = ctx->d_pot;
-        a.eps2 = ctx->eps * ctx->eps;
-        a.rmin2 = ctx->r_min * ctx->r_min;
-        a.G = ctx->G;
-        a.eta = ctx->eta;
-        a.dt_min = ctx->dt_min;
-        a.dt_max = ctx->dt_max;
-        a.t0 = ctx->t_shared;
-        a.dt = dt;
-        a.n_steps = (int)n_steps;
-        a.err = ctx->d_err;
-        CK(ctx, launch_shared_steps(a, guard_on(ctx), ctx->stream));
-        ctx->sh_count += (uint32_t)ctx->sh_grid * (uint32_t)n_steps;  // every CTA arrives once per step
+        const int rc = shared_launch(ctx, ctx->t_shared, dt, n_steps, 0, ctx->dt_min, ctx->dt_max);
+        if (rc != KIRIN_OK)
+            return rc;
         double t = ctx->t_shared;
         for (int64_t s = 0; s < n_steps; ++s)  // the kernel's time arithmetic, step by step
             t = t + dt;
@@ -1417,13 +1453,7 @@ int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps)
         ctx->pred_t = t;
         ctx->images_dirty = true;
         ctx->pending = false;
-        const int rc = read_device_errors(ctx);
-        if (rc == KIRIN_ETIMEOUT) {  // CTAs left mid-run: the counter starts from zero again
-            CK(ctx, cudaMemsetAsync(ctx->sh_arrivals, 0, sizeof(unsigned), ctx->stream));
-            CK(ctx, cudaStreamSynchronize(ctx->stream));
-            ctx->sh_count = 0;
-        }
-        return rc;
+        return read_shared_errors(ctx);
     }
     for (int64_t s = 0; s < n_steps; ++s) {  // enqueued back to back; one synchronisation at the end
         const double t_next = ctx->t_shared + dt;

@@ -152,20 +152,6 @@ __global__ void __launch_bounds__(1024) k_energy(int n, const double *__restrict
     }
 }
 
-__device__ __forceinline__ double norm3(const double *p)
-{
-    return sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-}
-
-// Largest power of two <= d within [dt_min, dt_max].
-__device__ __forceinline__ double quantise_down(double d, double dt_min, double dt_max)
-{
-    double q = dt_max;
-    while (q > d && q > dt_min)
-        q *= 0.5;
-    return q;
-}
-
 __global__ void k_hermite_init(int n, double t, const double *acc, const double *jerk, double dt_min,
                                double dt_max, double *ba, double *bj, double *bt, double *bdt)
 {
@@ -181,7 +167,7 @@ __global__ void k_hermite_init(int n, double t, const double *acc, const double 
         bj[3 * (size_t)k + c] = j[c];
     }
     bt[k] = t;
-    bdt[k] = quantise_down(0.01 * norm3(a) / norm3(j), dt_min, dt_max);
+    bdt[k] = initial_step(a, j, dt_min, dt_max);
 }
 
 // Order-preserving map of doubles to unsigned keys (the sign bit set for

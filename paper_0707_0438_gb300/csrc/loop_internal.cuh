@@ -84,6 +84,8 @@ struct SharedStepArgs {
     double eta, dt_min, dt_max;
     double t0, dt;            // the run starts at t0 and takes n_steps steps of dt
     int n_steps;
+    int init;                 // 1: instead, evaluate at t0 and initialise (a, jerk, t, first step);
+                              // the CTAs arrive once
     int ctas;                 // CTAs of the launch (all resident: a cooperative launch)
     unsigned *err;
 };

@@ -192,12 +192,13 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
         M = A.m[kc];
     }
     __syncthreads();
-    // step 0's image: own particles predicted to t0 + dt; the last CTA writes both images' padding
+    // the first image: own particles predicted to t0 + dt (or, to initialise, as they are); the last
+    // CTA writes both images' padding
     if (comp) {
-        const PredictDt Pd = predict_dt((A.t0 + A.dt) - tb);
-        double X, V;
-        predict_xv(Pd, st[st_row(c, 0) * I_CTA + lane], st[st_row(c, 1) * I_CTA + lane],
-                   st[st_row(c, 2) * I_CTA + lane], st[st_row(c, 3) * I_CTA + lane], X, V);
+        double X = st[st_row(c, 0) * I_CTA + lane], V = st[st_row(c, 1) * I_CTA + lane];
+        if (!A.init)
+            predict_xv(predict_dt((A.t0 + A.dt) - tb), X, V, st[st_row(c, 2) * I_CTA + lane],
+                       st[st_row(c, 3) * I_CTA + lane], X, V);
         st[st_row(c, 4) * I_CTA + lane] = X;
         st[st_row(c, 5) * I_CTA + lane] = V;
         emit_component(A, A.img, c, kc, X, V, M);
@@ -211,12 +212,14 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
     }
     arrive(A.arrivals);
     double t = A.t0;
-    for (int step = 0; step < A.n_steps; ++step) {
-        const double tn = t + A.dt;
+    const int n_iter = A.init ? 1 : A.n_steps;
+    for (int step = 0; step < n_iter; ++step) {
+        const double tn = A.init ? A.t0 : t + A.dt;
         const uint32_t parity = (uint32_t)(step & 1);
         // 0. while thread 0 waits: the corrector's interval and powers (warp 1, from the particle's
         //    own time) and the predictor's for the next step (warp 2), into shared memory
-        if (warp == 1 && lane < own) {
+        if (A.init) {
+        } else if (warp == 1 && lane < own) {
             const CorrectDt S = correct_dt(tn - tb);
             const double r[7] = {S.dt, S.idt2, S.idt3, S.c3, S.c4, S.c5, S.dt6};
 #pragma unroll
@@ -327,6 +330,22 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
                 A.f_pot[p] = row;
         }
         __syncthreads();
+        // 4. initialisation: a, jerk and t of each own particle, and its first block step
+        if (A.init) {
+            if (warp == 0 && lane < own) {
+                double a0[3], j0[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    a0[q] = st[force_row(q) * I_CTA + lane];
+                    j0[q] = st[force_row(3 + q) * I_CTA + lane];
+                    A.a[3 * (size_t)kc + q] = a0[q];
+                    A.jerk_b[3 * (size_t)kc + q] = j0[q];
+                }
+                A.t_b[kc] = A.t0;
+                A.dt_b[kc] = initial_step(a0, j0, A.dt_min, A.dt_max);
+            }
+            break;
+        }
         // 4. component c of each own particle corrected (shared step: the step size stays), then
         //    predicted to the next step into the other image
         if (comp) {
@@ -454,7 +473,7 @@ cudaError_t launch_shared_steps(const SharedStepArgs &a, bool guard, cudaStream_
         a.n_steps < 0 || a.ctas < 1 || a.ctas > a.n || own_max_of(a.n, a.ctas) > SH_MAX_OWN || !a.img ||
         !a.arrivals)
         return cudaErrorInvalidValue;
-    if (a.n_steps == 0)
+    if (a.n_steps == 0 && !a.init)
         return cudaSuccess;
     const int own = own_max_of(a.n, a.ctas);
     return guard ? sh_dispatch<true>(a, own, false, nullptr, st) : sh_dispatch<false>(a, own, false, nullptr, st);

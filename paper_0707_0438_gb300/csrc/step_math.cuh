@@ -108,6 +108,27 @@ __device__ __forceinline__ void predict_one(int k, int n, double t, int predict,
     write_images(k, X[0], X[1], X[2], M, V[0], V[1], V[2], jm, jd);
 }
 
+__device__ __forceinline__ double norm3(const double *p)
+{
+    return sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+}
+
+// Largest power of two <= d within [dt_min, dt_max].
+__device__ __forceinline__ double quantise_down(double d, double dt_min, double dt_max)
+{
+    double q = dt_max;
+    while (q > d && q > dt_min)
+        q *= 0.5;
+    return q;
+}
+
+// Initial block step of a particle from its first a and jerk: 0.01 |a| / |j|
+// on the power-of-two ladder.
+__device__ __forceinline__ double initial_step(const double *a, const double *j, double dt_min, double dt_max)
+{
+    return quantise_down(0.01 * norm3(a) / norm3(j), dt_min, dt_max);
+}
+
 // Hermite corrector for the block (Sect. 3): a2, a3 from the two (a, jerk)
 // pairs, corrected x and v, and (update_dt) Aarseth's step on the
 // power-of-two ladder.

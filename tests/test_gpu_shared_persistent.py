@@ -41,6 +41,31 @@ def test_persistent_shared_run_matches_the_oracle(kirin_lib, n):
         assert np.median(metrics.rel_err_vec(after[0], ref[0])) <= 1e-6
 
 
+@pytest.mark.parametrize("n", [2, 777, 2048])
+def test_persistent_hermite_init_matches_the_oracle(kirin_lib, n):
+    """kirin_hermite_init in one launch of the shared-step kernel: the first a and jerk against the
+    oracle's, x and v untouched, t_i = t, and the initial steps 0.01 |a| / |jerk| on the power-of-two ladder
+    (the oracle's quantiser applied to the oracle's forces; a force error of 1e-6 can only move a
+    particle whose raw step sits that close to a power of two)."""
+    p = workloads.plummer(n, (2002, n), eps=1.0 / 256)
+    with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        assert k.shared_persistent_active()
+        k.hermite_init(0.25)
+        st = k.get_state()
+    ref = oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps)
+    for got, want in ((st["a"], ref[0]), (st["j"], ref[1])):
+        err = metrics.rel_err_vec(got, want)
+        assert np.median(err) <= 1e-6 and err.max() <= 1e-4
+    assert np.array_equal(st["x"], p.x) and np.array_equal(st["v"], p.v)
+    assert np.all(st["t"] == 0.25)
+    raw = 0.01 * np.linalg.norm(ref[0], axis=1) / np.linalg.norm(ref[1], axis=1)
+    want_dt = hermite.quantise_initial(raw)
+    near = np.abs(np.log2(raw) - np.round(np.log2(raw))) < 1e-5
+    assert np.array_equal(st["dt"][~near], want_dt[~near])
+    assert np.all(np.isin(st["dt"], [want_dt.min() / 2] + list(np.unique(want_dt)) + [want_dt.max() * 2]))
+
+
 @pytest.mark.parametrize("n,eps,r_min,tol", [(1024, 1.0 / 256, 0.0, 1e-10), (900, 0.0, 1e-6, 1e-8)])
 def test_persistent_shared_run_agrees_with_the_kernel_path(kirin_lib, n, eps, r_min, tol):
     """The same 64 steps through the single launch and through the predictor, force and corrector
