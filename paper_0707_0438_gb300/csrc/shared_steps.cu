@@ -32,6 +32,7 @@
 #include "loop_internal.cuh"
 #include "pair_mixed.cuh"
 #include "step_math.cuh"
+#include "grid_sync.cuh"
 #include "tma.cuh"
 
 namespace kirin {
@@ -64,65 +65,6 @@ template <int GT>
 __host__ __device__ constexpr size_t sh_smem_bytes(int n_pad)
 {
     return SH_BAR_BYTES + (size_t)n_pad * sizeof(JMixed) + sh_red_bytes<GT>() + (size_t)ST_ROWS * 2 * GT * sizeof(double);
-}
-
-__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Order this thread's earlier global accesses before later bulk copies, which read global memory
-// through the async proxy.
-__device__ __forceinline__ void fence_proxy_async_global()
-{
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-// This CTA's image records of its next step are written (the CTA barrier orders every thread's
-// stores before thread 0's release): one more arrival.
-__device__ __forceinline__ void arrive(unsigned *arrivals)
-{
-    __syncthreads();
-    if (threadIdx.x == 0)
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(arrivals) : "memory");
-}
-
-// Wait until the counter reaches target (compared modulo 2^32): thread 0 polls relaxed for at most
-// WAIT_LIMIT_NS, then one acquire load orders what the arrivals published.  False (and
-// ERR_TIMEOUT) when it never came; every thread of the CTA calls it and gets the same answer.
-__device__ __forceinline__ bool wait_arrivals(const unsigned *arrivals, unsigned target, unsigned *err)
-{
-    bool ok = true;
-    if (threadIdx.x == 0) {
-        if ((int)(ld_relaxed_gpu(arrivals) - target) < 0) {
-            const unsigned long long t0 = global_ns();
-            while ((int)(ld_relaxed_gpu(arrivals) - target) < 0)
-                if (global_ns() - t0 > WAIT_LIMIT_NS) {
-                    ok = false;
-                    break;
-                }
-        }
-        if (ok)
-            ok = (int)(ld_acquire_gpu(arrivals) - target) >= 0;  // it only grows: true, and now ordered
-    }
-    const bool failed = __syncthreads_or(!ok);
-    if (failed && threadIdx.x == 0)
-        atomicOr(err, ERR_TIMEOUT);
-    return !failed;
 }
 
 // Component c of particle k predicted to X, V: the FP64 rows x_p, v_p, and the c-parts of its j

@@ -44,20 +44,23 @@ def test_device_loop_is_bitwise_the_host_loop(kirin_lib, precision, n):
     assert dev[2] == host[2]
 
 
-def test_device_loop_fp64_follows_the_oracle_schedule(kirin_lib):
+@pytest.mark.parametrize("n,t_end", [(256, 1.0 / 8), (4096, 1.0 / 8), (8192, 1.0 / 32)])
+def test_device_loop_fp64_follows_the_oracle_schedule(kirin_lib, n, t_end):
     """Automatic shapes (a ladder of launches by block size): the oracle's block
     sequence length and pair count, its times and steps exactly, its positions
-    to FP64 rounding."""
-    p = workloads.plummer(256, 1002, eps=1e-3)
-    t_end = 1.0 / 8
+    to FP64 rounding.  N = 4096 to t = 1/8 takes 1300 block steps, N = 8192 to
+    1/32 621, with blocks from one particle to all of them."""
+    p = workloads.plummer(n, 1002, eps=1e-3)
     ref = hermite.block_steps(p.m, p.x, p.v, p.eps, t_end=t_end)
     [(steps, pairs)], st, e = _run(p, "fp64", True, [t_end])
     assert steps == len(ref["blocks"])
     assert pairs == float(sum(ref["blocks"])) * p.n
-    assert np.array_equal(st["t"], ref["t"]) and np.all(st["t"] == t_end)
+    assert np.array_equal(st["t"], ref["t"])
     assert np.array_equal(st["dt"], ref["dt"])
     assert np.abs(st["x"] - ref["x"]).max() <= 1e-9
-    assert e == pytest.approx(ref["e_end"], rel=1e-10)
+    if t_end % hermite.DT_MAX == 0:  # a multiple of the largest step: every particle ends there, and
+        assert np.all(st["t"] == t_end)  # the energy of the synchronised state is defined
+        assert e == pytest.approx(ref["e_end"], rel=1e-10)
 
 
 def test_device_loop_max_steps_and_rebuild_on_new_shape(kirin_lib):
