@@ -108,3 +108,91 @@ def test_persistent_shared_run_limits(kirin_lib):
         assert k.shared_persistent_active()
         k.set_launch(2, 4)
         assert not k.shared_persistent_active()
+
+
+def test_persistent_shared_run_guard_with_a_coincident_pair(kirin_lib):
+    """eps = 0 with the r_min guard and two particles on the same spot: the guard drops that pair, the
+    run stays finite, and the pair's other forces match the oracle's with the same guard."""
+    p = workloads.plummer(300, 3030, eps=0.0)
+    x = p.x.copy()
+    x[7] = x[3]
+    with abi.Kirin(p.n, 0.0, r_min=1e-6, precision="mixed") as k:
+        k.set_j_particles(p.m, x, p.v)
+        assert k.shared_persistent_active()
+        k.hermite_init(0.0)
+        st0 = k.get_state()
+        k.hermite_shared_run(1.0 / 4096, 8)
+        st = k.get_state()
+    for key in ("x", "v", "a", "j"):
+        assert np.all(np.isfinite(st[key])), key
+    ref = oracle.acc_jerk_pot(p.m, x, p.v, 0.0, r_min=1e-6)
+    assert np.median(metrics.rel_err_vec(st0["a"], ref[0])) <= 1e-6
+
+
+def test_persistent_contexts_of_different_sizes_interleave(kirin_lib):
+    """Contexts that take different group widths (N = 200, 1500, 2048) run alternately on one device;
+    each run equals the same run repeated alone, bit for bit."""
+    sizes = (200, 1500, 2048)
+    parts = {n: workloads.plummer(n, (5050, n), eps=1.0 / 256) for n in sizes}
+
+    def alone(n):
+        p = parts[n]
+        with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+            k.set_j_particles(p.m, p.x, p.v)
+            k.hermite_init(0.0)
+            k.hermite_shared_run(1.0 / 1024, 6)
+            return k.get_state()
+
+    ref = {n: alone(n) for n in sizes}
+    ks = {n: abi.Kirin(parts[n].n, parts[n].eps, precision="mixed") for n in sizes}
+    try:
+        for n in sizes:
+            ks[n].set_j_particles(parts[n].m, parts[n].x, parts[n].v)
+            ks[n].hermite_init(0.0)
+        for _ in range(2):
+            for n in sizes:
+                ks[n].hermite_shared_run(1.0 / 1024, 3)
+        for n in sizes:
+            st = ks[n].get_state()
+            for key in ("x", "v", "a", "j", "t"):
+                assert np.array_equal(st[key], ref[n][key]), (n, key)
+    finally:
+        for k in ks.values():
+            k.close()
+
+
+def test_persistent_shared_run_from_a_negative_time(kirin_lib):
+    """The kernel's step times are the host's sequential sums t0 + dt + dt + ..., from any start."""
+    p = workloads.plummer(512, 6060, eps=1.0 / 256)
+    t0, dt, steps = -0.3, 1.0 / 1000, 7
+    with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(t0)
+        k.hermite_shared_run(dt, steps)
+        st = k.get_state()
+    t = t0
+    for _ in range(steps):
+        t = t + dt
+    assert np.all(st["t"] == t)
+    xr, vr, _, _, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, dt, steps)
+    assert np.abs(st["x"] - xr).max() <= 1e-7 * np.abs(p.x).max()
+
+
+def test_switching_paths_mid_run_continues_the_state(kirin_lib):
+    """Five steps in the single launch, then five through the step kernels, against ten through the
+    step kernels: the same state to rounding (each path leaves what the other continues from)."""
+    p = workloads.plummer(1024, 7070, eps=1.0 / 256)
+    dt = 1.0 / 1024
+    out = []
+    for first in (True, False):
+        with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+            k.set_shared_persistent(first)
+            k.set_j_particles(p.m, p.x, p.v)
+            k.hermite_init(0.0)
+            k.hermite_shared_run(dt, 5)
+            k.set_shared_persistent(False)
+            k.hermite_shared_run(dt, 5)
+            out.append(k.get_state())
+    assert np.all(out[0]["t"] == out[1]["t"])
+    assert np.abs(out[0]["x"] - out[1]["x"]).max() <= 1e-10 * np.abs(p.x).max()
+    assert np.median(metrics.rel_err_vec(out[0]["a"], out[1]["a"])) <= 1e-6
