@@ -26,13 +26,16 @@
 //    by record (consecutive 80-byte records fall on disjoint banks); partial
 //    sums folded in double-single, the groups of a warp combined by shuffles
 //    and the warps in warp order.
+// With init set, the launch instead evaluates the particles as they are at t0
+// and initialises the integrator (a, jerk, t and the first block step, the
+// initialisation kernel's arithmetic): one launch for kirin_hermite_init.
 #include <cuda_runtime.h>
 
 #include "kirin_internal.cuh"
 #include "loop_internal.cuh"
 #include "pair_mixed.cuh"
-#include "step_math.cuh"
 #include "grid_sync.cuh"
+#include "step_math.cuh"
 #include "tma.cuh"
 
 namespace kirin {
