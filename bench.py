@@ -155,6 +155,19 @@ def _fp32_peak_tflops(nsm: int, mhz: float) -> float:
     return nsm * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def _sub_roofline(rate, k, note, device=0):
+    """Roofline of a secondary workload: its pair rate x k flops per pair against the FP32 CUDA-core
+    peak (the headline's denominator), over the whole run it reports."""
+    import torch
+    props = torch.cuda.get_device_properties(device)
+    peaks, src = _peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = _fp32_peak_tflops(props.multi_processor_count, f_max)
+    achieved = k * rate / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_note": f"FP32 CUDA-core peak at {f_max:.0f} MHz ({src}); k={k} flops per pair: {note}"}
+
+
 def _time_oracle_sample(p, k_i, seed):
     import oracle
     il = _subset(p.n, k_i, seed)
@@ -551,7 +564,8 @@ def measure_small(steps, warmup, device=0):
                                      "x_after_10_steps_rel_diff": _rel_diff(st["x"], x_ref),
                                      "v_after_10_steps_rel_diff": _rel_diff(st["v"], v_ref)}}
     m = res["mixed"]
-    return dict(m, unit=UNIT, workload=SMALL_WORKLOAD, fp64=res["fp64"])
+    roof = _sub_roofline(m["value"], 60, "acc+jerk+pot (Eq. 3), init and steps included", device)
+    return dict(m, unit=UNIT, workload=SMALL_WORKLOAD, fp64=res["fp64"], roofline=roof)
 
 
 def run_small(args):
@@ -639,6 +653,8 @@ def measure_block(n=65536, t_end=0.125, fp64_t_end=0.125, host_loop=True, histog
         total = sum(h[1] for h in hist.values())
         res["n_active_histogram"] = {str(b): {"steps": h[0], "pair_share": round(h[1] / total, 4)}
                                      for b, h in sorted(hist.items())}
+    res["roofline"] = _sub_roofline(res["value"], 60, "acc+jerk+pot (Eq. 3), over the whole run with its "
+                                    "predictor, scheduler and corrector", device)
     return res
 
 
@@ -717,6 +733,7 @@ def measure_ensemble(runs=3, no_graph=True, device=0):
                       "timed_ms_per_step": {f"{e[0]}x{e[1]}": round(1e3 * e[2], 3) for e in tuned[2]}}}
     if "no_graph" in res:
         out["no_graph"] = res["no_graph"]
+    out["roofline"] = _sub_roofline(g["value"], 38, "acc+pot (Eq. 3 without the jerk)", device)
     return out
 
 
@@ -790,9 +807,12 @@ def measure_adjoint(steps, warmup, device=0):
             "max_over_rms": float(f"{err.max() / np.sqrt(np.mean(np.sum(ref * ref, axis=1))):.3g}")}
     # force evaluations: 65 forward, 64 recomputed, 65 adjoint (one per distinct position)
     evals = 65 + 64 + 65
+    rate = evals * float(n) * n / t
     return {"value": t, "unit": "s", "ms_per_forward_backward": 1e3 * t, "runs": steps,
-            "pair_evaluations_per_s": evals * float(n) * n / t, "loss": float(loss.item()),
-            "clocks": clk.summary(), "workload": ADJOINT_WORKLOAD, "parity": parity}
+            "pair_evaluations_per_s": rate, "loss": float(loss.item()),
+            "clocks": clk.summary(), "workload": ADJOINT_WORKLOAD, "parity": parity,
+            "roofline": _sub_roofline(rate, 38, "every pair evaluation counted as acc+pot, a floor (an adjoint "
+                                      "pair costs about twice a force-only one)", device)}
 
 
 def run_adjoint(args):

@@ -52,6 +52,9 @@ def test_native_line_contract(kirin_lib):
         sub = line[name]
         assert "error" not in sub, (name, sub)
         assert sub["value"] > 0 and sub["clocks"]["sm_max_mhz"] > 0 and sub["parity"], name
+        sr = sub["roofline"]
+        assert sr["bound"] == "alu" and sr["unit"] == "TFLOP/s" and 0 < sr["frac"] < 1.2, name
+        assert sr["achieved"] == pytest.approx(sr["frac"] * sr["peak"]), name
     blk = line["block"]
     assert blk["t_end"] == 0.125 and blk["fp64"]["t_end"] == 0.125 and blk["block_steps"] > 1000
     assert blk["parity"]["x_final_device_vs_host_loop_rel_diff"] < 1e-6
