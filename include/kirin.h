@@ -264,16 +264,17 @@ int kirin_hermite_shared_step(kirin_ctx *ctx, double dt);
  * (no fixed launch shape, no j partition) runs the whole call in one
  * cooperative launch, one CTA per SM: each CTA owns a slice of the particles,
  * corrects it with the step kernels' corrector and predicts it with their
- * FP64 predictor into a global j image (two images, for even and odd steps);
- * after one bounded grid barrier per step every CTA copies the image into its
- * shared memory and sums its slice's acc, jerk and pot against all j with the
- * force kernels' pair arithmetic.  Otherwise the steps are the predictor,
+ * FP64 predictor into a global j image (two images, for even and odd steps)
+ * and counts its arrival on a counter that only grows; once every CTA has
+ * arrived for the step (a bounded wait) each copies the image into its shared
+ * memory and sums its slice's acc, jerk and pot against all j with the force
+ * kernels' pair arithmetic.  Otherwise the steps are the predictor,
  * force and corrector kernels enqueued back to back, the same kernels and
  * results as n_steps calls of kirin_hermite_shared_step.  The two paths sum
  * the j in different orders, so they agree to rounding; each gives the same
  * bits on every call.  kirin_hermite_shared_step is this call with one step.
  * Errors: EINVAL (dt <= 0, n_steps < 0), ESTATE before kirin_hermite_init,
- * ENOMEM (the two images), ETIMEOUT (a grid barrier or copy wait gave up). */
+ * ENOMEM (the two images), ETIMEOUT (an arrival or copy wait gave up). */
 int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps);
 
 /* kirin_set_shared_persistent: enable != 0 (default) lets
