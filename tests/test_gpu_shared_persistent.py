@@ -94,7 +94,8 @@ def test_persistent_shared_run_is_deterministic(kirin_lib):
 
 
 def test_persistent_shared_run_limits(kirin_lib):
-    """Above 2048 particles, in FP64 and under a fixed launch shape the per-kernel path runs."""
+    """Above 2048 particles, in FP64 and under a fixed launch shape the per-kernel path runs; a run of
+    no steps changes nothing."""
     p = workloads.plummer(2049, 1, eps=0.01)
     with abi.Kirin(p.n, p.eps, precision="mixed") as k:
         k.set_j_particles(p.m, p.x, p.v)
@@ -106,6 +107,12 @@ def test_persistent_shared_run_limits(kirin_lib):
     with abi.Kirin(q.n, q.eps, precision="mixed") as k:
         k.set_j_particles(q.m, q.x, q.v)
         assert k.shared_persistent_active()
+        k.hermite_init(0.0)
+        before = k.get_state()
+        k.hermite_shared_run(1.0 / 1024, 0)  # no steps: nothing changes
+        after = k.get_state()
+        for key in ("x", "v", "a", "j", "t", "dt"):
+            assert np.array_equal(before[key], after[key]), key
         k.set_launch(2, 4)
         assert not k.shared_persistent_active()
 
