@@ -305,6 +305,13 @@ int kirin_set_state(kirin_ctx *ctx, int64_t n, const double *m, const double *x,
  * No counterpart in the paper. */
 int kirin_selftest_wait_timeout(kirin_ctx *ctx, int64_t limit_ns);
 
+/* Failure-path self-test of the waits between CTAs of the single-launch shared
+ * steps: one CTA waits for an arrival on a counter that nothing increments,
+ * with a wait limit of limit_ns, exactly as a CTA waits for the others' step;
+ * it returns KIRIN_ETIMEOUT (the context stays usable).  Errors: EINVAL
+ * (NULL, limit_ns < 0).  No counterpart in the paper. */
+int kirin_selftest_arrival_timeout(kirin_ctx *ctx, int64_t limit_ns);
+
 /* ---- accelerations of device particle sets (leapfrog clients, Sect. 4.3) ----
  * Acceleration (and optionally potential) of all n particles of (m, x), every
  * particle against every other, without jerk: the force-only evaluation the

@@ -90,6 +90,7 @@ _SIGS = {
     "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
     "kirin_set_state": (ctypes.c_int, [_P, _I64, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _D, _D, _D]),
     "kirin_selftest_wait_timeout": (ctypes.c_int, [_P, _I64]),
+    "kirin_selftest_arrival_timeout": (ctypes.c_int, [_P, _I64]),
     "kirin_accel_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P]),
     "kirin_accel_adjoint_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
     "kirin_leapfrog_dev": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _D, _I32, _I32, _P]),
@@ -436,6 +437,10 @@ class Kirin:
     def selftest_wait_timeout(self, limit_ns=1_000_000):
         """Run the bounded-wait self-test; returns the library's return code (KIRIN_ETIMEOUT expected)."""
         return self.lib.kirin_selftest_wait_timeout(self.ctx, int(limit_ns))
+
+    def selftest_arrival_timeout(self, limit_ns=1_000_000):
+        """Device wait for an arrival that never comes: returns KIRIN_ETIMEOUT (not an exception)."""
+        return self.lib.kirin_selftest_arrival_timeout(self.ctx, int(limit_ns))
 
     # -- device particle sets
     def accel_dev(self, m, x, acc, pot=None):

@@ -1530,6 +1530,15 @@ int kirin_selftest_wait_timeout(kirin_ctx *ctx, int64_t limit_ns)
     return read_device_errors(ctx);
 }
 
+int kirin_selftest_arrival_timeout(kirin_ctx *ctx, int64_t limit_ns)
+{
+    if (!ctx || limit_ns < 0)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    CK(ctx, launch_arrival_selftest((unsigned long long)limit_ns, ctx->d_err, ctx->stream));
+    return read_device_errors(ctx);
+}
+
 // ---- device particle sets -------------------------------------------------------
 
 int kirin_accel_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x, double *acc, double *pot)

@@ -43,16 +43,17 @@ __device__ __forceinline__ void arrive(unsigned *arrivals)
 }
 
 // Wait until the counter reaches target (compared modulo 2^32): thread 0 polls relaxed for at most
-// WAIT_LIMIT_NS, then one acquire load orders what the arrivals published.  False (and
-// ERR_TIMEOUT) when it never came; every thread of the CTA calls it and gets the same answer.
-__device__ __forceinline__ bool wait_arrivals(const unsigned *arrivals, unsigned target, unsigned *err)
+// limit_ns, then one acquire load orders what the arrivals published.  False (and ERR_TIMEOUT)
+// when it never came; every thread of the CTA calls it and gets the same answer.
+__device__ __forceinline__ bool wait_arrivals(const unsigned *arrivals, unsigned target, unsigned *err,
+                                              unsigned long long limit_ns = WAIT_LIMIT_NS)
 {
     bool ok = true;
     if (threadIdx.x == 0) {
         if ((int)(ld_relaxed_gpu(arrivals) - target) < 0) {
             const unsigned long long t0 = global_ns();
             while ((int)(ld_relaxed_gpu(arrivals) - target) < 0)
-                if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                if (global_ns() - t0 > limit_ns) {
                     ok = false;
                     break;
                 }

@@ -93,5 +93,7 @@ struct SharedStepArgs {
 // when the kernel does not fit.
 int shared_steps_grid(int n, bool guard);
 cudaError_t launch_shared_steps(const SharedStepArgs &a, bool guard, cudaStream_t st);
+// One CTA waits for an arrival that never comes, giving up after limit_ns (sets ERR_TIMEOUT).
+cudaError_t launch_arrival_selftest(unsigned long long limit_ns, unsigned *err, cudaStream_t st);
 
 }  // namespace kirin

@@ -336,6 +336,15 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
     }
 }
 
+// Self-test of the bounded arrival wait: one CTA waits for an arrival on a word that nothing
+// increments and gives up after limit_ns, as a shared-step CTA does when another never arrives.
+__device__ unsigned g_never_arrives = 0u;
+
+__global__ void k_arrival_selftest(unsigned long long limit_ns, unsigned *err)
+{
+    wait_arrivals(&g_never_arrives, 1u, err, limit_ns);
+}
+
 template <int GT, bool GUARD>
 cudaError_t sh_launch(const SharedStepArgs &a, bool query_only, int *grid, cudaStream_t st)
 {
@@ -410,6 +419,12 @@ int shared_steps_grid(int n, bool guard)
         return 0;
     }
     return grid;
+}
+
+cudaError_t launch_arrival_selftest(unsigned long long limit_ns, unsigned *err, cudaStream_t st)
+{
+    k_arrival_selftest<<<1, 64, 0, st>>>(limit_ns, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_shared_steps(const SharedStepArgs &a, bool guard, cudaStream_t st)

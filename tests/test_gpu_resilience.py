@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import hermite
 from paper_0707_0438_gb300 import abi, workloads
 from tests.gpu_util import assert_parity
 
@@ -40,6 +41,22 @@ def test_bounded_wait_times_out_and_context_survives(kirin_lib):
         got = k.forces()
         assert_parity(got, oracle.acc_jerk_pot(p.m, p.x, p.v, p.eps), "mixed")
         k.sync()  # the error flag was cleared when it was reported
+
+
+def test_arrival_wait_times_out_and_shared_run_continues(kirin_lib):
+    """The waits between the CTAs of the single-launch shared steps are bounded: a wait for an
+    arrival that never comes gives up (2 ms limit) with KIRIN_ETIMEOUT, and the same context then
+    runs shared steps in one launch that match the oracle."""
+    p = workloads.plummer(256, 5, eps=1.0 / 256)
+    with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+        assert k.selftest_arrival_timeout(2_000_000) == abi.KIRIN_ETIMEOUT
+        k.set_j_particles(p.m, p.x, p.v)
+        assert k.shared_persistent_active()
+        k.hermite_init(0.0)
+        k.hermite_shared_run(1.0 / 1024, 4)
+        st = k.get_state()
+    xr, _, _, _, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, 1.0 / 1024, 4)
+    assert np.abs(st["x"] - xr).max() <= 1e-7 * np.abs(p.x).max()
 
 
 def test_contexts_and_batches_release_device_memory(kirin_lib):
