@@ -203,3 +203,20 @@ def test_switching_paths_mid_run_continues_the_state(kirin_lib):
     assert np.all(out[0]["t"] == out[1]["t"])
     assert np.abs(out[0]["x"] - out[1]["x"]).max() <= 1e-10 * np.abs(p.x).max()
     assert np.median(metrics.rel_err_vec(out[0]["a"], out[1]["a"])) <= 1e-6
+
+
+def test_persistent_shared_run_lognormal_masses_small_softening(kirin_lib):
+    """Unequal (log-normal, sigma 0.5) masses and a small softening eps = 4/N: the single launch follows
+    the oracle's Hermite steps, and its final forces match the oracle's at the final state."""
+    n = 1500
+    p = workloads.plummer(n, 8080, masses="lognormal", sigma=0.5, eps=4.0 / n)
+    dt, steps = 1.0 / 2048, 8
+    xr, vr, _, _, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, dt, steps)
+    active, st, after = _run(p, p.eps, dt, steps, True)
+    assert active
+    assert np.abs(st["x"] - xr).max() <= 1e-7 * np.abs(p.x).max()
+    assert np.abs(st["v"] - vr).max() <= 1e-6 * np.abs(p.v).max()
+    ref = oracle.acc_jerk_pot(p.m, st["x"], st["v"], p.eps)
+    for got, want in ((after[0], ref[0]), (after[1], ref[1])):
+        err = metrics.rel_err_vec(got, want)
+        assert np.median(err) <= 1e-6 and err.max() <= 1e-4
