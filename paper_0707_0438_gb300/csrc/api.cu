@@ -70,6 +70,9 @@ struct kirin_ctx {
     double *h_scal = nullptr;  // pinned mirrors
     int32_t *h_count = nullptr;
     unsigned *h_err = nullptr;
+    // a host word the single-launch kernels report their errors to directly (mapped pinned memory:
+    // read after the stream synchronises, no copy), or null where mapping is unavailable
+    unsigned *h_err_map = nullptr, *d_err_map = nullptr;
 
     bool pending = false;
     int64_t pending_n = 0;
@@ -382,14 +385,11 @@ int run_force(kirin_ctx *c, int64_t n_i, const int32_t *d_ilist, int n_j, int mo
     return KIRIN_OK;
 }
 
-int read_device_errors(kirin_ctx *c)
+// The return code of a set of device error bits.
+int error_code(kirin_ctx *c, unsigned e)
 {
-    CK(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    const unsigned e = *c->h_err;
     if (e == 0)
         return KIRIN_OK;
-    CK(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
     if (e & (ERR_TIMEOUT | ERR_DRAIN))
         return set_msg(c, KIRIN_ETIMEOUT, "a bounded device wait gave up (flags 0x%x)", e);
     if (e & ERR_NONFINITE)
@@ -399,6 +399,17 @@ int read_device_errors(kirin_ctx *c)
     if (e & ERR_INDEX)
         return set_msg(c, KIRIN_EINVAL, "i index outside [0, n_j) on the device");
     return set_msg(c, KIRIN_ECUDA, "device error flags 0x%x", e);
+}
+
+int read_device_errors(kirin_ctx *c)
+{
+    CK(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const unsigned e = *c->h_err;
+    if (e == 0)
+        return KIRIN_OK;
+    CK(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+    return error_code(c, e);
 }
 
 bool all_finite(const double *p, int64_t n)
@@ -426,6 +437,8 @@ void free_all(kirin_ctx *c)
         cudaFreeHost(c->h_count);
     if (c->h_err)
         cudaFreeHost(c->h_err);
+    if (c->h_err_map)
+        cudaFreeHost(c->h_err_map);
     if (c->h_run)
         cudaFreeHost(c->h_run);
     if (c->d_run)
@@ -568,19 +581,32 @@ int shared_launch(kirin_ctx *c, double t0, double dt, int64_t n_steps, int init,
     a.dt = dt;
     a.n_steps = init ? 0 : (int)n_steps;
     a.init = init;
-    a.err = c->d_err;
+    a.err = c->d_err_map ? c->d_err_map : c->d_err;
     CK(c, launch_shared_steps(a, guard_on(c), c->stream));
     // every CTA arrives once per step (once when initialising)
     c->sh_count += (uint32_t)c->sh_grid * (uint32_t)(init ? 1 : n_steps);
     return KIRIN_OK;
 }
 
-// read_device_errors after a shared-step launch; after a timeout (CTAs left mid-run) the arrival
-// counter starts from zero again.
+// The errors of a shared-step launch: from the mapped host word once the stream has synchronised (no
+// copy), else as read_device_errors; after a timeout (CTAs left mid-run) the arrival counter starts
+// from zero again.
+int read_mapped_errors(kirin_ctx *c)
+{
+    if (!c->h_err_map)
+        return read_device_errors(c);
+    CK(c, cudaStreamSynchronize(c->stream));
+    volatile unsigned *w = c->h_err_map;
+    const unsigned e = *w;
+    if (e)
+        *w = 0u;  // written before the next launch, which therefore sees it
+    return error_code(c, e);
+}
+
 int read_shared_errors(kirin_ctx *c)
 {
-    const int rc = read_device_errors(c);
-    if (rc == KIRIN_ETIMEOUT) {
+    const int rc = read_mapped_errors(c);
+    if (rc == KIRIN_ETIMEOUT && c->sh_arrivals) {
         CK(c, cudaMemsetAsync(c->sh_arrivals, 0, sizeof(unsigned), c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
         c->sh_count = 0;
@@ -865,6 +891,20 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
         ok = false;
     if (ok && cudaMallocHost((void **)&c->h_err, sizeof(unsigned)) != cudaSuccess)
         ok = false;
+    int host_atomics = 0;  // the kernels' atomicOr on the mapped word needs native host atomics
+    cudaDeviceGetAttribute(&host_atomics, cudaDevAttrHostNativeAtomicSupported, c->device);
+    if (ok && host_atomics) {  // optional: without it the single-launch kernels report through d_err
+        if (cudaHostAlloc((void **)&c->h_err_map, sizeof(unsigned), cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer((void **)&c->d_err_map, c->h_err_map, 0) == cudaSuccess) {
+            *(volatile unsigned *)c->h_err_map = 0u;
+        } else {
+            cudaGetLastError();
+            if (c->h_err_map)
+                cudaFreeHost(c->h_err_map);
+            c->h_err_map = nullptr;
+            c->d_err_map = nullptr;
+        }
+    }
     dalloc((void **)&c->d_run, sizeof(RunState));
     if (ok && cudaMallocHost((void **)&c->h_run, sizeof(RunState)) != cudaSuccess)
         ok = false;
@@ -1535,8 +1575,10 @@ int kirin_selftest_arrival_timeout(kirin_ctx *ctx, int64_t limit_ns)
     if (!ctx || limit_ns < 0)
         return KIRIN_EINVAL;
     DeviceGuard dg(ctx->device);
-    CK(ctx, launch_arrival_selftest((unsigned long long)limit_ns, ctx->d_err, ctx->stream));
-    return read_device_errors(ctx);
+    // reported the way the shared-step launches report (the mapped host word where there is one)
+    CK(ctx, launch_arrival_selftest((unsigned long long)limit_ns, ctx->d_err_map ? ctx->d_err_map : ctx->d_err,
+                                    ctx->stream));
+    return read_mapped_errors(ctx);
 }
 
 // ---- device particle sets -------------------------------------------------------

@@ -220,3 +220,25 @@ def test_persistent_shared_run_lognormal_masses_small_softening(kirin_lib):
     for got, want in ((after[0], ref[0]), (after[1], ref[1])):
         err = metrics.rel_err_vec(got, want)
         assert np.median(err) <= 1e-6 and err.max() <= 1e-4
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_shared_run_reports_a_non_finite_state_and_recovers(kirin_lib, persistent):
+    """A step so large that the predictor overflows (dt = 1e300) is reported as KIRIN_ENONFINITE by both
+    paths (the single launch reports through its own error word), and the error is cleared: the same
+    context then runs correctly from fresh particles."""
+    p = workloads.plummer(512, 9090, eps=1.0 / 256)
+    with abi.Kirin(p.n, p.eps, precision="mixed") as k:
+        k.set_shared_persistent(persistent)
+        k.set_j_particles(p.m, p.x, p.v)
+        assert k.shared_persistent_active() == persistent
+        k.hermite_init(0.0)
+        with pytest.raises(abi.KirinError) as exc:
+            k.hermite_shared_run(1e300, 1)
+        assert exc.value.code == abi.KIRIN_ENONFINITE
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        k.hermite_shared_run(1.0 / 1024, 3)
+        st = k.get_state()
+    xr, _, _, _, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, 1.0 / 1024, 3)
+    assert np.abs(st["x"] - xr).max() <= 1e-7 * np.abs(p.x).max()
