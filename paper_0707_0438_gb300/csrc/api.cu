@@ -70,8 +70,8 @@ struct kirin_ctx {
     double *h_scal = nullptr;  // pinned mirrors
     int32_t *h_count = nullptr;
     unsigned *h_err = nullptr;
-    // a host word the single-launch kernels report their errors to directly (mapped pinned memory:
-    // read after the stream synchronises, no copy), or null where mapping is unavailable
+    // a host word the kernels report their errors to directly (mapped pinned memory: read after the
+    // stream synchronises, no copy), or null where mapping is unavailable (then d_err)
     unsigned *h_err_map = nullptr, *d_err_map = nullptr;
 
     bool pending = false;
@@ -284,13 +284,17 @@ int ensure_partial(kirin_ctx *c, size_t doubles)
     return KIRIN_OK;
 }
 
+// The word the context's kernels report errors to: the mapped host word where there is one (read
+// after a synchronisation without a copy), else a device word copied back.
+unsigned *err_word(const kirin_ctx *c) { return c->d_err_map ? c->d_err_map : c->d_err; }
+
 int ensure_images(kirin_ctx *c)
 {
     if (!c->images_dirty)
         return KIRIN_OK;
     const int64_t n_pad = round_up(std::max<int64_t>(c->n_j, 1), TILE_J);
     CK(c, launch_predict_pack((int)c->n_j, (int)n_pad, c->pred_t, c->pred_mode, c->bm, c->bx, c->bv,
-                              c->ba, c->bj, c->bt, c->xp, c->vp, img_m(c), img_d(c), c->d_err, c->stream));
+                              c->ba, c->bj, c->bt, c->xp, c->vp, img_m(c), img_d(c), err_word(c), c->stream));
     c->images_dirty = false;
     return KIRIN_OK;
 }
@@ -323,7 +327,7 @@ int enqueue_force(kirin_ctx *c, cudaStream_t st, Shape s, int64_t n_i, const int
     a.jerk = jerk;
     a.pot = pot;
     a.accumulate = accumulate;
-    a.err = c->d_err;
+    a.err = err_word(c);
     a.nn = nn;
     a.nn_r2 = nn_r2;
     a.nq = mode == MODE_NN ? 9 : 7;
@@ -401,8 +405,17 @@ int error_code(kirin_ctx *c, unsigned e)
     return set_msg(c, KIRIN_ECUDA, "device error flags 0x%x", e);
 }
 
+// Synchronise the stream and report (and clear) the kernels' error bits.
 int read_device_errors(kirin_ctx *c)
 {
+    if (c->h_err_map) {
+        CK(c, cudaStreamSynchronize(c->stream));
+        volatile unsigned *w = c->h_err_map;
+        const unsigned e = *w;
+        if (e)
+            *w = 0u;  // written before the next launch, which therefore sees it
+        return error_code(c, e);
+    }
     CK(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     const unsigned e = *c->h_err;
@@ -581,31 +594,18 @@ int shared_launch(kirin_ctx *c, double t0, double dt, int64_t n_steps, int init,
     a.dt = dt;
     a.n_steps = init ? 0 : (int)n_steps;
     a.init = init;
-    a.err = c->d_err_map ? c->d_err_map : c->d_err;
+    a.err = err_word(c);
     CK(c, launch_shared_steps(a, guard_on(c), c->stream));
     // every CTA arrives once per step (once when initialising)
     c->sh_count += (uint32_t)c->sh_grid * (uint32_t)(init ? 1 : n_steps);
     return KIRIN_OK;
 }
 
-// The errors of a shared-step launch: from the mapped host word once the stream has synchronised (no
-// copy), else as read_device_errors; after a timeout (CTAs left mid-run) the arrival counter starts
-// from zero again.
-int read_mapped_errors(kirin_ctx *c)
-{
-    if (!c->h_err_map)
-        return read_device_errors(c);
-    CK(c, cudaStreamSynchronize(c->stream));
-    volatile unsigned *w = c->h_err_map;
-    const unsigned e = *w;
-    if (e)
-        *w = 0u;  // written before the next launch, which therefore sees it
-    return error_code(c, e);
-}
-
+// The errors of a shared-step launch (read_device_errors); after a timeout (CTAs left mid-run) the
+// arrival counter starts from zero again.
 int read_shared_errors(kirin_ctx *c)
 {
-    const int rc = read_mapped_errors(c);
+    const int rc = read_device_errors(c);
     if (rc == KIRIN_ETIMEOUT && c->sh_arrivals) {
         CK(c, cudaMemsetAsync(c->sh_arrivals, 0, sizeof(unsigned), c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
@@ -692,7 +692,7 @@ int build_run_graph(kirin_ctx *c, const RunPlan &p, cudaGraphExec_t *exec_out)
     a.run = c->d_run;
     a.count_out = c->d_count;
     a.t_next_out = c->d_scal;
-    a.err = c->d_err;
+    a.err = err_word(c);
     a.loop = h_loop;
     a.n_classes = p.n_classes;
     for (int q = 0; q < p.n_classes; ++q)
@@ -893,7 +893,7 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
         ok = false;
     int host_atomics = 0;  // the kernels' atomicOr on the mapped word needs native host atomics
     cudaDeviceGetAttribute(&host_atomics, cudaDevAttrHostNativeAtomicSupported, c->device);
-    if (ok && host_atomics) {  // optional: without it the single-launch kernels report through d_err
+    if (ok && host_atomics) {  // optional: without it the kernels report through d_err
         if (cudaHostAlloc((void **)&c->h_err_map, sizeof(unsigned), cudaHostAllocMapped) == cudaSuccess &&
             cudaHostGetDevicePointer((void **)&c->d_err_map, c->h_err_map, 0) == cudaSuccess) {
             *(volatile unsigned *)c->h_err_map = 0u;
@@ -1093,7 +1093,7 @@ int kirin_set_j_particles_dev(kirin_ctx *ctx, int64_t first, int64_t n, const do
         return KIRIN_OK;
     DeviceGuard dg(ctx->device);
     CK(ctx, launch_scatter_state((int)first, (int)n, m, x, v, a, jerk, t0, ctx->bm, ctx->bx, ctx->bv,
-                                 ctx->ba, ctx->bj, ctx->bt, ctx->d_err, ctx->stream));
+                                 ctx->ba, ctx->bj, ctx->bt, err_word(ctx), ctx->stream));
     ctx->n_hi = std::max(ctx->n_hi, first + n);
     ctx->n_j = std::max(ctx->n_j, first + n);
     ctx->pred_mode = 0;
@@ -1566,7 +1566,7 @@ int kirin_selftest_wait_timeout(kirin_ctx *ctx, int64_t limit_ns)
     if (!ctx || limit_ns < 0)
         return KIRIN_EINVAL;
     DeviceGuard dg(ctx->device);
-    CK(ctx, launch_wait_selftest((unsigned long long)limit_ns, ctx->d_err, ctx->stream));
+    CK(ctx, launch_wait_selftest((unsigned long long)limit_ns, err_word(ctx), ctx->stream));
     return read_device_errors(ctx);
 }
 
@@ -1575,10 +1575,8 @@ int kirin_selftest_arrival_timeout(kirin_ctx *ctx, int64_t limit_ns)
     if (!ctx || limit_ns < 0)
         return KIRIN_EINVAL;
     DeviceGuard dg(ctx->device);
-    // reported the way the shared-step launches report (the mapped host word where there is one)
-    CK(ctx, launch_arrival_selftest((unsigned long long)limit_ns, ctx->d_err_map ? ctx->d_err_map : ctx->d_err,
-                                    ctx->stream));
-    return read_mapped_errors(ctx);
+    CK(ctx, launch_arrival_selftest((unsigned long long)limit_ns, err_word(ctx), ctx->stream));
+    return read_device_errors(ctx);
 }
 
 // ---- device particle sets -------------------------------------------------------
@@ -1591,7 +1589,7 @@ int kirin_accel_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x,
         return KIRIN_OK;
     DeviceGuard dg(ctx->device);
     const int64_t n_pad = round_up(n, TILE_J);
-    CK(ctx, launch_pack_xm((int)n, (int)n_pad, m, x, img_m(ctx), img_d(ctx), ctx->d_err, ctx->stream));
+    CK(ctx, launch_pack_xm((int)n, (int)n_pad, m, x, img_m(ctx), img_d(ctx), err_word(ctx), ctx->stream));
     ctx->images_dirty = true;  // the images no longer show the context's particles
     return run_force(ctx, n, nullptr, (int)n, MODE_ACC_POT, acc, nullptr, pot);
 }
@@ -1607,7 +1605,7 @@ int kirin_accel_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const do
     const int64_t n_pad = round_up(n, TILE_J);
     // images of (x, m) with g in the velocity slots
     CK(ctx, launch_predict_pack((int)n, (int)n_pad, 0.0, 0, m, x, g, nullptr, nullptr, nullptr, nullptr,
-                                nullptr, img_m(ctx), img_d(ctx), ctx->d_err, ctx->stream));
+                                nullptr, img_m(ctx), img_d(ctx), err_word(ctx), ctx->stream));
     ctx->images_dirty = true;
     return run_force(ctx, n, nullptr, (int)n, MODE_ADJOINT, nullptr, gx, gm);
 }
@@ -1626,7 +1624,7 @@ int kirin_leapfrog_dev(kirin_ctx *ctx, int64_t n, const double *m, double *x, do
     const int64_t n_pad = round_up(n, TILE_J);
     const double h = 0.5 * dt;
     auto accel = [&]() -> int {
-        CK(ctx, launch_pack_xm(nn, (int)n_pad, m, x, img_m(ctx), img_d(ctx), ctx->d_err, ctx->stream));
+        CK(ctx, launch_pack_xm(nn, (int)n_pad, m, x, img_m(ctx), img_d(ctx), err_word(ctx), ctx->stream));
         return run_force(ctx, n, nullptr, nn, MODE_ACC_POT, acc, nullptr, nullptr);
     };
     ctx->images_dirty = true;
@@ -1663,7 +1661,7 @@ int kirin_leapfrog_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const
     ctx->images_dirty = true;
     // lx += J(x)^T (c lv), lm += M(x)^T (c lv)
     auto adjoint_at = [&](const double *xk, double c) -> int {
-        CK(ctx, launch_pack_adjoint(nn, (int)n_pad, m, xk, lv, c, img_m(ctx), img_d(ctx), ctx->d_err, ctx->stream));
+        CK(ctx, launch_pack_adjoint(nn, (int)n_pad, m, xk, lv, c, img_m(ctx), img_d(ctx), err_word(ctx), ctx->stream));
         return run_force(ctx, n, nullptr, nn, MODE_ADJOINT, nullptr, lx, lm, 1);
     };
     for (int k = n_steps - 1; k >= 0; --k) {
