@@ -73,6 +73,9 @@ struct kirin_ctx {
     // a host word the kernels report their errors to directly (mapped pinned memory: read after the
     // stream synchronises, no copy), or null where mapping is unavailable (then d_err)
     unsigned *h_err_map = nullptr, *d_err_map = nullptr;
+    // mapped host copies of a host-driven block step's time and size (same condition), or null
+    double *h_sel_t = nullptr, *d_sel_t = nullptr;
+    int32_t *h_sel_n = nullptr, *d_sel_n = nullptr;
 
     bool pending = false;
     int64_t pending_n = 0;
@@ -452,6 +455,8 @@ void free_all(kirin_ctx *c)
         cudaFreeHost(c->h_err);
     if (c->h_err_map)
         cudaFreeHost(c->h_err_map);
+    if (c->h_sel_t)
+        cudaFreeHost(c->h_sel_t);
     if (c->h_run)
         cudaFreeHost(c->h_run);
     if (c->d_run)
@@ -897,6 +902,18 @@ int kirin_init(kirin_ctx **out, int64_t n_max, const kirin_config *cfg)
         if (cudaHostAlloc((void **)&c->h_err_map, sizeof(unsigned), cudaHostAllocMapped) == cudaSuccess &&
             cudaHostGetDevicePointer((void **)&c->d_err_map, c->h_err_map, 0) == cudaSuccess) {
             *(volatile unsigned *)c->h_err_map = 0u;
+            // the block step's time and size, in one mapped allocation (a double, then an int32)
+            if (cudaHostAlloc((void **)&c->h_sel_t, 16, cudaHostAllocMapped) == cudaSuccess &&
+                cudaHostGetDevicePointer((void **)&c->d_sel_t, c->h_sel_t, 0) == cudaSuccess) {
+                c->h_sel_n = reinterpret_cast<int32_t *>(c->h_sel_t + 1);
+                c->d_sel_n = reinterpret_cast<int32_t *>(c->d_sel_t + 1);
+            } else {
+                cudaGetLastError();
+                if (c->h_sel_t)
+                    cudaFreeHost(c->h_sel_t);
+                c->h_sel_t = nullptr;
+                c->d_sel_t = nullptr;
+            }
         } else {
             cudaGetLastError();
             if (c->h_err_map)
@@ -1384,12 +1401,20 @@ int kirin_hermite_block_step(kirin_ctx *ctx, double t_end, double *t_now, int64_
     const int n = (int)ctx->n_j;
     CK(ctx, launch_block_select(n, ctx->bt, ctx->bdt, t_end, ctx->d_ilist, ctx->d_scal, ctx->d_count,
                                 reinterpret_cast<unsigned long long *>(ctx->d_scal + 3), ctx->d_sel_counts,
-                                ctx->stream));
-    CK(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(ctx->h_count, ctx->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    const double t_next = ctx->h_scal[0];
-    const int n_act = *ctx->h_count;
+                                ctx->stream, ctx->d_sel_t, ctx->d_sel_n));
+    double t_next;
+    int n_act;
+    if (ctx->h_sel_t) {  // the selection wrote its mapped copies: read them once the stream is done
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        t_next = *(volatile double *)ctx->h_sel_t;
+        n_act = *(volatile int32_t *)ctx->h_sel_n;
+    } else {
+        CK(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(ctx->h_count, ctx->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        t_next = ctx->h_scal[0];
+        n_act = *ctx->h_count;
+    }
     if (t_now)
         *t_now = t_next;
     if (n_active)

@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *
                                                            const unsigned long long *minw,
                                                            const int32_t *__restrict__ counts, double t_end,
                                                            int32_t *ilist, double *t_next_out,
-                                                           int32_t *count_out)
+                                                           int32_t *count_out, double *t_next_host,
+                                                           int32_t *count_host)
 {
     __shared__ int warp_tot[SEL_THREADS / 32];
     __shared__ int red[SEL_THREADS];
@@ -274,6 +275,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_write(int n, const double *
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         *count_out = due ? base : 0;
         *t_next_out = tn;
+        if (count_host) {  // mapped host copies: the host reads them once the stream has synchronised
+            *count_host = due ? base : 0;
+            *t_next_host = tn;
+        }
     }
 }
 
@@ -628,7 +633,7 @@ cudaError_t launch_hermite_init(int n, double t, const double *acc, const double
 
 cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end, int32_t *ilist,
                                 double *t_next_out, int32_t *count_out, unsigned long long *minw,
-                                int32_t *counts, cudaStream_t st)
+                                int32_t *counts, cudaStream_t st, double *t_next_host, int32_t *count_host)
 {
     const int nblk = blocks_for(n, SEL_PER_CTA);
     cudaError_t e = cudaMemsetAsync(minw, 0xff, sizeof(unsigned long long), st);
@@ -636,7 +641,8 @@ cudaError_t launch_block_select(int n, const double *bt, const double *bdt, doub
         return e;
     k_sel_min<<<std::min(nblk * SEL_ITEMS, 1024), SEL_THREADS, 0, st>>>(n, bt, bdt, minw);
     k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts);
-    k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, t_end, ilist, t_next_out, count_out);
+    k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(n, bt, bdt, minw, counts, t_end, ilist, t_next_out, count_out,
+                                              t_next_host, count_host);
     return cudaGetLastError();
 }
 

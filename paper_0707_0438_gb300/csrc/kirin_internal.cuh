@@ -181,9 +181,11 @@ cudaError_t launch_hermite_init(int n, double t, const double *acc, const double
                                 double dt_min, double dt_max, double *ba, double *bj,
                                 double *bt, double *bdt, cudaStream_t st);
 // counts: ceil(n / 1024) int32 of scratch; minw: one 64-bit word of scratch.
+// (t_next_host, count_host: optional mapped host copies of the block's time and size)
 cudaError_t launch_block_select(int n, const double *bt, const double *bdt, double t_end, int32_t *ilist,
                                 double *t_next_out, int32_t *count_out, unsigned long long *minw,
-                                int32_t *counts, cudaStream_t st);
+                                int32_t *counts, cudaStream_t st, double *t_next_host = nullptr,
+                                int32_t *count_host = nullptr);
 cudaError_t launch_hermite_correct(int n_act, const int32_t *ilist, double t_next, double eta,
                                    double dt_min, double dt_max, int update_dt,
                                    const double *xp, const double *vp, const double *acc,
