@@ -243,6 +243,10 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
                 return Shape{c->table_groups[kind][k], std::min<int>(c->table_split[kind][k], std::max(1, ntiles))};
     }
     const int per_thread = prec == KIRIN_MIXED ? MIX_I_PER_THREAD : 1;
+    // a split's partial write and reduction launch in pair slots of this precision: an FP64 pair
+    // takes about 64 times a mixed one (1.6e10 against 1e12 pairs/s), so the same time is worth
+    // 64 times fewer FP64 slots
+    const double split_scale = prec == KIRIN_MIXED ? 1.0 : 1.0 / 64.0;
     Shape best{1, 1};
     double best_cost = 1e300;
     const size_t cap_entries = (size_t)1 << 27;  // bound on n_split * 7 * n_i_pad doubles (1 GiB)
@@ -261,7 +265,7 @@ Shape choose_shape(kirin_ctx *c, int64_t n_i, int ntiles, int prec, int mode, bo
             const double cta_cost = (tiles_per + 2.0) * TILE_J * (double)i_cta;
             double cost = waves * cta_cost;
             if (ns > 1)  // partial write + reduction, in pair-slot units
-                cost += (double)ns * 7 * iblocks * i_cta * 4.0 / slots + 5.0e3 * TILE_J;
+                cost += split_scale * ((double)ns * 7 * iblocks * i_cta * 4.0 / slots + 5.0e3 * TILE_J);
             if (cost < best_cost * 0.999) {
                 best_cost = cost;
                 best = Shape{groups, ns};
