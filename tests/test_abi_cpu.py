@@ -64,6 +64,12 @@ def test_null_context_is_rejected(lib):
     assert lib.kirin_batch_get_state_dev(None, None, None) == abi.KIRIN_EINVAL
     assert lib.kirin_batch_accel_dev(None, None) == abi.KIRIN_EINVAL
     assert lib.kirin_batch_get_launch(None, None, None, None) == abi.KIRIN_EINVAL
+    assert lib.kirin_hermite_init(None, 0.0, 0.01, 2.0 ** -20, 2.0 ** -3) == abi.KIRIN_EINVAL
+    assert lib.kirin_hermite_shared_run(None, 0.1, 1) == abi.KIRIN_EINVAL
+    assert lib.kirin_set_shared_persistent(None, 1) == abi.KIRIN_EINVAL
+    assert lib.kirin_get_shared_persistent(None, None) == abi.KIRIN_EINVAL
+    assert lib.kirin_selftest_arrival_timeout(None, 1000) == abi.KIRIN_EINVAL
+    assert lib.kirin_selftest_wait_timeout(None, 1000) == abi.KIRIN_EINVAL
     assert lib.kirin_last_error(None).decode() == "no context"
 
 
