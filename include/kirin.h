@@ -260,15 +260,15 @@ int kirin_set_device_loop(kirin_ctx *ctx, int32_t enable);
 int kirin_hermite_shared_step(kirin_ctx *ctx, double dt);
 
 /* n_steps shared steps of size dt, with a single synchronisation (and error
- * check) at the end.  A mixed-precision system of at most 2048 particles
+ * check) at the end.  A mixed-precision system of at most 8192 particles
  * (no fixed launch shape, no j partition) runs the whole call in one
  * cooperative launch, one CTA per SM: each CTA owns a slice of the particles,
  * corrects it with the step kernels' corrector and predicts it with their
  * FP64 predictor into a global j image (two images, for even and odd steps)
  * and counts its arrival on a counter that only grows; once every CTA has
  * arrived for the step (a bounded wait) each copies the image into its shared
- * memory and sums its slice's acc, jerk and pot against all j with the force
- * kernels' pair arithmetic.  Otherwise the steps are the predictor,
+ * memory (above 2048 particles through a ring of tiles) and sums its slice's
+ * acc, jerk and pot against all j with the force kernels' pair arithmetic.  Otherwise the steps are the predictor,
  * force and corrector kernels enqueued back to back, the same kernels and
  * results as n_steps calls of kirin_hermite_shared_step.  The two paths sum
  * the j in different orders, so they agree to rounding; each gives the same

@@ -70,7 +70,7 @@ constexpr int STEP_CTAS_PER_SM = 2;
 // that only grows; each CTA waits for all arrivals of the step, copies the
 // whole image into its shared memory and sums its own particles against it
 // (mixed precision).
-constexpr int SH_MAX_N = 2048;
+constexpr int SH_MAX_N = 8192;
 struct SharedStepArgs {
     int n, n_pad;             // particles; image records (a multiple of TILE_J)
     const double *m;

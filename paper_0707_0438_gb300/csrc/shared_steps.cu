@@ -8,11 +8,12 @@
 // arithmetic.  Here one CTA per SM stays resident for the whole run:
 //  * CTA b owns particles [b n / P, (b + 1) n / P) of P CTAs and keeps their
 //    FP64 state in shared memory for the launch (written through to the
-//    context's arrays every step).  Warps 0, 1 and 2 correct the x, y and z
-//    components of the slice and predict them at once to the next step, with
-//    the step kernels' arithmetic: FP64 is the scarce pipe on this part and
-//    a warp instruction costs the same with 1 or 32 lanes, so three short
-//    chains on three SM sub-partitions beat one long chain;
+//    context's arrays every step).  Warps 0, 1 and 2 (and 3, 4, 5 for a
+//    slice of more than 32) correct the x, y and z components of the slice
+//    and predict them at once to the next step, with the step kernels'
+//    arithmetic: FP64 is the scarce pipe on this part and a warp instruction
+//    costs the same with 1 or 32 lanes, so three short chains on three SM
+//    sub-partitions beat one long chain;
 //  * the predicted records go to the global j image of the next step's
 //    parity (two images alternate), and the CTA adds 1 to an arrival counter
 //    that only grows (a fire-and-forget release add).  Before step s each CTA
@@ -25,7 +26,10 @@
 //    contiguous sixteenth of the j, its groups of threads interleaved record
 //    by record (consecutive 80-byte records fall on disjoint banks); partial
 //    sums folded in double-single, the groups of a warp combined by shuffles
-//    and the warps in warp order.
+//    and the warps in warp order.  Above 2048 records the image streams
+//    through a ring of tiles instead, in two halves (the CTA sums one while
+//    the other fills, one CTA barrier per half), each warp taking its
+//    sixteenth of every tile.
 // With init set, the launch instead evaluates the particles as they are at t0
 // and initialises the integrator (a, jerk, t and the first block step, the
 // initialisation kernel's arithmetic): one launch for kirin_hermite_init.
@@ -43,14 +47,21 @@ namespace {
 
 constexpr int SH_THREADS = 512;
 constexpr int SH_WARPS = SH_THREADS / 32;
-constexpr int SH_MAX_OWN = 32;  // particles per CTA (groups of up to 16 threads, two i each)
+constexpr int SH_MAX_OWN = 64;  // particles per CTA (groups of up to 32 threads, two i each)
+// Images of more than SH_RESIDENT_N records stream through a ring of SH_RING tiles in two halves of
+// SH_CH: the CTA sums one half while the other fills, one CTA barrier per half.
+constexpr int SH_RESIDENT_N = 2048;
+constexpr int SH_CH = 6;
+constexpr int SH_RING = 2 * SH_CH;
 constexpr int SH_FLUSH_J = 256;  // j per FP32 partial sum and thread, as in the force kernels
-constexpr int SH_MAX_TILES = SH_MAX_N / TILE_J;
+constexpr int SH_MAX_TILES = SH_RESIDENT_N / TILE_J;
 constexpr int SH_BAR_BYTES = 256;  // the tiles' mbarriers, ahead of the image
 constexpr uint32_t SH_TILE_BYTES = TILE_J * sizeof(JMixed);
-static_assert(SH_MAX_N % TILE_J == 0 && SH_MAX_TILES * 8 <= SH_BAR_BYTES, "mbarrier area");
+static_assert(SH_RESIDENT_N % TILE_J == 0 && SH_MAX_N % TILE_J == 0, "whole tiles");
+static_assert(SH_MAX_TILES * 8 <= SH_BAR_BYTES && SH_RING * 8 <= SH_BAR_BYTES, "mbarrier area");
 static_assert(SH_TILE_BYTES % 16 == 0 && SH_BAR_BYTES % 16 == 0, "bulk copies want 16-byte multiples");
-static_assert(SH_MAX_N * (SH_MAX_OWN / 2) / SH_THREADS <= SH_FLUSH_J, "one fold per step holds a group's j");
+static_assert(SH_RESIDENT_N * 16 / SH_THREADS <= SH_FLUSH_J, "one fold per step holds a resident group's j");
+static_assert(TILE_J % SH_WARPS == 0 && (TILE_J / SH_WARPS) % 2 == 0, "a warp's records of a streamed tile");
 
 // Own-state rows in shared memory, doubles [row][I_CTA]: per component c the
 // rows 6c + (x, v, a, jerk, x_p, v_p), the 7 force rows of the step, then the
@@ -64,10 +75,12 @@ constexpr int CORR_ROW = 25, PRED_ROW = 32;
 template <int GT>
 __host__ __device__ constexpr size_t sh_red_bytes() { return (size_t)SH_WARPS * 7 * 2 * GT * sizeof(float2); }
 
-template <int GT>
+// Resident: the whole image.  Streamed: the ring, then the CTA's own records.
+template <int GT, bool STREAM>
 __host__ __device__ constexpr size_t sh_smem_bytes(int n_pad)
 {
-    return SH_BAR_BYTES + (size_t)n_pad * sizeof(JMixed) + sh_red_bytes<GT>() + (size_t)ST_ROWS * 2 * GT * sizeof(double);
+    return SH_BAR_BYTES + (size_t)(STREAM ? SH_RING * TILE_J + 2 * GT : n_pad) * sizeof(JMixed) + sh_red_bytes<GT>() +
+           (size_t)ST_ROWS * 2 * GT * sizeof(double);
 }
 
 // Component c of particle k predicted to X, V: the FP64 rows x_p, v_p, and the c-parts of its j
@@ -95,7 +108,7 @@ __device__ __forceinline__ void emit_component(const SharedStepArgs &A, JMixed *
     fence_proxy_async_global();
 }
 
-template <int GT, bool GUARD>
+template <int GT, bool GUARD, bool STREAM>
 __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStepArgs A)
 {
     constexpr int GROUPS = SH_THREADS / GT;
@@ -103,9 +116,11 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
     static_assert(32 % GT == 0 && I_CTA <= SH_MAX_OWN, "groups tile the warps");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int n = A.n, n_pad = A.n_pad, n_tiles = n_pad / TILE_J;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);                     // [n_tiles]
-    JMixed *img = reinterpret_cast<JMixed *>(smem_raw + SH_BAR_BYTES);           // [n_pad]
-    float2 *red = reinterpret_cast<float2 *>(img + n_pad);                        // [SH_WARPS][7][I_CTA]
+    constexpr int IMG = STREAM ? SH_RING * TILE_J + I_CTA : 0;  // streamed: ring and own records
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);                     // [n_tiles] or [SH_RING]
+    JMixed *img = reinterpret_cast<JMixed *>(smem_raw + SH_BAR_BYTES);           // [n_pad] or the ring
+    JMixed *orec = img + SH_RING * TILE_J;                                        // streamed: [I_CTA]
+    float2 *red = reinterpret_cast<float2 *>(img + (STREAM ? IMG : n_pad));       // [SH_WARPS][7][I_CTA]
     double *st = reinterpret_cast<double *>(red + SH_WARPS * 7 * I_CTA);          // [ST_ROWS][I_CTA]
     const int P = (int)gridDim.x, b = (int)blockIdx.x;
     const int lo = (int)((long long)n * b / P), hi = (int)((long long)n * (b + 1) / P);
@@ -118,10 +133,13 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
     const float eps2f = (float)A.eps2, rmin2f = (float)A.rmin2;
     const bool need_mask = eps2f != 0.f;  // with eps = 0 the guard zeroes the self pair anyway
     const unsigned count0 = A.arrivals0, per_step = (unsigned)P;
-    // the component lanes: warp c < 3, lane = slot of the particle
-    const bool comp = warp < 3 && lane < own;
-    const int c = warp, kc = lo + lane;
-    if (tid == 0) {
+    // the component lanes: warp w < 3 CW (CW warps per component), component c = w % 3, particle
+    // slot sl = lane + 32 (w / 3)
+    constexpr int CW = I_CTA > 32 ? 2 : 1;
+    const int c = warp % 3, sl = lane + 32 * (warp / 3);
+    const bool comp = warp < 3 * CW && sl < own;
+    const int kc = lo + sl;
+    if (tid == 0 && !STREAM) {  // (streamed: the ring's barriers are set up at every step)
         for (int q = 0; q < n_tiles; ++q)
             mbar_init(&bars[q], 1);
         mbar_fence_init();
@@ -140,12 +158,12 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
     // the first image: own particles predicted to t0 + dt (or, to initialise, as they are); the last
     // CTA writes both images' padding
     if (comp) {
-        double X = st[st_row(c, 0) * I_CTA + lane], V = st[st_row(c, 1) * I_CTA + lane];
+        double X = st[st_row(c, 0) * I_CTA + sl], V = st[st_row(c, 1) * I_CTA + sl];
         if (!A.init)
-            predict_xv(predict_dt((A.t0 + A.dt) - tb), X, V, st[st_row(c, 2) * I_CTA + lane],
-                       st[st_row(c, 3) * I_CTA + lane], X, V);
-        st[st_row(c, 4) * I_CTA + lane] = X;
-        st[st_row(c, 5) * I_CTA + lane] = V;
+            predict_xv(predict_dt((A.t0 + A.dt) - tb), X, V, st[st_row(c, 2) * I_CTA + sl],
+                       st[st_row(c, 3) * I_CTA + sl], X, V);
+        st[st_row(c, 4) * I_CTA + sl] = X;
+        st[st_row(c, 5) * I_CTA + sl] = V;
         emit_component(A, A.img, c, kc, X, V, M);
     }
     if (b == P - 1) {
@@ -164,37 +182,22 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
         // 0. while thread 0 waits: the corrector's interval and powers (warp 1, from the particle's
         //    own time) and the predictor's for the next step (warp 2), into shared memory
         if (A.init) {
-        } else if (warp == 1 && lane < own) {
+        } else if (comp && c == 1) {
             const CorrectDt S = correct_dt(tn - tb);
             const double r[7] = {S.dt, S.idt2, S.idt3, S.c3, S.c4, S.c5, S.dt6};
 #pragma unroll
             for (int q = 0; q < 7; ++q)
-                st[(CORR_ROW + q) * I_CTA + lane] = r[q];
-        } else if (warp == 2 && lane < own) {
+                st[(CORR_ROW + q) * I_CTA + sl] = r[q];
+        } else if (comp && c == 2) {
             const PredictDt Pd = predict_dt((tn + A.dt) - tn);
-            st[PRED_ROW * I_CTA + lane] = Pd.dt;
-            st[(PRED_ROW + 1) * I_CTA + lane] = Pd.dt2;
-            st[(PRED_ROW + 2) * I_CTA + lane] = Pd.dt3;
+            st[PRED_ROW * I_CTA + sl] = Pd.dt;
+            st[(PRED_ROW + 1) * I_CTA + sl] = Pd.dt2;
+            st[(PRED_ROW + 2) * I_CTA + sl] = Pd.dt3;
         }
         // 1. every CTA's records of this step are out: the whole image into shared memory
         if (!wait_arrivals(A.arrivals, count0 + ((unsigned)step + 1u) * per_step, A.err))
             return;  // no copy of this step was issued yet
-        if (tid == 0) {
-            fence_proxy_async_global();
-            const JMixed *src = A.img + (size_t)(step & 1) * n_pad;
-            for (int q = 0; q < n_tiles; ++q) {
-                mbar_arrive_expect_tx(&bars[q], SH_TILE_BYTES);
-                bulk_g2s(img + (size_t)q * TILE_J, src + (size_t)q * TILE_J, SH_TILE_BYTES, &bars[q]);
-            }
-        }
-        // 2. own particles (thread s of group g holds slots s and s + GT) against the group's j; wait
-        //    for the tiles this thread reads (a failed wait is made warp-uniform, so no lane leaves its
-        //    warp's votes behind)
-        bool failed = !__all_sync(0xffffffffu, mbar_wait_bounded(&bars[lo / TILE_J], parity) &&
-                                                   mbar_wait_bounded(&bars[(hi - 1) / TILE_J], parity) &&
-                                                   mbar_wait_bounded(&bars[wb / TILE_J], parity) &&
-                                                   mbar_wait_bounded(&bars[(wb + W * L - 1) / TILE_J], parity));
-        int idx[2];
+        int idx[2];  // thread s of group g holds slots s and s + GT
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int k = lo + s + q * GT;
@@ -203,35 +206,130 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
         Lane7 acc0, acc1;
         acc0.zero();
         acc1.zero();
-        if (!failed) {
-            const IPair I = load_ipair(img + (idx[0] >= 0 ? idx[0] : lo), img + (idx[1] >= 0 ? idx[1] : lo), eps2f,
-                                       rmin2f);
+        const JMixed *src = A.img + (size_t)(step & 1) * n_pad;
+        if constexpr (!STREAM) {
+            if (tid == 0) {
+                fence_proxy_async_global();
+                for (int q = 0; q < n_tiles; ++q) {
+                    mbar_arrive_expect_tx(&bars[q], SH_TILE_BYTES);
+                    bulk_g2s(img + (size_t)q * TILE_J, src + (size_t)q * TILE_J, SH_TILE_BYTES, &bars[q]);
+                }
+            }
+            // 2. own particles against the group's j; wait for the tiles this thread reads (a failed wait is
+            //    made warp-uniform, so no lane leaves its warp's votes behind)
+            const bool failed = !__all_sync(0xffffffffu, mbar_wait_bounded(&bars[lo / TILE_J], parity) &&
+                                                             mbar_wait_bounded(&bars[(hi - 1) / TILE_J], parity) &&
+                                                             mbar_wait_bounded(&bars[wb / TILE_J], parity) &&
+                                                             mbar_wait_bounded(&bars[(wb + W * L - 1) / TILE_J], parity));
+            if (!failed) {
+                const IPair I = load_ipair(img + (idx[0] >= 0 ? idx[0] : lo), img + (idx[1] >= 0 ? idx[1] : lo),
+                                           eps2f, rmin2f);
+                Tile7 tt;
+                tt.zero();
+                const JMixed *T = img + wb + gw;
+                const bool mine =
+                    (unsigned)(idx[0] - wb) < (unsigned)(W * L) || (unsigned)(idx[1] - wb) < (unsigned)(W * L);
+                if (need_mask && __any_sync(0xffffffffu, mine)) {
+                    for (int jj = 0; jj < L; ++jj)
+                        pair<GUARD, MODE_ACC_JERK_POT, true>(T[W * jj], I, tt, wb + gw + W * jj, idx[0], idx[1]);
+                } else {
+#pragma unroll 4
+                    for (int jj = 0; jj < L; ++jj)
+                        pair<GUARD, MODE_ACC_JERK_POT>(T[W * jj], I, tt);
+                }
+                fold<MODE_ACC_JERK_POT>(tt, acc0, acc1);
+            }
+            fence_proxy_async_smem();  // this step's reads of the image before the next step's copies
+            if (__syncthreads_or(failed)) {
+                if (tid == 0) {  // no copy of this CTA may still be landing when it leaves
+                    atomicOr(A.err, ERR_TIMEOUT);
+                    for (int q = 0; q < n_tiles; ++q)
+                        if (!mbar_wait_bounded(&bars[q], parity)) {
+                            atomicOr(A.err, ERR_DRAIN);
+                            break;
+                        }
+                }
+                return;  // the other CTAs give up waiting for this one's arrival
+            }
+        } else {
+            // 2 streamed: the CTA's own records from the global image (its own writes), and the image
+            // tile by tile through the ring.  The ring's barriers are set up afresh every step, so tile q
+            // (slot q % SH_RING) completes phase (q / SH_RING) & 1 of its slot's barrier.  Warp w sums
+            // records [w JW, (w + 1) JW) of each tile, its groups interleaved record by record.
+            constexpr int JW = TILE_J / SH_WARPS;
+            for (int q = tid; q < 5 * own; q += SH_THREADS) {
+                const int k = q / 5, w5 = q - 5 * k;
+                orec[k].q[w5] = __ldcg(reinterpret_cast<const float4 *>(src + lo + k) + w5);
+            }
+            auto issue = [&](int q) {
+                const int slot = q % SH_RING;
+                mbar_arrive_expect_tx(&bars[slot], SH_TILE_BYTES);
+                bulk_g2s(img + (size_t)slot * TILE_J, src + (size_t)q * TILE_J, SH_TILE_BYTES, &bars[slot]);
+            };
+            if (tid == 0) {
+                for (int q = 0; q < SH_RING; ++q)
+                    mbar_init(&bars[q], 1);
+                mbar_fence_init();
+                fence_proxy_async_global();
+                for (int q = 0; q < n_tiles && q < SH_RING; ++q)
+                    issue(q);
+            }
+            __syncthreads();  // own records and barriers ready
+            const IPair I = load_ipair(orec + (idx[0] >= 0 ? idx[0] - lo : 0), orec + (idx[1] >= 0 ? idx[1] - lo : 0),
+                                       eps2f, rmin2f);
             Tile7 tt;
             tt.zero();
-            const JMixed *T = img + wb + gw;
-            const bool mine =
-                (unsigned)(idx[0] - wb) < (unsigned)(W * L) || (unsigned)(idx[1] - wb) < (unsigned)(W * L);
-            if (need_mask && __any_sync(0xffffffffu, mine)) {
-                for (int jj = 0; jj < L; ++jj)
-                    pair<GUARD, MODE_ACC_JERK_POT, true>(T[W * jj], I, tt, wb + gw + W * jj, idx[0], idx[1]);
-            } else {
-#pragma unroll 4
-                for (int jj = 0; jj < L; ++jj)
-                    pair<GUARD, MODE_ACC_JERK_POT>(T[W * jj], I, tt);
-            }
-            fold<MODE_ACC_JERK_POT>(tt, acc0, acc1);
-        }
-        fence_proxy_async_smem();  // this step's reads of the image before the next step's copies
-        if (__syncthreads_or(failed)) {
-            if (tid == 0) {  // no copy of this CTA may still be landing when it leaves
-                atomicOr(A.err, ERR_TIMEOUT);
-                for (int q = 0; q < n_tiles; ++q)
-                    if (!mbar_wait_bounded(&bars[q], parity)) {
-                        atomicOr(A.err, ERR_DRAIN);
+            int since = 0;
+            bool failed = false;
+            const int n_chunks = (n_tiles + SH_CH - 1) / SH_CH;
+            int cch = 0;
+            for (; cch < n_chunks; ++cch) {
+                const int q1 = min(n_tiles, (cch + 1) * SH_CH);
+                for (int q = cch * SH_CH; q < q1; ++q) {
+                    const int slot = q % SH_RING;
+                    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[slot], (uint32_t)(q / SH_RING) & 1u))) {
+                        failed = true;
                         break;
                     }
+                    const int j0 = q * TILE_J + warp * JW;
+                    const JMixed *T = img + (size_t)slot * TILE_J + warp * JW + gw;
+                    const bool mine =
+                        (unsigned)(idx[0] - j0) < (unsigned)JW || (unsigned)(idx[1] - j0) < (unsigned)JW;
+                    if (need_mask && __any_sync(0xffffffffu, mine)) {
+                        for (int jj = 0; jj < JW / W; ++jj)
+                            pair<GUARD, MODE_ACC_JERK_POT, true>(T[W * jj], I, tt, j0 + gw + W * jj, idx[0], idx[1]);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < JW / W; ++jj)
+                            pair<GUARD, MODE_ACC_JERK_POT>(T[W * jj], I, tt);
+                    }
+                    since += JW / W;
+                    if (since >= SH_FLUSH_J) {
+                        fold<MODE_ACC_JERK_POT>(tt, acc0, acc1);
+                        since = 0;
+                    }
+                }
+                fence_proxy_async_smem();  // this half's reads before its refill
+                if (__syncthreads_or(failed)) {
+                    failed = true;
+                    break;
+                }
+                if (tid == 0)  // the half just summed takes the chunk after next
+                    for (int q = (cch + 2) * SH_CH; q < n_tiles && q < (cch + 3) * SH_CH; ++q)
+                        issue(q);
             }
-            return;  // the other CTAs give up waiting for this one's flag
+            if (failed) {
+                if (tid == 0) {  // every copy issued and not yet consumed lands first (chunks cch, cch + 1)
+                    atomicOr(A.err, ERR_TIMEOUT);
+                    for (int q = cch * SH_CH; q < n_tiles && q < (cch + 2) * SH_CH; ++q)
+                        if (!mbar_wait_bounded(&bars[q % SH_RING], (uint32_t)(q / SH_RING) & 1u)) {
+                            atomicOr(A.err, ERR_DRAIN);
+                            break;
+                        }
+                }
+                return;
+            }
+            fold<MODE_ACC_JERK_POT>(tt, acc0, acc1);
         }
         // 3. the groups of a warp combined by shuffles (a fixed tree), then the warps in warp order
 #pragma unroll
@@ -277,12 +375,12 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
         __syncthreads();
         // 4. initialisation: a, jerk and t of each own particle, and its first block step
         if (A.init) {
-            if (warp == 0 && lane < own) {
+            if (comp && c == 0) {
                 double a0[3], j0[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    a0[q] = st[force_row(q) * I_CTA + lane];
-                    j0[q] = st[force_row(3 + q) * I_CTA + lane];
+                    a0[q] = st[force_row(q) * I_CTA + sl];
+                    j0[q] = st[force_row(3 + q) * I_CTA + sl];
                     A.a[3 * (size_t)kc + q] = a0[q];
                     A.jerk_b[3 * (size_t)kc + q] = j0[q];
                 }
@@ -295,22 +393,22 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
         //    predicted to the next step into the other image
         if (comp) {
             CorrectDt S;
-            S.dt = st[CORR_ROW * I_CTA + lane];
-            S.idt2 = st[(CORR_ROW + 1) * I_CTA + lane];
-            S.idt3 = st[(CORR_ROW + 2) * I_CTA + lane];
-            S.c3 = st[(CORR_ROW + 3) * I_CTA + lane];
-            S.c4 = st[(CORR_ROW + 4) * I_CTA + lane];
-            S.c5 = st[(CORR_ROW + 5) * I_CTA + lane];
-            S.dt6 = st[(CORR_ROW + 6) * I_CTA + lane];
-            const double a1 = st[force_row(c) * I_CTA + lane], j1 = st[force_row(3 + c) * I_CTA + lane];
+            S.dt = st[CORR_ROW * I_CTA + sl];
+            S.idt2 = st[(CORR_ROW + 1) * I_CTA + sl];
+            S.idt3 = st[(CORR_ROW + 2) * I_CTA + sl];
+            S.c3 = st[(CORR_ROW + 3) * I_CTA + sl];
+            S.c4 = st[(CORR_ROW + 4) * I_CTA + sl];
+            S.c5 = st[(CORR_ROW + 5) * I_CTA + sl];
+            S.dt6 = st[(CORR_ROW + 6) * I_CTA + sl];
+            const double a1 = st[force_row(c) * I_CTA + sl], j1 = st[force_row(3 + c) * I_CTA + sl];
             double x1, v1, a2, a3;
-            correct_xv(S, st[st_row(c, 2) * I_CTA + lane], st[st_row(c, 3) * I_CTA + lane], a1, j1,
-                       st[st_row(c, 4) * I_CTA + lane], st[st_row(c, 5) * I_CTA + lane], x1, v1, a2, a3);
+            correct_xv(S, st[st_row(c, 2) * I_CTA + sl], st[st_row(c, 3) * I_CTA + sl], a1, j1,
+                       st[st_row(c, 4) * I_CTA + sl], st[st_row(c, 5) * I_CTA + sl], x1, v1, a2, a3);
             tb = tn;
-            st[st_row(c, 0) * I_CTA + lane] = x1;
-            st[st_row(c, 1) * I_CTA + lane] = v1;
-            st[st_row(c, 2) * I_CTA + lane] = a1;
-            st[st_row(c, 3) * I_CTA + lane] = j1;
+            st[st_row(c, 0) * I_CTA + sl] = x1;
+            st[st_row(c, 1) * I_CTA + sl] = v1;
+            st[st_row(c, 2) * I_CTA + sl] = a1;
+            st[st_row(c, 3) * I_CTA + sl] = j1;
             const size_t o = 3 * (size_t)kc + c;
             A.x[o] = x1;
             A.v[o] = v1;
@@ -320,13 +418,13 @@ __global__ void __launch_bounds__(SH_THREADS, 1) k_shared_steps(const SharedStep
                 A.t_b[kc] = tn;
             if (step + 1 < A.n_steps) {
                 PredictDt Pd;
-                Pd.dt = st[PRED_ROW * I_CTA + lane];
-                Pd.dt2 = st[(PRED_ROW + 1) * I_CTA + lane];
-                Pd.dt3 = st[(PRED_ROW + 2) * I_CTA + lane];
+                Pd.dt = st[PRED_ROW * I_CTA + sl];
+                Pd.dt2 = st[(PRED_ROW + 1) * I_CTA + sl];
+                Pd.dt3 = st[(PRED_ROW + 2) * I_CTA + sl];
                 double X, V;
                 predict_xv(Pd, x1, v1, a1, j1, X, V);
-                st[st_row(c, 4) * I_CTA + lane] = X;
-                st[st_row(c, 5) * I_CTA + lane] = V;
+                st[st_row(c, 4) * I_CTA + sl] = X;
+                st[st_row(c, 5) * I_CTA + sl] = V;
                 emit_component(A, A.img + (size_t)((step + 1) & 1) * n_pad, c, kc, X, V, M);
             }
         }
@@ -345,21 +443,21 @@ __global__ void k_arrival_selftest(unsigned long long limit_ns, unsigned *err)
     wait_arrivals(&g_never_arrives, 1u, err, limit_ns);
 }
 
-template <int GT, bool GUARD>
+template <int GT, bool GUARD, bool STREAM>
 cudaError_t sh_launch(const SharedStepArgs &a, bool query_only, int *grid, cudaStream_t st)
 {
-    const auto kern = k_shared_steps<GT, GUARD>;
+    const auto kern = k_shared_steps<GT, GUARD, STREAM>;
     if (query_only) {
         // opt in once for the largest image, so a smaller context cannot lower a larger one's limit
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sh_smem_bytes<GT>(SH_MAX_N));
+                                             (int)sh_smem_bytes<GT, STREAM>(SH_RESIDENT_N));
         if (e != cudaSuccess)
             return e;
         int dev = 0, nsm = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
             (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH_THREADS, sh_smem_bytes<GT>(a.n_pad))) !=
-                cudaSuccess)
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH_THREADS,
+                                                               sh_smem_bytes<GT, STREAM>(a.n_pad))) != cudaSuccess)
             return e;
         const int ctas = per_sm > 0 ? nsm : 0;  // one CTA per SM
         *grid = ctas < a.n ? ctas : a.n;
@@ -368,7 +466,7 @@ cudaError_t sh_launch(const SharedStepArgs &a, bool query_only, int *grid, cudaS
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(a.ctas);
     cfg.blockDim = dim3(SH_THREADS);
-    cfg.dynamicSmemBytes = sh_smem_bytes<GT>(a.n_pad);
+    cfg.dynamicSmemBytes = sh_smem_bytes<GT, STREAM>(a.n_pad);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -378,16 +476,26 @@ cudaError_t sh_launch(const SharedStepArgs &a, bool query_only, int *grid, cudaS
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-// Narrowest j-group that holds a CTA's share of the particles.
+// Narrowest j-group that holds a CTA's share of the particles; the image resident in shared memory up
+// to SH_RESIDENT_N records, streamed above.
 template <bool GUARD>
 cudaError_t sh_dispatch(const SharedStepArgs &a, int own_max, bool query_only, int *grid, cudaStream_t st)
 {
-    if (own_max <= 8)
-        return sh_launch<4, GUARD>(a, query_only, grid, st);
+    if (a.n_pad <= SH_RESIDENT_N) {
+        if (own_max <= 8)
+            return sh_launch<4, GUARD, false>(a, query_only, grid, st);
+        if (own_max <= 16)
+            return sh_launch<8, GUARD, false>(a, query_only, grid, st);
+        if (own_max <= 32)
+            return sh_launch<16, GUARD, false>(a, query_only, grid, st);
+        return cudaErrorInvalidValue;
+    }
     if (own_max <= 16)
-        return sh_launch<8, GUARD>(a, query_only, grid, st);
+        return sh_launch<8, GUARD, true>(a, query_only, grid, st);
+    if (own_max <= 32)
+        return sh_launch<16, GUARD, true>(a, query_only, grid, st);
     if (own_max <= SH_MAX_OWN)
-        return sh_launch<16, GUARD>(a, query_only, grid, st);
+        return sh_launch<32, GUARD, true>(a, query_only, grid, st);
     return cudaErrorInvalidValue;
 }
 
@@ -402,12 +510,13 @@ int shared_steps_grid(int n, bool guard)
     SharedStepArgs a{};
     a.n = n;
     a.n_pad = (n + TILE_J - 1) / TILE_J * TILE_J;
-    // the grid does not depend on the group width (one CTA per SM): ask the widest, then check the
-    // share against the width that will run
+    // the grid does not depend on the group width (one CTA per SM): ask the widest of the path (resident
+    // or streamed), then check the share against the width that will run
+    const int widest = a.n_pad <= SH_RESIDENT_N ? 32 : SH_MAX_OWN;
     int grid = 0;
-    cudaError_t e = guard ? sh_dispatch<true>(a, SH_MAX_OWN, true, &grid, nullptr)
-                          : sh_dispatch<false>(a, SH_MAX_OWN, true, &grid, nullptr);
-    if (e != cudaSuccess || grid < 1 || own_max_of(n, grid) > SH_MAX_OWN) {
+    cudaError_t e = guard ? sh_dispatch<true>(a, widest, true, &grid, nullptr)
+                          : sh_dispatch<false>(a, widest, true, &grid, nullptr);
+    if (e != cudaSuccess || grid < 1 || own_max_of(n, grid) > widest) {
         cudaGetLastError();
         return 0;
     }

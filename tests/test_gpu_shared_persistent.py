@@ -94,9 +94,9 @@ def test_persistent_shared_run_is_deterministic(kirin_lib):
 
 
 def test_persistent_shared_run_limits(kirin_lib):
-    """Above 2048 particles, in FP64 and under a fixed launch shape the per-kernel path runs; a run of
+    """Above 8192 particles, in FP64 and under a fixed launch shape the per-kernel path runs; a run of
     no steps changes nothing."""
-    p = workloads.plummer(2049, 1, eps=0.01)
+    p = workloads.plummer(8193, 1, eps=0.01)
     with abi.Kirin(p.n, p.eps, precision="mixed") as k:
         k.set_j_particles(p.m, p.x, p.v)
         assert not k.shared_persistent_active()
@@ -242,3 +242,42 @@ def test_shared_run_reports_a_non_finite_state_and_recovers(kirin_lib, persisten
         st = k.get_state()
     xr, _, _, _, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, 1.0 / 1024, 3)
     assert np.abs(st["x"] - xr).max() <= 1e-7 * np.abs(p.x).max()
+
+
+@pytest.mark.parametrize("n", [2049, 3000, 4096, 6000, 8192])
+def test_streamed_shared_run_matches_the_oracle(kirin_lib, n):
+    """Above 2048 particles the image streams through a ring of tiles (two halves of 6 tiles): ragged and
+    whole tile counts, slices of up to 54 particles per CTA (six component warps), against the oracle's
+    Hermite steps and its forces at the final state."""
+    p = workloads.plummer(n, (9191, n), eps=1.0 / 256)
+    dt, steps = 1.0 / 1024, 6
+    xr, vr, _, _, _ = hermite.shared_steps(p.m, p.x, p.v, p.eps, dt, steps)
+    active, st, after = _run(p, p.eps, dt, steps, True)
+    assert active
+    assert np.all(st["t"] == steps * dt)
+    assert np.abs(st["x"] - xr).max() <= 1e-7 * np.abs(p.x).max()
+    assert np.abs(st["v"] - vr).max() <= 1e-6 * np.abs(p.v).max()
+    ref = oracle.acc_jerk_pot(p.m, st["x"], st["v"], p.eps)
+    err = metrics.rel_err_vec(after[0], ref[0])
+    assert np.median(err) <= 1e-6 and err.max() <= 1e-4
+
+
+@pytest.mark.parametrize("n,eps,r_min", [(5000, 1.0 / 256, 0.0), (4500, 0.0, 1e-6)])
+def test_streamed_shared_run_agrees_with_the_kernel_path_and_itself(kirin_lib, n, eps, r_min):
+    """The streamed single launch against the step kernels (to rounding), with and without the guard, and
+    a run split over two calls against the same run in one call (bit for bit)."""
+    p = workloads.plummer(n, 9292, eps=eps)
+    dt = 1.0 / 1024
+    a_on, on, _ = _run(p, eps, dt, 16, True, r_min)
+    a_off, off, _ = _run(p, eps, dt, 16, False, r_min)
+    assert a_on and not a_off
+    assert np.all(on["t"] == off["t"])
+    assert np.abs(on["x"] - off["x"]).max() <= 1e-8 * np.abs(p.x).max()
+    with abi.Kirin(p.n, eps, r_min=r_min, precision="mixed") as k:
+        k.set_j_particles(p.m, p.x, p.v)
+        k.hermite_init(0.0)
+        k.hermite_shared_run(dt, 7)
+        k.hermite_shared_run(dt, 9)
+        split = k.get_state()
+    for key in ("x", "v", "a", "j", "t"):
+        assert np.array_equal(split[key], on[key]), key
