@@ -30,6 +30,7 @@
 #include <new>
 #include <vector>
 
+#include "f32_pack.cuh"
 #include "kirin_internal.cuh"
 #include "pair_mixed.cuh"
 #include "tma.cuh"
@@ -279,10 +280,11 @@ __global__ void __launch_bounds__(FORCE_THREADS, 2) k_batch_accel(const BatchArg
 
 __device__ __forceinline__ void pack_record(JMixed *dst, double X, double Y, double Z, double M)
 {
-    const float xh = __double2float_rn(X), yh = __double2float_rn(Y), zh = __double2float_rn(Z);
-    const float xl = __double2float_rn(X - (double)xh), yl = __double2float_rn(Y - (double)yh),
-                zl = __double2float_rn(Z - (double)zh);
-    const float m = __double2float_rn(M);
+    float xh, xl, yh, yl, zh, zl;
+    f32pack::split(X, xh, xl);
+    f32pack::split(Y, yh, yl);
+    f32pack::split(Z, zh, zl);
+    const float m = f32pack::to_f32(M);
     JMixed r;
     r.q[0] = make_float4(xh, xh, yh, yh);
     r.q[1] = make_float4(zh, zh, m, m);
@@ -309,7 +311,7 @@ __global__ void k_kick_drift(int n, double h, double dt, const double *__restric
         v[o] = vh;
         x[o] = X[c];
     }
-    if (!(isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2])))
+    if (!(f32pack::finite(X[0]) && f32pack::finite(X[1]) && f32pack::finite(X[2])))
         atomicOr(err, ERR_NONFINITE);
     pack_record(jm + img_idx[p], X[0], X[1], X[2], m[p]);
 }

@@ -92,16 +92,16 @@ __device__ __forceinline__ void emit_component(const SharedStepArgs &A, JMixed *
     A.vp[3 * (size_t)k + c] = V;
     float h, l;
     split_ds(X, h, l);
-    const float vf = __double2float_rn(V);
+    const float vf = f32pack::to_f32(V);
     float2 *rec = reinterpret_cast<float2 *>(img + k);
     rec[c] = make_float2(h, h);           // q[0].xy, q[0].zw, q[1].xy: x, y, z high words
     rec[4 + c] = make_float2(l, l);       // q[2].xy, q[2].zw, q[3].xy: low words
     rec[7 + c] = make_float2(vf, vf);     // q[3].zw, q[4].xy, q[4].zw: velocity
-    bool bad = !(isfinite(X) && isfinite(V));
+    bool bad = !(f32pack::finite(X) && f32pack::finite(V));
     if (c == 0) {
-        const float mf = __double2float_rn(M);
+        const float mf = f32pack::to_f32(M);
         rec[3] = make_float2(mf, mf);     // q[1].zw: mass
-        bad = bad || !isfinite(M);
+        bad = bad || !f32pack::finite(M);
     }
     if (bad)
         atomicOr(A.err, ERR_NONFINITE);

@@ -6,16 +6,14 @@
 
 #include <cuda_runtime.h>
 
+#include "f32_pack.cuh"
 #include "kirin_internal.cuh"
 
 namespace kirin {
 namespace {
 
-__device__ __forceinline__ void split_ds(double v, float &hi, float &lo)
-{
-    hi = __double2float_rn(v);
-    lo = __double2float_rn(v - (double)hi);
-}
+// hi = RN32(v), lo = RN32(v - hi), built on the integer pipes (f32_pack.cuh).
+__device__ __forceinline__ void split_ds(double v, float &hi, float &lo) { f32pack::split(v, hi, lo); }
 
 __device__ __forceinline__ void write_images(int k, double X, double Y, double Z, double M, double VX,
                                              double VY, double VZ, JMixed *jm, JF64 *jd)
@@ -25,8 +23,8 @@ __device__ __forceinline__ void write_images(int k, double X, double Y, double Z
         split_ds(X, xh, xl);
         split_ds(Y, yh, yl);
         split_ds(Z, zh, zl);
-        const float m = __double2float_rn(M);
-        const float vx = __double2float_rn(VX), vy = __double2float_rn(VY), vz = __double2float_rn(VZ);
+        const float m = f32pack::to_f32(M);
+        const float vx = f32pack::to_f32(VX), vy = f32pack::to_f32(VY), vz = f32pack::to_f32(VZ);
         JMixed r;
         r.q[0] = make_float4(xh, xh, yh, yh);
         r.q[1] = make_float4(zh, zh, m, m);
@@ -102,8 +100,9 @@ __device__ __forceinline__ void predict_one(int k, int n, double t, int predict,
         }
     }
     const double M = m[k];
-    if (!(isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2]) && isfinite(V[0]) && isfinite(V[1]) &&
-          isfinite(V[2]) && isfinite(M)))
+    using f32pack::finite;
+    if (!(finite(X[0]) && finite(X[1]) && finite(X[2]) && finite(V[0]) && finite(V[1]) && finite(V[2]) &&
+          finite(M)))
         atomicOr(err, ERR_NONFINITE);
     write_images(k, X[0], X[1], X[2], M, V[0], V[1], V[2], jm, jd);
 }
