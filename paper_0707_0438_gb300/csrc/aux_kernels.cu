@@ -379,12 +379,27 @@ __device__ __forceinline__ int cta_rank(bool flag, int &all)
 // kernel listed the chunk's members in index order from chunk_off[b], so a
 // member's rank among them gives its row of the force results.  Members add
 // their new end time to the minimum, the others their unchanged one.
+//
+// A pass with at most SPLIT_MEMBERS members (every pass of a small block)
+// corrects each member on three warps, one per component, and then runs
+// Aarseth's criterion on one thread: an FP64 warp instruction costs the same
+// whatever its active lanes, so the latency of a member's corrector is its
+// instruction chain, and the components' share of it runs side by side.  The
+// operations are correct_at's, in its order, so the bits are the same.
+constexpr int SPLIT_MEMBERS = 64;
+
 __global__ void __launch_bounds__(STEP_THREADS) k_step_correct(const StepArgs A)
 {
+    static_assert(STEP_WARPS >= 3 * (SPLIT_MEMBERS / 32), "three component warps per 32 members");
+    __shared__ int mem_i[SPLIT_MEMBERS];                 // the pass's members by rank
+    __shared__ double comp_v[4][3][SPLIT_MEMBERS];       // a1, j1, a2e, a3 per component
+    __shared__ double step_v[3][SPLIT_MEMBERS];          // dt, dt^2, 1/dt of each member's step
+    __shared__ bool step_p2[SPLIT_MEMBERS];
     RunState *R = A.run;
     const int par = (int)(R->steps & 1);
     const bool any = R->pending > 0;
     const double t_prev = R->t_last;
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     int c0, c1;
     chunk_of(A.n, c0, c1);
     int base = any ? A.chunk_off[blockIdx.x] : 0;
@@ -399,11 +414,55 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_correct(const StepArgs A)
         }
         int all;
         const int rank = cta_rank(member, all);
-        if (member)
-            end = correct_at((size_t)i, base + rank, t_prev, A.eta, A.dt_min, A.dt_max, 1, A.xp, A.vp, A.acc,
-                             A.jerk, A.bx, A.bv, A.ba, A.bj, A.bt, A.bdt);
-        if (i < c1)
-            mn = min(mn, time_key(end));
+        if (all == 0 || all > SPLIT_MEMBERS) {
+            if (member)
+                end = correct_at((size_t)i, base + rank, t_prev, A.eta, A.dt_min, A.dt_max, 1, A.xp, A.vp, A.acc,
+                                 A.jerk, A.bx, A.bv, A.ba, A.bj, A.bt, A.bdt);
+            if (i < c1)
+                mn = min(mn, time_key(end));
+        } else {
+            if (member)
+                mem_i[rank] = i;
+            else if (i < c1)
+                mn = min(mn, time_key(end));
+            __syncthreads();
+            const int c = warp % 3, sl = lane + 32 * (warp / 3);
+            if (warp < 3 * (SPLIT_MEMBERS / 32) && sl < all) {
+                const size_t im = (size_t)mem_i[sl];
+                const CorrectDt S = correct_dt(t_prev - A.bt[im]);
+                double a1, j1, a2e, a3;
+                correct_component(S, c, im, base + sl, A.xp, A.vp, A.acc, A.jerk, A.bx, A.bv, A.ba, A.bj, a1, j1,
+                                  a2e, a3);
+                comp_v[0][c][sl] = a1;
+                comp_v[1][c][sl] = j1;
+                comp_v[2][c][sl] = a2e;
+                comp_v[3][c][sl] = a3;
+                if (c == 0) {
+                    step_v[0][sl] = S.dt;
+                    step_v[1][sl] = S.dt2;
+                    step_v[2][sl] = S.idt;
+                    step_p2[sl] = S.p2;
+                }
+            }
+            __syncthreads();
+            const int m = (int)threadIdx.x;
+            if (m < all) {
+                double A2 = 0.0, J = 0.0, N2 = 0.0, N3 = 0.0;
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    A2 = fma(comp_v[0][cc][m], comp_v[0][cc][m], A2);
+                    J = fma(comp_v[1][cc][m], comp_v[1][cc][m], J);
+                    N2 = fma(comp_v[2][cc][m], comp_v[2][cc][m], N2);
+                    N3 = fma(comp_v[3][cc][m], comp_v[3][cc][m], N3);
+                }
+                const size_t im = (size_t)mem_i[m];
+                const double q = aarseth_step(A2, J, N2, N3, step_v[0][m], step_v[1][m], step_p2[m], step_v[2][m],
+                                              t_prev, A.eta, A.dt_min, A.dt_max);
+                A.bt[im] = t_prev;
+                A.bdt[im] = q;
+                mn = min(mn, time_key(t_prev + q));
+            }
+        }
         base += all;
     }
     mn = cta_min_u64(mn);

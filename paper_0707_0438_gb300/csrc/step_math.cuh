@@ -174,65 +174,84 @@ __device__ __forceinline__ void correct_xv(const CorrectDt &S, double a0, double
     v1 = fma(a3, S.c4, fma(a2, S.c3, vp));
 }
 
+// Component c of the Hermite corrector of block member k (particle i): the
+// new a and jerk (acc/jerk row k) are stored, x and v corrected; a1, j1, the
+// a2 at the end of the step (a2e) and a3 go to Aarseth's criterion.
+__device__ __forceinline__ void correct_component(const CorrectDt &S, int c, size_t i, int k, const double *xp,
+                                                  const double *vp, const double *acc, const double *jerk,
+                                                  double *bx, double *bv, double *ba, double *bj, double &a1,
+                                                  double &j1, double &a2e, double &a3)
+{
+    a1 = acc[3 * (size_t)k + c];
+    j1 = jerk[3 * (size_t)k + c];
+    double a2;
+    correct_xv(S, ba[3 * i + c], bj[3 * i + c], a1, j1, xp[3 * i + c], vp[3 * i + c], bx[3 * i + c], bv[3 * i + c],
+               a2, a3);
+    ba[3 * i + c] = a1;
+    bj[3 * i + c] = j1;
+    a2e = fma(S.dt, a3, a2);
+}
+
+// Aarseth's block step after a step of dt ending at t_next, from the squared
+// norms A = |a|^2, J = |jerk|^2, N2 = |a2e|^2, N3 = |a3|^2 (each summed over
+// the components in order x, y, z): the criterion quantised to a power of two
+// that may shrink freely and double only where t_next is a multiple of the
+// doubled step.  FP64 is the scarce pipe on this part, so this spends it
+// sparingly:
+//  - dt_A = sqrt(X / Y), X = eta (|a||a2| + |j|^2), Y = |j||a3| + |a2|^2, is
+//    compared in squared form (q < dt_A <=> q^2 Y < X), with
+//    |a||a2| = sqrt(|a|^2 |a2|^2): two square roots, no divide;
+//  - "t_next is a multiple of 2 dt" is tested exactly by scaling when 2 dt is
+//    a power of two (idt = 1/dt from the exponent), by fmod otherwise.
+__device__ __forceinline__ double aarseth_step(double A, double J, double N2, double N3, double dt, double dt2,
+                                               bool p2, double idt, double t_next, double eta, double dt_min,
+                                               double dt_max)
+{
+    const double X = eta * (sqrt(A * N2) + J), Y = sqrt(J * N3) + N2;
+    double q = dt;
+    if (X == 0.0 && Y == 0.0) {
+        // no criterion (0 / 0): keep the step
+    } else if (X < dt2 * Y) {
+        while (q > dt_min && X < q * q * Y)
+            q *= 0.5;
+    } else if (X >= 4.0 * dt2 * Y && 2.0 * dt <= dt_max) {
+        bool multiple;
+        if (p2) {
+            const double r = t_next * (0.5 * idt);  // exact: a power-of-two scaling
+            multiple = r == trunc(r);
+        } else {
+            multiple = fmod(t_next, 2.0 * dt) == 0.0;
+        }
+        if (multiple)
+            q = 2.0 * dt;
+    }
+    return fmin(fmax(q, dt_min), dt_max);
+}
+
 // Hermite corrector of block member k (particle ilist[k], or k) at t_next
 // from its new a, jerk (acc/jerk row k), and with update_dt its new block
-// step: Aarseth's criterion quantised to a power of two that may shrink
-// freely and double only where t_next is a multiple of the doubled step.
-// FP64 is the scarce pipe on this part (about 1 TFLOP/s, and a single
-// member's dependency chain is latency-bound), so this spends it sparingly:
-//  - 1/dt of a power-of-two step from its exponent (exact), else a divide;
-//  - the powers of dt shared by the three components, fused multiply-adds;
-//  - the criterion dt_A = sqrt(X / Y), X = eta (|a||a2| + |j|^2),
-//    Y = |j||a3| + |a2|^2, compared in squared form (q < dt_A <=> q^2 Y < X),
-//    with |a||a2| = sqrt(|a|^2 |a2|^2): two square roots, no divide;
-//  - "t_next is a multiple of 2 dt" tested exactly by scaling when 2 dt is a
-//    power of two, by fmod otherwise.
-// Member k of the block is particle i; returns its new t_i + dt_i.
+// step (aarseth_step).  The powers of dt are shared by the three components
+// (correct_dt).  Member k of the block is particle i; returns its new
+// t_i + dt_i.
 __device__ __forceinline__ double correct_at(size_t i, int k, double t_next, double eta, double dt_min,
                                              double dt_max, int update_dt, const double *xp, const double *vp,
                                              const double *acc, const double *jerk, double *bx, double *bv,
                                              double *ba, double *bj, double *bt, double *bdt)
 {
     const CorrectDt S = correct_dt(t_next - bt[i]);
-    const double dt = S.dt, dt2 = S.dt2;
     double A = 0.0, J = 0.0, N2 = 0.0, N3 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double a1 = acc[3 * (size_t)k + c], j1 = jerk[3 * (size_t)k + c];
-        double a2, a3;
-        correct_xv(S, ba[3 * i + c], bj[3 * i + c], a1, j1, xp[3 * i + c], vp[3 * i + c], bx[3 * i + c],
-                   bv[3 * i + c], a2, a3);
-        ba[3 * i + c] = a1;
-        bj[3 * i + c] = j1;
-        const double a2e = fma(dt, a3, a2);  // a2 at the end of the step
+        double a1, j1, a2e, a3;
+        correct_component(S, c, i, k, xp, vp, acc, jerk, bx, bv, ba, bj, a1, j1, a2e, a3);
         A = fma(a1, a1, A);
         J = fma(j1, j1, J);
         N2 = fma(a2e, a2e, N2);
         N3 = fma(a3, a3, N3);
     }
     bt[i] = t_next;
-    const bool p2 = S.p2;
-    const double idt = S.idt;
     if (update_dt) {
-        const double X = eta * (sqrt(A * N2) + J), Y = sqrt(J * N3) + N2;
-        double q = dt;
-        if (X == 0.0 && Y == 0.0) {
-            // no criterion (0 / 0): keep the step
-        } else if (X < dt2 * Y) {
-            while (q > dt_min && X < q * q * Y)
-                q *= 0.5;
-        } else if (X >= 4.0 * dt2 * Y && 2.0 * dt <= dt_max) {
-            bool multiple;
-            if (p2) {
-                const double r = t_next * (0.5 * idt);  // exact: a power-of-two scaling
-                multiple = r == trunc(r);
-            } else {
-                multiple = fmod(t_next, 2.0 * dt) == 0.0;
-            }
-            if (multiple)
-                q = 2.0 * dt;
-        }
-        q = fmin(fmax(q, dt_min), dt_max);
+        const double q = aarseth_step(A, J, N2, N3, S.dt, S.dt2, S.p2, S.idt, t_next, eta, dt_min, dt_max);
         bdt[i] = q;
         return t_next + q;
     }
