@@ -277,6 +277,30 @@ int kirin_hermite_shared_step(kirin_ctx *ctx, double dt);
  * ENOMEM (the two images), ETIMEOUT (an arrival or copy wait gave up). */
 int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps);
 
+/* Tracing (no counterpart in the paper, which times its kernels with host
+ * timers and leaves transfers out, Sect. 4.1).  With tracing on, each of these
+ * calls, once past its argument checks, opens an NVTX range named after it (seen
+ * by an attached profiler; free otherwise) and brackets the stream work it
+ * enqueues with two CUDA events: kirin_compute_forces (its i_list copy
+ * included), kirin_compute_forces_dev, kirin_compute_forces_nn_dev,
+ * kirin_energy, kirin_hermite_init, kirin_hermite_block_step,
+ * kirin_hermite_run, kirin_hermite_shared_run, kirin_accel_dev,
+ * kirin_accel_adjoint_dev, kirin_leapfrog_dev and kirin_leapfrog_adjoint_dev.
+ * A call made inside another (kirin_hermite_run's host-driven steps) is timed
+ * as part of the outer one; nothing is timed while the context's stream is
+ * being captured into a graph.  Tracing is off by default.
+ *
+ * kirin_set_tracing: enable != 0 turns it on, 0 off; either way the totals
+ * start again from zero (event pairs still pending are waited for and dropped).
+ * kirin_get_trace: synchronises on the pending pairs and returns the number of
+ * timed calls and their summed device time in milliseconds since the last
+ * kirin_set_tracing.  Every 1024 timed calls the pending pairs are folded in
+ * the same way, which waits for the stream once.
+ * Errors: EINVAL (NULL context or output); ECUDA when an event could not be
+ * read (that call is not counted). */
+int kirin_set_tracing(kirin_ctx *ctx, int32_t enable);
+int kirin_get_trace(kirin_ctx *ctx, int64_t *n_calls, double *device_ms);
+
 /* kirin_set_shared_persistent: enable != 0 (default) lets
  * kirin_hermite_shared_run use the single-launch kernel where it can; 0 keeps
  * the per-kernel steps.  kirin_get_shared_persistent: *active = 1 if the next

@@ -85,6 +85,8 @@ _SIGS = {
     "kirin_set_device_loop": (ctypes.c_int, [_P, _I32]),
     "kirin_set_shared_persistent": (ctypes.c_int, [_P, _I32]),
     "kirin_get_shared_persistent": (ctypes.c_int, [_P, _PI32]),
+    "kirin_set_tracing": (ctypes.c_int, [_P, _I32]),
+    "kirin_get_trace": (ctypes.c_int, [_P, _PI64, _PD]),
     "kirin_hermite_shared_run": (ctypes.c_int, [_P, _D, _I64]),
     "kirin_hermite_shared_step": (ctypes.c_int, [_P, _D]),
     "kirin_get_state": (ctypes.c_int, [_P, _PD, _PD, _PD, _PD, _PD, _PD]),
@@ -398,6 +400,17 @@ class Kirin:
 
     def set_device_loop(self, enable=True):
         self._check(self.lib.kirin_set_device_loop(self.ctx, 1 if enable else 0), "kirin_set_device_loop")
+
+    def set_tracing(self, enable=True):
+        """Time the device work of this context's compute calls with CUDA events (and name them in
+        NVTX ranges); the totals start again from zero."""
+        self._check(self.lib.kirin_set_tracing(self.ctx, 1 if enable else 0), "kirin_set_tracing")
+
+    def get_trace(self):
+        """(timed calls, their device time in ms) since the last set_tracing."""
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        self._check(self.lib.kirin_get_trace(self.ctx, ctypes.byref(n), ctypes.byref(ms)), "kirin_get_trace")
+        return n.value, ms.value
 
     def set_shared_persistent(self, enable=True):
         """Let shared-step runs of small mixed-precision systems take the single-launch kernel."""

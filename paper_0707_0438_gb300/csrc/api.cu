@@ -15,8 +15,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "kirin_internal.cuh"
 #include "loop_internal.cuh"
@@ -131,6 +135,14 @@ struct kirin_ctx {
     bool nn_valid = false;
     int32_t *d_nn = nullptr;
     double *d_nn_r2 = nullptr;
+
+    // tracing (kirin_set_tracing): event pairs around the stream work of traced calls, folded into
+    // the totals when read or when many are pending
+    bool tracing = false;
+    int trace_depth = 0;  // nested traced calls record once, at the outermost
+    int64_t trace_calls = 0;
+    double trace_ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> trace_pending, trace_free;
 
     char msg[256] = {0};
 };
@@ -467,9 +479,86 @@ void free_all(kirin_ctx *c)
         cudaFree(c->d_run);
     if (c->run_exec)
         cudaGraphExecDestroy(c->run_exec);
+    for (auto *v : {&c->trace_pending, &c->trace_free})
+        for (auto &e : *v) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
     if (c->own_stream && c->stream)
         cudaStreamDestroy(c->stream);
 }
+
+// Add every pending event pair's elapsed time to the totals (waiting for the last of them) and
+// keep the events for reuse; with count false (a reset) the pairs are only waited for.
+cudaError_t trace_fold(kirin_ctx *c, bool count)
+{
+    cudaError_t err = cudaSuccess;
+    for (auto &e : c->trace_pending) {
+        float ms = 0.f;
+        cudaError_t r = cudaEventSynchronize(e.second);
+        if (r == cudaSuccess)
+            r = cudaEventElapsedTime(&ms, e.first, e.second);
+        if (r != cudaSuccess && err == cudaSuccess)
+            err = r;
+        if (count && r == cudaSuccess) {
+            c->trace_calls += 1;
+            c->trace_ms += (double)ms;
+        }
+        c->trace_free.push_back(e);
+    }
+    c->trace_pending.clear();
+    return err;
+}
+
+// One traced API call: with tracing on, an NVTX range named after the call (seen by an attached
+// profiler) and two CUDA events around the stream work it enqueues, unless the stream is being
+// captured into a graph (events there become graph nodes and time nothing).  Declared after the
+// call's argument checks and DeviceGuard; the outermost of nested traced calls records.
+struct TraceScope {
+    kirin_ctx *c;
+    bool on = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TraceScope(kirin_ctx *ctx, const char *name) : c(ctx)
+    {
+        if (!c->tracing || c->trace_depth++ > 0)
+            return;
+        on = true;
+        nvtxRangePushA(name);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return;
+        }
+        if (!c->trace_free.empty()) {
+            e0 = c->trace_free.back().first;
+            e1 = c->trace_free.back().second;
+            c->trace_free.pop_back();
+        } else if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            if (e0)
+                cudaEventDestroy(e0);
+            cudaGetLastError();
+            e0 = e1 = nullptr;
+            return;
+        }
+        cudaEventRecord(e0, c->stream);
+    }
+    ~TraceScope()
+    {
+        if (!c->tracing && !on)
+            return;
+        if (c->trace_depth > 0)
+            --c->trace_depth;
+        if (!on)
+            return;
+        if (e0) {
+            cudaEventRecord(e1, c->stream);
+            c->trace_pending.emplace_back(e0, e1);
+            if (c->trace_pending.size() >= 1024)
+                trace_fold(c, true);
+        }
+        nvtxRangePop();
+    }
+};
 
 int check_params(double eps, double G, double r_min, int prec)
 {
@@ -1154,13 +1243,15 @@ int kirin_compute_forces(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list)
         n_i = ctx->n_j;
     if (n_i < 0 || n_i > ctx->n_max)
         return set_msg(ctx, KIRIN_EINVAL, "compute_forces: n_i out of range");
-    DeviceGuard dg(ctx->device);
-    const int32_t *d_list = nullptr;
-    if (i_list) {
+    if (i_list)
         for (int64_t k = 0; k < n_i; ++k)
             if (i_list[k] < 0 || i_list[k] >= ctx->n_j)
                 return set_msg(ctx, KIRIN_EINVAL, "compute_forces: i_list[%lld] = %d outside [0, %lld)",
                                (long long)k, i_list[k], (long long)ctx->n_j);
+    DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_compute_forces");
+    const int32_t *d_list = nullptr;
+    if (i_list) {
         // the previous upload may still be in flight from the pinned buffer
         CK(ctx, cudaStreamSynchronize(ctx->stream));
         memcpy(ctx->h_ilist, i_list, (size_t)n_i * sizeof(int32_t));
@@ -1267,6 +1358,7 @@ int kirin_compute_forces_nn_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_li
     if (n_i < 0 || n_i > ctx->n_max)
         return set_msg(ctx, KIRIN_EINVAL, "compute_forces_nn_dev: n_i out of range");
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_compute_forces_nn_dev");
     int rc = ensure_images(ctx);
     if (rc)
         return rc;
@@ -1304,6 +1396,7 @@ int kirin_compute_forces_dev(kirin_ctx *ctx, int64_t n_i, const int32_t *i_list,
     if (n_i < 0 || n_i > ctx->n_max)
         return set_msg(ctx, KIRIN_EINVAL, "compute_forces_dev: n_i out of range");
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_compute_forces_dev");
     int rc = ensure_images(ctx);
     if (rc)
         return rc;
@@ -1325,6 +1418,7 @@ int kirin_energy(kirin_ctx *ctx, const double *v, double *kin, double *pot)
     if (ctx->n_j == 0)
         return set_msg(ctx, KIRIN_ESTATE, "energy: no particles");
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_energy");
     int rc = ensure_images(ctx);
     if (rc)
         return rc;
@@ -1363,6 +1457,7 @@ int kirin_hermite_init(kirin_ctx *ctx, double t, double eta, double dt_min, doub
     if (ctx->n_j == 0)
         return set_msg(ctx, KIRIN_ESTATE, "hermite_init: no particles");
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_hermite_init");
     ctx->pred_mode = 0;
     ctx->images_dirty = true;
     int rc;
@@ -1402,6 +1497,7 @@ int kirin_hermite_block_step(kirin_ctx *ctx, double t_end, double *t_now, int64_
     if (!ctx->hermite_ready)
         return set_msg(ctx, KIRIN_ESTATE, "hermite_block_step: call kirin_hermite_init first");
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_hermite_block_step");
     const int n = (int)ctx->n_j;
     CK(ctx, launch_block_select(n, ctx->bt, ctx->bdt, t_end, ctx->d_ilist, ctx->d_scal, ctx->d_count,
                                 reinterpret_cast<unsigned long long *>(ctx->d_scal + 3), ctx->d_sel_counts,
@@ -1448,6 +1544,8 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
         return KIRIN_EINVAL;
     if (!ctx->hermite_ready)
         return set_msg(ctx, KIRIN_ESTATE, "hermite_run: call kirin_hermite_init first");
+    DeviceGuard dg0(ctx->device);
+    TraceScope ts(ctx, "kirin_hermite_run");
     if (ctx->device_loop && ctx->n_parts == 1)  // a partitioned context exchanges from the host each step
         return hermite_run_device(ctx, t_end, max_steps, n_steps, n_pairs);
     int64_t steps = 0;
@@ -1472,6 +1570,37 @@ int kirin_hermite_run(kirin_ctx *ctx, double t_end, int64_t max_steps, int64_t *
         *n_pairs = pairs;
     DeviceGuard dg(ctx->device);
     return read_device_errors(ctx);
+}
+
+int kirin_set_tracing(kirin_ctx *ctx, int32_t enable)
+{
+    if (!ctx)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    const cudaError_t err = trace_fold(ctx, false);  // pending pairs of the old setting are dropped
+    ctx->trace_calls = 0;
+    ctx->trace_ms = 0.0;
+    ctx->tracing = enable != 0;
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return set_msg(ctx, KIRIN_ECUDA, "set_tracing: %s", cudaGetErrorString(err));
+    }
+    return KIRIN_OK;
+}
+
+int kirin_get_trace(kirin_ctx *ctx, int64_t *n_calls, double *device_ms)
+{
+    if (!ctx || !n_calls || !device_ms)
+        return KIRIN_EINVAL;
+    DeviceGuard dg(ctx->device);
+    const cudaError_t err = trace_fold(ctx, true);
+    *n_calls = ctx->trace_calls;
+    *device_ms = ctx->trace_ms;
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return set_msg(ctx, KIRIN_ECUDA, "get_trace: %s", cudaGetErrorString(err));
+    }
+    return KIRIN_OK;
 }
 
 int kirin_set_shared_persistent(kirin_ctx *ctx, int32_t enable)
@@ -1508,6 +1637,7 @@ int kirin_hermite_shared_run(kirin_ctx *ctx, double dt, int64_t n_steps)
     if (!ctx->hermite_ready)
         return set_msg(ctx, KIRIN_ESTATE, "hermite_shared_run: call kirin_hermite_init first");
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_hermite_shared_run");
     const int n = (int)ctx->n_j;
     if (shared_steps_on(ctx) && n_steps > 0 && n_steps <= INT32_MAX) {
         // the whole run in one cooperative launch (small systems, mixed precision)
@@ -1617,6 +1747,7 @@ int kirin_accel_dev(kirin_ctx *ctx, int64_t n, const double *m, const double *x,
     if (n == 0)
         return KIRIN_OK;
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_accel_dev");
     const int64_t n_pad = round_up(n, TILE_J);
     CK(ctx, launch_pack_xm((int)n, (int)n_pad, m, x, img_m(ctx), img_d(ctx), err_word(ctx), ctx->stream));
     ctx->images_dirty = true;  // the images no longer show the context's particles
@@ -1631,6 +1762,7 @@ int kirin_accel_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const do
     if (n == 0)
         return KIRIN_OK;
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_accel_adjoint_dev");
     const int64_t n_pad = round_up(n, TILE_J);
     // images of (x, m) with g in the velocity slots
     CK(ctx, launch_predict_pack((int)n, (int)n_pad, 0.0, 0, m, x, g, nullptr, nullptr, nullptr, nullptr,
@@ -1649,6 +1781,7 @@ int kirin_leapfrog_dev(kirin_ctx *ctx, int64_t n, const double *m, double *x, do
     if (n == 0)
         return KIRIN_OK;
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_leapfrog_dev");
     const int nn = (int)n;
     const int64_t n_pad = round_up(n, TILE_J);
     const double h = 0.5 * dt;
@@ -1683,6 +1816,7 @@ int kirin_leapfrog_adjoint_dev(kirin_ctx *ctx, int64_t n, const double *m, const
     if (n == 0)
         return KIRIN_OK;
     DeviceGuard dg(ctx->device);
+    TraceScope ts(ctx, "kirin_leapfrog_adjoint_dev");
     const int nn = (int)n;
     const int64_t n_pad = round_up(n, TILE_J);
     const double h = 0.5 * dt;

@@ -68,6 +68,8 @@ def test_null_context_is_rejected(lib):
     assert lib.kirin_hermite_shared_run(None, 0.1, 1) == abi.KIRIN_EINVAL
     assert lib.kirin_set_shared_persistent(None, 1) == abi.KIRIN_EINVAL
     assert lib.kirin_get_shared_persistent(None, None) == abi.KIRIN_EINVAL
+    assert lib.kirin_set_tracing(None, 1) == abi.KIRIN_EINVAL
+    assert lib.kirin_get_trace(None, None, None) == abi.KIRIN_EINVAL
     assert lib.kirin_selftest_arrival_timeout(None, 1000) == abi.KIRIN_EINVAL
     assert lib.kirin_selftest_wait_timeout(None, 1000) == abi.KIRIN_EINVAL
     assert lib.kirin_last_error(None).decode() == "no context"
