@@ -540,7 +540,8 @@ struct TraceScope {
             e0 = e1 = nullptr;
             return;
         }
-        cudaEventRecord(e0, c->stream);
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess)
+            cudaGetLastError();  // the pair is then not counted; the call's own checks stay clean
     }
     ~TraceScope()
     {
@@ -551,10 +552,11 @@ struct TraceScope {
         if (!on)
             return;
         if (e0) {
-            cudaEventRecord(e1, c->stream);
+            if (cudaEventRecord(e1, c->stream) != cudaSuccess)
+                cudaGetLastError();
             c->trace_pending.emplace_back(e0, e1);
-            if (c->trace_pending.size() >= 1024)
-                trace_fold(c, true);
+            if (c->trace_pending.size() >= 1024 && trace_fold(c, true) != cudaSuccess)
+                cudaGetLastError();  // an unreadable pair is dropped, as kirin_get_trace would report
         }
         nvtxRangePop();
     }
